@@ -1,0 +1,185 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) fused MRT lattice Boltzmann step for
+ * natural convection of a power-law fluid in a porous square cavity
+ * (Islam, Nag & Molla, "GPU Accelerated Lattice Boltzmann Simulation of
+ * Non-Newtonian Power-Law Fluid in a Porous Enclosure", ICME2019).
+ *
+ * The problem (section "Mathematical formulations"): a cavity of side L with
+ * the left wall hot (theta = 1), the right wall cold (theta = 0), adiabatic
+ * top and bottom walls and no-slip everywhere, filled with a porous medium
+ * (Darcy number Da, porosity) saturated by a power-law fluid (index n), driven
+ * by Boussinesq buoyancy (Rayleigh number Ra, Prandtl number Pr).
+ *
+ * Conventions for every call:
+ *  - Return value 0 on success, a negative LBM_ERR_* code otherwise; no
+ *    exception or signal crosses this boundary.  lbm_strerror() names a code.
+ *  - A node (i, j) sits at x = i + 1/2, y = j + 1/2 in lattice units; the
+ *    walls lie halfway between the boundary nodes and the domain edge.
+ *    Every host array of per-node values is row-major [ny][nx] (x fastest).
+ *  - Host buffers are owned by the caller and must stay valid for the call.
+ *    Device memory is owned by the library (allocated in lbm_init, released
+ *    in lbm_destroy); no device pointer is exposed.
+ *  - lbm_step only enqueues work on the context's stream; every call that
+ *    returns host data synchronises that stream before returning.
+ *  - A context may be used by one host thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,       /* invalid argument, size or state             */
+    LBM_ERR_UNSTABLE = -2,  /* a relaxation time maps to <= 1/2 + 1e-6     */
+    LBM_ERR_NONFINITE = -3, /* NaN or Inf found in the fields              */
+    LBM_ERR_CUDA = -4,      /* a CUDA runtime call failed                  */
+    LBM_ERR_OOM = -5,       /* device memory allocation failed             */
+    LBM_ERR_TIMEOUT = -6,   /* a bounded device wait gave up               */
+    LBM_ERR_UNSUPPORTED = -7/* option combination not built               */
+};
+
+/* Storage precision of the distributions.  Arithmetic is FP64 for LBM_F64
+ * and FP32 otherwise.  The *D forms store the deviation of each population
+ * from its rest-state value (w_i for the flow, w_i T_m for the heat) in 16
+ * bits; the per-node relaxation time is then stored as FP32. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_BF16D = 2, LBM_F16D = 3 } lbm_prec;
+
+/* Options; lbm_default_opts() fills the defaults listed per field. */
+typedef struct {
+    int prec;          /* lbm_prec                                   [F64]  */
+    double Ma;         /* Mach number of the velocity scale U_c      [0.1]  */
+    int clamp_mode;    /* 0: literal modified power law, Eq. (MPL);
+                          1: continuous clamp of the shear rate      [0]    */
+    int porous_model;  /* 0: the paper's Darcy drag (porosity 1, no
+                          Forchheimer term); 1: generalized Brinkman-
+                          Forchheimer model with the porosity        [1]    */
+    double s_e, s_p;   /* free thermal MRT rates (4th, 5th moment)   [1.5]  */
+    int resid_interval;/* steps between convergence checks           [1000] */
+    int layout;        /* 0: two-buffer pull scheme                  [0]    */
+    void *cuda_stream; /* cudaStream_t to run on; NULL: the library
+                          creates and owns one                       [NULL] */
+    int device;        /* CUDA device ordinal the context lives on and
+                          every call selects; -1: the device current
+                          in the calling thread at lbm_init          [-1]   */
+} lbm_opts;
+
+/* Lattice-unit parameters the library derived from the problem groups
+ * (a reading of the paper, which defers the mapping to earlier work):
+ *   U_c = Ma / sqrt(3), L = nx;
+ *   nu_ref = nu_0 U_c L with nu_0 = Pr / sqrt(Ra)^(2-n) (power-law section);
+ *   gamma* = |gamma| L / U_c (non-dimensional shear rate for Eq. MPL);
+ *   tauT = 3 U_c L / sqrt(Ra) + 1/2 (diffusivity 1/sqrt(Ra) of the energy
+ *   equation); g beta = Pr U_c^2 / L (buoyancy term Pr theta); K = Da L^2;
+ *   tau = 3 nu + 1/2 (Eq. kinematic_viscosity with c_s^2 = 1/3). */
+typedef struct {
+    int nx, ny;
+    double n, nu_ref, gamma_scale, gamma1, gamma2;
+    int clamp_mode;
+    double K, eps, Feps, gbeta, Tm, tauT, s_e, s_p;
+    double T_hot, T_cold, L, tau0;
+    int prec;
+    int64_t pitch;     /* elements between rows of a device plane           */
+} lbm_lattice;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Fill *opts with the defaults above.  Never fails. */
+void lbm_default_opts(lbm_opts *opts);
+
+/* Create a cavity run: nx x ny nodes, power-law index n, Darcy number Da,
+ * Rayleigh number Ra, Prandtl number Pr and porosity (problem statement of
+ * section "Mathematical formulations"; groups of Eq. non_dim_var).  The
+ * state starts at rest: rho = 1, u = 0, T = (T_h + T_c)/2, f = f^eq,
+ * g = g^eq, tau = tau0.  opts may be NULL (defaults).
+ * Errors: LBM_ERR_ARG (nx or ny < 2, ny > 65535, n, Da, Ra or Pr <= 0, porosity outside
+ * (0, 1], bad option), LBM_ERR_UNSTABLE, LBM_ERR_OOM, LBM_ERR_CUDA.
+ * On error *out is set to NULL and nothing is leaked. */
+int lbm_init(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra,
+             double Pr, double porosity, const lbm_opts *opts);
+
+/* Release every device and host resource of ctx (NULL is ignored). */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Copy the lattice-unit parameters of ctx into *out. */
+int lbm_get_lattice(const lbm_ctx *ctx, lbm_lattice *out);
+
+/* Advance k >= 0 time steps.  Each step is one launch of the fused kernel:
+ * pull streaming with the wall rules, macroscopic moments (Eqs.
+ * macro_fluid_density, velo), porous velocity solve, strain rate from the
+ * non-equilibrium moments and the modified power law (Eq. MPL and the
+ * strain-rate equation), forced MRT flow collision (Eq. normalMRTequation)
+ * and MRT thermal collision (Eq. thermalMRTequation).  Asynchronous on the
+ * context's stream.  Errors: LBM_ERR_ARG (k < 0), LBM_ERR_CUDA. */
+int lbm_step(lbm_ctx *ctx, int64_t k);
+
+/* Wait for all work queued on the context's stream. */
+int lbm_synchronize(lbm_ctx *ctx);
+
+/* Streamed (pre-collision) macroscopic fields at the current step, i.e. the
+ * values the next collision sees: density, velocity after the porous solve,
+ * temperature, and the apparent lattice viscosity the next collision will
+ * use.  Each pointer is NULL (skipped) or a host array of nx*ny doubles.
+ * Synchronous.  Errors: LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_fields(lbm_ctx *ctx, double *rho, double *ux, double *uy, double *T,
+               double *nu);
+
+/* Average Nusselt number on the hot wall (Eq. avgNu: the mean over the wall
+ * of Nu(Y) = -d theta/dX at X = 0) and the outward one on the cold wall,
+ * from the streamed temperature, accumulated in FP64.  The wall derivative is
+ * the second-order one-sided difference through the wall value and the two
+ * nearest nodes: -L (9 theta_0 - theta_1 - 8 theta_w) / 3.  nu_local is NULL
+ * or a host array of ny doubles (hot-wall local Nu).  Synchronous. */
+int lbm_nusselt(lbm_ctx *ctx, double *nu_hot, double *nu_cold,
+                double *nu_local);
+
+/* Convergence residual against the fields of the previous call:
+ * r = max over phi in {u_x, u_y, T} of ||phi - phi_prev||_2 / ||phi||_2,
+ * accumulated in FP64, plus a flag for any non-finite value.  The first call
+ * after lbm_init or lbm_set_state only stores the snapshot and returns
+ * *resid = +inf.  Synchronous.  Returns LBM_ERR_NONFINITE if the flag is set. */
+int lbm_residual(lbm_ctx *ctx, double *resid);
+
+/* Run until the residual (checked every resid_interval steps) falls below
+ * tol, stagnates (no new minimum over 10 checks), or max_steps is reached.
+ * *steps_done, *resid and *reason (0 tol reached, 1 stagnated, 2 max_steps)
+ * may be NULL.  Returns LBM_ERR_NONFINITE on NaN or Inf. */
+int lbm_run_to_steady(lbm_ctx *ctx, double tol, int64_t max_steps,
+                      int64_t *steps_done, double *resid, int *reason);
+
+/* Size in bytes of the native state: 14 planes of nx*ny distribution values
+ * in the storage type (f0..f8, then g0..g4; 16-bit forms hold deviations),
+ * followed by one plane of nx*ny relaxation times (double for LBM_F64, float
+ * otherwise), each plane row-major [ny][nx]. */
+size_t lbm_state_bytes(const lbm_ctx *ctx);
+
+/* Copy the native state (layout of lbm_state_bytes) to / from host memory.
+ * bytes must equal lbm_state_bytes(ctx).  Pinned host memory gives
+ * asynchronous-speed copies.  Synchronous.  Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+int lbm_get_state(lbm_ctx *ctx, void *host, size_t bytes);
+int lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
+
+/* The post-collision state as FP64 host arrays: f[9][ny][nx], g[5][ny][nx]
+ * and tau[ny][nx] (full population values, deviations resolved).  The
+ * import rounds to the storage precision.  Any pointer may be NULL (skipped
+ * on export, left unchanged on import).  Synchronous. */
+int lbm_get_state_f64(lbm_ctx *ctx, double *f, double *g, double *tau);
+int lbm_set_state_f64(lbm_ctx *ctx, const double *f, const double *g,
+                      const double *tau);
+
+/* Name of an LBM_* code (static storage). */
+const char *lbm_strerror(int code);
+
+/* Text of the last CUDA runtime error seen by this host thread inside the
+ * library ("" if none); thread-local storage, valid until the next call. */
+const char *lbm_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,404 @@
+// lbm_capi.cu -- the C ABI of include/lbm.h: argument checks, the mapping of
+// the paper's non-dimensional groups to lattice units, device memory, and the
+// host-side control of the kernels in lbm_kernels.cu.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "lbm_internal.h"
+
+static thread_local char g_last_cuda[256] = "";
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            snprintf(g_last_cuda, sizeof(g_last_cuda), "%s: %s", #call,               \
+                     cudaGetErrorString(e_));                                          \
+            return e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;       \
+        }                                                                              \
+    } while (0)
+
+namespace {
+
+size_t store_elem(int prec) { return prec == LBM_F64 ? 8 : (prec == LBM_F32 ? 4 : 2); }
+size_t tau_elem(int prec) { return prec == LBM_F64 ? 8 : 4; }
+
+// Mapping of the non-dimensional problem to lattice units.  The paper defers
+// it to earlier work, so this is a stated reading:
+//   velocity scale U_c = Ma c_s (c_s^2 = 1/3), length scale L = nx;
+//   alpha = U_c L / sqrt(Ra) (energy equation: diffusivity 1/sqrt(Ra)),
+//   tauT = 3 alpha + 1/2;
+//   nu_0 = Pr / sqrt(Ra)^(2 - n) (power-law section), nu_ref = nu_0 U_c L;
+//   gamma* = |gamma| L / U_c is the shear rate the thresholds gamma_1 = 0.01,
+//   gamma_2 = 1e6 of Eq. (MPL) apply to;
+//   g beta (T_h - T_c) = Pr U_c^2 / L (buoyancy Pr theta of the
+//   non-dimensional v-momentum equation), T_m = (T_h + T_c)/2;
+//   K = Da L^2 (Eq. non_dim_var); tau = 3 nu + 1/2 (Eq. kinematic_viscosity).
+//   Porous model 1 (generalized Brinkman-Forchheimer): porosity eps and
+//   Ergun's F_eps = 1.75 / sqrt(150 eps^3); model 0: eps = 1, F_eps = 0.
+int map_lattice(int nx, int ny, double n, double Da, double Ra, double Pr, double porosity,
+                const lbm_opts &o, lbm_lattice *L)
+{
+    if (nx < 2 || ny < 2 || ny > 65535 || nx > (1 << 30) || !(n > 0) || !(Da > 0) || !(Ra > 0) || !(Pr > 0) || !(porosity > 0) ||
+        porosity > 1 || !isfinite(n) || !isfinite(Da) || !isfinite(Ra) || !isfinite(Pr))
+        return LBM_ERR_ARG;
+    if (o.prec < LBM_F64 || o.prec > LBM_F16D || !(o.Ma > 0) || o.Ma > 1 ||
+        (o.clamp_mode != 0 && o.clamp_mode != 1) || (o.porous_model != 0 && o.porous_model != 1) ||
+        !(o.s_e > 0) || !(o.s_e < 2) || !(o.s_p > 0) || !(o.s_p < 2) || o.resid_interval < 1 ||
+        o.device < -1)
+        return LBM_ERR_ARG;
+    if (o.layout != 0) return LBM_ERR_UNSUPPORTED;
+    memset(L, 0, sizeof(*L));
+    const double Uc = o.Ma / sqrt(3.0);
+    const double len = (double)nx;
+    L->nx = nx;
+    L->ny = ny;
+    L->n = n;
+    L->nu_ref = Pr / pow(sqrt(Ra), 2.0 - n) * Uc * len;
+    L->gamma_scale = len / Uc;
+    L->gamma1 = 0.01;
+    L->gamma2 = 1.0e6;
+    L->clamp_mode = o.clamp_mode;
+    L->K = Da * len * len;
+    L->eps = o.porous_model == 1 ? porosity : 1.0;
+    L->Feps = o.porous_model == 1 ? 1.75 / sqrt(150.0 * porosity * porosity * porosity) : 0.0;
+    L->T_hot = 1.0;
+    L->T_cold = 0.0;
+    L->Tm = 0.5;
+    L->gbeta = Pr * Uc * Uc / len;
+    L->tauT = 3.0 * Uc * len / sqrt(Ra) + 0.5;
+    L->s_e = o.s_e;
+    L->s_p = o.s_p;
+    L->L = len;
+    // at rest gamma* = 0: D = 1 for the literal law, gamma_1^(n-1) for the clamp
+    const double D0 = o.clamp_mode == 0 ? 1.0 : pow(L->gamma1, n - 1.0);
+    L->tau0 = 3.0 * L->nu_ref * D0 + 0.5;
+    L->prec = o.prec;
+    if (!(L->tau0 > 0.5 + 1e-6) || !(L->tauT > 0.5 + 1e-6)) return LBM_ERR_UNSTABLE;
+    return LBM_OK;
+}
+
+void free_ctx(lbm_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    for (int b = 0; b < 2; b++) {
+        cudaFree(c->buf.dist[b]);
+        cudaFree(c->buf.tau[b]);
+    }
+    cudaFree(c->d_small);
+    cudaFreeHost(c->h_small);
+    cudaFree(c->d_stage);
+    cudaFree(c->d_snap);
+    cudaFree(c->d_part);
+    cudaFree(c->d_nuloc);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int ensure_stage(lbm_ctx *c)
+{
+    if (c->d_stage) return LBM_OK;
+    CK(cudaMalloc(&c->d_stage, sizeof(double) * 15 * (size_t)c->nx * c->ny));
+    return LBM_OK;
+}
+
+int init_ctx(lbm_ctx *c)
+{
+    if (c->opts.device >= 0) {
+        CK(cudaSetDevice(c->opts.device));
+        c->device = c->opts.device;
+    } else {
+        CK(cudaGetDevice(&c->device));
+    }
+    const size_t es = store_elem(c->opts.prec), ts = tau_elem(c->opts.prec);
+    c->pitch = ((int64_t)c->nx + 63) / 64 * 64;
+    c->plane = c->pitch * c->ny;
+    c->dist_elem = es;
+    c->tau_elem = ts;
+    if (c->opts.cuda_stream) {
+        c->stream = (cudaStream_t)c->opts.cuda_stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    for (int b = 0; b < 2; b++) {
+        CK(cudaMalloc(&c->buf.dist[b], es * 14 * (size_t)c->plane));
+        CK(cudaMalloc(&c->buf.tau[b], ts * (size_t)c->plane));
+        CK(cudaMemsetAsync(c->buf.dist[b], 0, es * 14 * (size_t)c->plane, c->stream));
+        CK(cudaMemsetAsync(c->buf.tau[b], 0, ts * (size_t)c->plane, c->stream));
+    }
+    CK(cudaMalloc(&c->d_small, sizeof(double) * 16));
+    CK(cudaMallocHost(&c->h_small, sizeof(double) * 16));
+    CK(cudaMalloc(&c->d_nuloc, sizeof(double) * (size_t)c->ny));
+    c->n_part = lbm::residual_blocks(c);
+    CK(cudaMalloc(&c->d_part, sizeof(double) * 8 * (size_t)c->n_part));
+    c->lat.pitch = c->pitch;
+    CK(lbm::launch_init(c));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lbm_default_opts(lbm_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->prec = LBM_F64;
+    o->Ma = 0.1;
+    o->clamp_mode = 0;
+    o->porous_model = 1;
+    o->s_e = 1.5;
+    o->s_p = 1.5;
+    o->resid_interval = 1000;
+    o->layout = 0;
+    o->cuda_stream = nullptr;
+    o->device = -1;
+}
+
+int lbm_init(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra, double Pr,
+             double porosity, const lbm_opts *opts)
+{
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    lbm_opts o;
+    if (opts)
+        o = *opts;
+    else
+        lbm_default_opts(&o);
+    lbm_lattice L;
+    int rc = map_lattice(nx, ny, n, Da, Ra, Pr, porosity, o, &L);
+    if (rc != LBM_OK) return rc;
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ERR_OOM;
+    c->nx = nx;
+    c->ny = ny;
+    c->opts = o;
+    c->lat = L;
+    rc = init_ctx(c);
+    if (rc != LBM_OK) {
+        free_ctx(c);
+        return rc;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+}
+
+int lbm_get_lattice(const lbm_ctx *c, lbm_lattice *out)
+{
+    if (!c || !out) return LBM_ERR_ARG;
+    *out = c->lat;
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx *c, int64_t k)
+{
+    if (!c || k < 0) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    for (int64_t t = 0; t < k; t++) CK(lbm::launch_step(c));
+    c->steps += k;
+    return LBM_OK;
+}
+
+int lbm_synchronize(lbm_ctx *c)
+{
+    if (!c) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_fields(lbm_ctx *c, double *rho, double *ux, double *uy, double *T, double *nu)
+{
+    if (!c) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    int rc = ensure_stage(c);
+    if (rc) return rc;
+    CK(lbm::launch_fields(c, c->d_stage));
+    const size_t n = (size_t)c->nx * c->ny;
+    double *outs[5] = {rho, ux, uy, T, nu};
+    for (int i = 0; i < 5; i++)
+        if (outs[i])
+            CK(cudaMemcpyAsync(outs[i], c->d_stage + i * n, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                               c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_nusselt(lbm_ctx *c, double *hot, double *cold, double *local)
+{
+    if (!c) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(lbm::launch_nusselt(c));
+    CK(cudaMemcpyAsync(c->h_small, c->d_small, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
+    if (local)
+        CK(cudaMemcpyAsync(local, c->d_nuloc, sizeof(double) * c->ny, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hot) *hot = c->h_small[0];
+    if (cold) *cold = c->h_small[1];
+    return LBM_OK;
+}
+
+int lbm_residual(lbm_ctx *c, double *resid)
+{
+    if (!c) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    if (!c->d_snap) CK(cudaMalloc(&c->d_snap, sizeof(double) * 3 * (size_t)c->nx * c->ny));
+    const bool first = !c->have_snap;
+    CK(lbm::launch_residual(c, first));
+    CK(cudaMemcpyAsync(c->h_small + 2, c->d_small + 2, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_snap = true;
+    double r = c->h_small[2];
+    if (c->h_small[3] > r) r = c->h_small[3];
+    if (c->h_small[4] > r) r = c->h_small[4];
+    if (first) r = INFINITY;
+    if (resid) *resid = r;
+    if (c->h_small[5] > 0.0) return LBM_ERR_NONFINITE;
+    return LBM_OK;
+}
+
+int lbm_run_to_steady(lbm_ctx *c, double tol, int64_t max_steps, int64_t *steps_done, double *resid,
+                      int *reason)
+{
+    if (!c || max_steps < 0 || !(tol >= 0)) return LBM_ERR_ARG;
+    c->have_snap = false;
+    double r = INFINITY, best = INFINITY;
+    int rc = lbm_residual(c, &r);
+    int64_t done = 0;
+    int why = 2, since_best = 0;
+    while (rc == LBM_OK && done < max_steps) {
+        int64_t k = max_steps - done;
+        if (k > c->opts.resid_interval) k = c->opts.resid_interval;
+        rc = lbm_step(c, k);
+        if (rc) break;
+        done += k;
+        rc = lbm_residual(c, &r);
+        if (rc) break;
+        if (r < tol) {
+            why = 0;
+            break;
+        }
+        if (r < best) {
+            best = r;
+            since_best = 0;
+        } else if (++since_best >= 10) {
+            why = 1;
+            break;
+        }
+    }
+    if (steps_done) *steps_done = done;
+    if (resid) *resid = r;
+    if (reason) *reason = why;
+    return rc;
+}
+
+size_t lbm_state_bytes(const lbm_ctx *c)
+{
+    if (!c) return 0;
+    const size_t n = (size_t)c->nx * c->ny;
+    return 14 * n * c->dist_elem + n * c->tau_elem;
+}
+
+int lbm_get_state(lbm_ctx *c, void *host, size_t bytes)
+{
+    if (!c || !host || bytes != lbm_state_bytes(c)) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    const size_t es = c->dist_elem, ts = c->tau_elem, n = (size_t)c->nx * c->ny;
+    CK(cudaMemcpy2DAsync(host, c->nx * es, c->buf.dist[c->cur], c->pitch * es, c->nx * es, 14 * (size_t)c->ny,
+                         cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpy2DAsync((char *)host + 14 * n * es, c->nx * ts, c->buf.tau[c->cur], c->pitch * ts,
+                         c->nx * ts, c->ny, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_set_state(lbm_ctx *c, const void *host, size_t bytes)
+{
+    if (!c || !host || bytes != lbm_state_bytes(c)) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    const size_t es = c->dist_elem, ts = c->tau_elem, n = (size_t)c->nx * c->ny;
+    CK(cudaMemcpy2DAsync(c->buf.dist[c->cur], c->pitch * es, host, c->nx * es, c->nx * es, 14 * (size_t)c->ny,
+                         cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpy2DAsync(c->buf.tau[c->cur], c->pitch * ts, (const char *)host + 14 * n * es, c->nx * ts,
+                         c->nx * ts, c->ny, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_snap = false;
+    return LBM_OK;
+}
+
+int lbm_get_state_f64(lbm_ctx *c, double *f, double *g, double *tau)
+{
+    if (!c) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    int rc = ensure_stage(c);
+    if (rc) return rc;
+    CK(lbm::launch_export_f64(c, c->d_stage));
+    const size_t n = (size_t)c->nx * c->ny;
+    if (f) CK(cudaMemcpyAsync(f, c->d_stage, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, c->stream));
+    if (g)
+        CK(cudaMemcpyAsync(g, c->d_stage + 9 * n, sizeof(double) * 5 * n, cudaMemcpyDeviceToHost, c->stream));
+    if (tau)
+        CK(cudaMemcpyAsync(tau, c->d_stage + 14 * n, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_set_state_f64(lbm_ctx *c, const double *f, const double *g, const double *tau)
+{
+    if (!c) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    int rc = ensure_stage(c);
+    if (rc) return rc;
+    const size_t n = (size_t)c->nx * c->ny;
+    int mask = 0;
+    if (f) {
+        CK(cudaMemcpyAsync(c->d_stage, f, sizeof(double) * 9 * n, cudaMemcpyHostToDevice, c->stream));
+        mask |= 1;
+    }
+    if (g) {
+        CK(cudaMemcpyAsync(c->d_stage + 9 * n, g, sizeof(double) * 5 * n, cudaMemcpyHostToDevice, c->stream));
+        mask |= 2;
+    }
+    if (tau) {
+        CK(cudaMemcpyAsync(c->d_stage + 14 * n, tau, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+        mask |= 4;
+    }
+    if (mask) CK(lbm::launch_import_f64(c, c->d_stage, mask));
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_snap = false;
+    return LBM_OK;
+}
+
+const char *lbm_strerror(int code)
+{
+    switch (code) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_ERR_ARG: return "LBM_ERR_ARG: invalid argument";
+    case LBM_ERR_UNSTABLE: return "LBM_ERR_UNSTABLE: relaxation time <= 1/2";
+    case LBM_ERR_NONFINITE: return "LBM_ERR_NONFINITE: NaN or Inf in the fields";
+    case LBM_ERR_CUDA: return "LBM_ERR_CUDA: CUDA runtime error";
+    case LBM_ERR_OOM: return "LBM_ERR_OOM: device allocation failed";
+    case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT: bounded device wait gave up";
+    case LBM_ERR_UNSUPPORTED: return "LBM_ERR_UNSUPPORTED: option not built";
+    default: return "unknown lbm error";
+    }
+}
+
+const char *lbm_last_cuda_error(void) { return g_last_cuda; }
+
+}  // extern "C"

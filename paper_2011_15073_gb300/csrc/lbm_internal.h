@@ -1,0 +1,64 @@
+// lbm_internal.h -- library-private declarations shared by the CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// Device buffers of one run.  Distribution planes: f0..f8 then g0..g4, each
+// `plane` elements apart, rows `pitch` elements apart (pitch a multiple of 64
+// elements so that rows start 128-byte aligned for every storage type).
+struct Buffers {
+    void *dist[2] = {nullptr, nullptr};  // 14 planes in the storage type
+    void *tau[2] = {nullptr, nullptr};   // 1 plane (double for F64, else float)
+};
+
+struct Launch {
+    const void *src;
+    void *dst;
+    const void *tsrc;
+    void *tdst;
+};
+
+}  // namespace lbm
+
+struct lbm_ctx {
+    int nx = 0, ny = 0;
+    int device = 0;
+    lbm_opts opts{};
+    lbm_lattice lat{};
+    int64_t pitch = 0, plane = 0;  // elements
+    size_t dist_elem = 0, tau_elem = 0;
+    lbm::Buffers buf;
+    int cur = 0;  // buffer holding the current post-collision state
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    double *d_small = nullptr;   // 16 doubles of small device results
+    double *h_small = nullptr;   // pinned mirror of d_small
+    double *d_stage = nullptr;   // lazily allocated FP64 staging (15 planes)
+    double *d_snap = nullptr;    // residual snapshot u_x, u_y, T [3][ny][nx]
+    double *d_part = nullptr;    // per-block partial sums of the residual
+    int n_part = 0;
+    double *d_nuloc = nullptr;   // local hot-wall Nu [ny]
+    bool have_snap = false;
+    int64_t steps = 0;
+};
+
+namespace lbm {
+
+// Host launchers (lbm_kernels.cu).  All enqueue on ctx->stream and return a
+// cudaError_t from cudaGetLastError().
+cudaError_t launch_init(lbm_ctx *c);
+cudaError_t launch_step(lbm_ctx *c);
+cudaError_t launch_fields(lbm_ctx *c, double *d_out5);
+cudaError_t launch_nusselt(lbm_ctx *c);  // -> d_small[0..1], d_nuloc
+cudaError_t launch_residual(lbm_ctx *c, bool first);  // -> d_small[2..5]
+cudaError_t launch_import_f64(lbm_ctx *c, const double *d_src15, int mask);
+cudaError_t launch_export_f64(lbm_ctx *c, double *d_dst15);
+int residual_blocks(const lbm_ctx *c);
+
+}  // namespace lbm

@@ -1,0 +1,364 @@
+// lbm_kernels.cu -- kernels of the fused MRT step and its reductions, with
+// their host launchers, instantiated for every storage precision.
+#include <math.h>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ------------------------------------------------------------ parameters
+template <class R>
+static Phys<R> make_params(const lbm_ctx *c)
+{
+    const lbm_lattice &L = c->lat;
+    Phys<R> p;
+    p.nx = c->nx;
+    p.ny = c->ny;
+    p.pitch = c->pitch;
+    p.plane = c->plane;
+    p.nu_ref = R(L.nu_ref);
+    p.gamma_scale = R(L.gamma_scale);
+    p.gamma1 = R(L.gamma1);
+    p.gamma2 = R(L.gamma2);
+    p.nm1 = R(L.n - 1.0);
+    p.D_hi = R(pow(L.gamma2, L.n - 1.0));
+    p.clamp_mode = L.clamp_mode;
+    p.eps = R(L.eps);
+    p.inv_eps = R(1.0 / L.eps);
+    p.half_eps_invK = R(L.eps / (4.0 * L.K));
+    p.eps_invK = R(L.eps / L.K);
+    p.c1 = R(L.eps * L.Feps / (2.0 * sqrt(L.K)));
+    p.eFe_isqK = R(L.eps * L.Feps / sqrt(L.K));
+    p.gbeta = R(L.gbeta);
+    p.Tm = R(L.Tm);
+    p.omegaT = R(1.0 / L.tauT);
+    p.s_e = R(L.s_e);
+    p.s_p = R(L.s_p);
+    p.abb_hot = R(2.0 / 6.0 * L.T_hot);
+    p.abb_cold = R(2.0 / 6.0 * L.T_cold);
+    return p;
+}
+
+// ---------------------------------------------------------------- kernels
+template <int PREC>
+__global__ void init_kernel(typename Store<PREC>::S *__restrict__ dist,
+                            typename Store<PREC>::TauS *__restrict__ tau,
+                            Phys<typename Store<PREC>::R> p, double tau0, double T0)
+{
+    using St = Store<PREC>;
+    using R = typename St::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= p.nx) return;
+    const int64_t k = (int64_t)y * p.pitch + x;
+    for (int i = 0; i < 9; i++) St::st(dist, i * p.plane + k, R(rest_f(i)), R(rest_f(i)));
+    for (int i = 0; i < 5; i++) {
+        const R v = R(rest_g(i) * 2.0 * T0);  // w_i T0 (rest_g holds w_i / 2)
+        St::st(dist + 9 * p.plane, i * p.plane + k, v, R(rest_g(i)));
+    }
+    tau[k] = typename St::TauS(tau0);
+}
+
+// One time step of the whole cavity: pull streaming with the wall rules,
+// collision, store to the other buffer.  One thread per node.
+template <int PREC>
+__global__ void __launch_bounds__(128)
+step_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
+            const typename Store<PREC>::TauS *__restrict__ tsrc, typename Store<PREC>::TauS *__restrict__ tdst,
+            Phys<typename Store<PREC>::R> p)
+{
+    using St = Store<PREC>;
+    using R = typename St::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= p.nx) return;
+    const int64_t k = (int64_t)y * p.pitch + x;
+    R f[9], g[5];
+    pull<PREC, R>(src, p, x, y, f, g);
+    Macro<R> m;
+    const R tau = collide<R>(p, f, g, R(tsrc[k]), m);
+#pragma unroll
+    for (int i = 0; i < 9; i++) St::st(dst, i * p.plane + k, f[i], R(rest_f(i)));
+#pragma unroll
+    for (int i = 0; i < 5; i++) St::st(dst + 9 * p.plane, i * p.plane + k, g[i], R(rest_g(i)));
+    tdst[k] = typename St::TauS(tau);
+}
+
+// Streamed macroscopic fields: rho, u_x, u_y, T, nu -> out[5][ny][nx].
+template <int PREC>
+__global__ void fields_kernel(const typename Store<PREC>::S *__restrict__ src,
+                              const typename Store<PREC>::TauS *__restrict__ tsrc,
+                              Phys<typename Store<PREC>::R> p, double *__restrict__ out)
+{
+    using St = Store<PREC>;
+    using R = typename St::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= p.nx) return;
+    const int64_t k = (int64_t)y * p.pitch + x;
+    const int64_t q = (int64_t)y * p.nx + x, n = (int64_t)p.nx * p.ny;
+    R f[9], g[5];
+    pull<PREC, R>(src, p, x, y, f, g);
+    Macro<R> m;
+    collide<R>(p, f, g, R(tsrc[k]), m);
+    out[q] = double(m.rho);
+    out[n + q] = double(m.ux);
+    out[2 * n + q] = double(m.uy);
+    out[3 * n + q] = double(m.T);
+    out[4 * n + q] = double(m.nu);
+}
+
+// FP64 block sum of one value (blockDim.x a multiple of 32, <= 1024); the
+// reduction tree is fixed, so results are reproducible run to run.
+__device__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = lane < nw ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+// Streamed temperature of node (x, y) in FP64 (thermal part of the pull).
+template <int PREC>
+__device__ double streamed_T(const typename Store<PREC>::S *__restrict__ src,
+                             const Phys<typename Store<PREC>::R> &p, int x, int y)
+{
+    using R = typename Store<PREC>::R;
+    R f[9], g[5];
+    pull<PREC, R>(src, p, x, y, f, g);
+    return (double)g[0] + (double)g[1] + (double)g[2] + (double)g[3] + (double)g[4];
+}
+
+// Wall Nusselt numbers: one block; row j of the hot wall gets
+// Nu_j = -L (9 theta_0 - theta_1 - 8) / 3, the cold wall the outward
+// L (9 theta_{nx-1} - theta_{nx-2}) / 3, theta = (T - T_c) / (T_h - T_c).
+template <int PREC>
+__global__ void __launch_bounds__(256)
+nusselt_kernel(const typename Store<PREC>::S *__restrict__ src, Phys<typename Store<PREC>::R> p,
+               double T_hot, double T_cold, double Lw, double *__restrict__ small,
+               double *__restrict__ nuloc)
+{
+    __shared__ double sh[32];
+    const double dT = T_hot - T_cold;
+    double sh_hot = 0.0, sh_cold = 0.0;
+    for (int j = threadIdx.x; j < p.ny; j += blockDim.x) {
+        const double t0 = (streamed_T<PREC>(src, p, 0, j) - T_cold) / dT;
+        const double t1 = (streamed_T<PREC>(src, p, 1, j) - T_cold) / dT;
+        const double ta = (streamed_T<PREC>(src, p, p.nx - 1, j) - T_cold) / dT;
+        const double tb = (streamed_T<PREC>(src, p, p.nx - 2, j) - T_cold) / dT;
+        const double nh = -Lw * (9.0 * t0 - t1 - 8.0) / 3.0;
+        const double nc = Lw * (9.0 * ta - tb) / 3.0;
+        nuloc[j] = nh;
+        sh_hot += nh;
+        sh_cold += nc;
+    }
+    const double a = block_sum(sh_hot, sh);
+    const double b = block_sum(sh_cold, sh);
+    if (threadIdx.x == 0) {
+        small[0] = a / p.ny;
+        small[1] = b / p.ny;
+    }
+}
+
+// Convergence residual, pass 1: each block accumulates, over a fixed
+// grid-stride set of nodes, sum (phi - phi_prev)^2 and sum phi^2 for
+// phi in {u_x, u_y, T} plus a count of non-finite values, and writes its
+// seven partial sums to part[blockIdx.x * 8 + 0..6].  The snapshot is updated.
+template <int PREC>
+__global__ void __launch_bounds__(256)
+residual_kernel(const typename Store<PREC>::S *__restrict__ src,
+                const typename Store<PREC>::TauS *__restrict__ tsrc, Phys<typename Store<PREC>::R> p,
+                double *__restrict__ snap, double *__restrict__ part, int first)
+{
+    using R = typename Store<PREC>::R;
+    __shared__ double sh[32];
+    const int64_t n = (int64_t)p.nx * p.ny;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int y = (int)(q / p.nx), x = (int)(q - (int64_t)y * p.nx);
+        R f[9], g[5];
+        pull<PREC, R>(src, p, x, y, f, g);
+        const Macro<R> m = macro<R>(p, f, g, R(tsrc[(int64_t)y * p.pitch + x]));
+        const double v[3] = {double(m.ux), double(m.uy), double(m.T)};
+        for (int c = 0; c < 3; c++) {
+            const double old = first ? v[c] : snap[c * n + q];
+            const double d = v[c] - old;
+            acc[2 * c] += d * d;
+            acc[2 * c + 1] += v[c] * v[c];
+            if (!isfinite(v[c])) acc[6] += 1.0;
+            snap[c * n + q] = v[c];
+        }
+    }
+    for (int c = 0; c < 7; c++) {
+        const double s = block_sum(acc[c], sh);
+        if (threadIdx.x == 0) part[blockIdx.x * 8 + c] = s;
+    }
+}
+
+// Pass 2: one block sums the partials in block order and writes
+// small[2..4] = relative change of u_x, u_y, T and small[5] = non-finite count.
+__global__ void __launch_bounds__(256)
+residual_final_kernel(const double *__restrict__ part, int nb, double *__restrict__ small)
+{
+    __shared__ double sh[32];
+    double tot[7];
+    for (int c = 0; c < 7; c++) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) a += part[b * 8 + c];
+        tot[c] = block_sum(a, sh);
+    }
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 3; c++) {
+            const double num = tot[2 * c], den = tot[2 * c + 1];
+            small[2 + c] = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+        }
+        small[5] = tot[6];
+    }
+}
+
+// FP64 staging [15][ny][nx] (f0..f8, g0..g4, tau) <-> device state.
+template <int PREC>
+__global__ void import_kernel(const double *__restrict__ in, typename Store<PREC>::S *__restrict__ dist,
+                              typename Store<PREC>::TauS *__restrict__ tau, int nx, int ny,
+                              int64_t pitch, int64_t plane, int mask)
+{
+    using St = Store<PREC>;
+    using R = typename St::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= nx) return;
+    const int64_t k = (int64_t)y * pitch + x, q = (int64_t)y * nx + x, n = (int64_t)nx * ny;
+    if (mask & 1)
+        for (int i = 0; i < 9; i++) St::st(dist, i * plane + k, R(in[i * n + q]), R(rest_f(i)));
+    if (mask & 2)
+        for (int i = 0; i < 5; i++)
+            St::st(dist + 9 * plane, i * plane + k, R(in[(9 + i) * n + q]), R(rest_g(i)));
+    if (mask & 4) tau[k] = typename St::TauS(in[14 * n + q]);
+}
+
+template <int PREC>
+__global__ void export_kernel(double *__restrict__ out, const typename Store<PREC>::S *__restrict__ dist,
+                              const typename Store<PREC>::TauS *__restrict__ tau, int nx, int ny,
+                              int64_t pitch, int64_t plane)
+{
+    using St = Store<PREC>;
+    using R = typename St::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= nx) return;
+    const int64_t k = (int64_t)y * pitch + x, q = (int64_t)y * nx + x, n = (int64_t)nx * ny;
+    for (int i = 0; i < 9; i++) out[i * n + q] = double(St::ld(dist, i * plane + k, R(rest_f(i))));
+    for (int i = 0; i < 5; i++)
+        out[(9 + i) * n + q] = double(St::ld(dist + 9 * plane, i * plane + k, R(rest_g(i))));
+    out[14 * n + q] = double(tau[k]);
+}
+
+// ------------------------------------------------------------- launchers
+static dim3 node_grid(const lbm_ctx *c, int bx) { return dim3((c->nx + bx - 1) / bx, c->ny); }
+
+int residual_blocks(const lbm_ctx *c)
+{
+    const int64_t n = (int64_t)c->nx * c->ny;
+    int64_t nb = (n + 255) / 256;
+    if (nb > 152 * 8) nb = 152 * 8;
+    return (int)(nb < 1 ? 1 : nb);
+}
+
+template <int PREC>
+static cudaError_t init_t(lbm_ctx *c)
+{
+    using St = Store<PREC>;
+    for (int b = 0; b < 2; b++)
+        init_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
+            (typename St::S *)c->buf.dist[b], (typename St::TauS *)c->buf.tau[b],
+            make_params<typename St::R>(c), c->lat.tau0, 0.5 * (c->lat.T_hot + c->lat.T_cold));
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t step_t(lbm_ctx *c)
+{
+    using St = Store<PREC>;
+    const int s = c->cur, d = 1 - c->cur;
+    step_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
+        (const typename St::S *)c->buf.dist[s], (typename St::S *)c->buf.dist[d],
+        (const typename St::TauS *)c->buf.tau[s], (typename St::TauS *)c->buf.tau[d],
+        make_params<typename St::R>(c));
+    c->cur = d;
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t fields_t(lbm_ctx *c, double *out)
+{
+    using St = Store<PREC>;
+    fields_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
+        (const typename St::S *)c->buf.dist[c->cur], (const typename St::TauS *)c->buf.tau[c->cur],
+        make_params<typename St::R>(c), out);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t nusselt_t(lbm_ctx *c)
+{
+    using St = Store<PREC>;
+    nusselt_kernel<PREC><<<1, 256, 0, c->stream>>>(
+        (const typename St::S *)c->buf.dist[c->cur], make_params<typename St::R>(c), c->lat.T_hot,
+        c->lat.T_cold, c->lat.L, c->d_small, c->d_nuloc);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t residual_t(lbm_ctx *c, bool first)
+{
+    using St = Store<PREC>;
+    const int nb = residual_blocks(c);
+    residual_kernel<PREC><<<nb, 256, 0, c->stream>>>(
+        (const typename St::S *)c->buf.dist[c->cur], (const typename St::TauS *)c->buf.tau[c->cur],
+        make_params<typename St::R>(c), c->d_snap, c->d_part, first ? 1 : 0);
+    residual_final_kernel<<<1, 256, 0, c->stream>>>(c->d_part, nb, c->d_small);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t import_t(lbm_ctx *c, const double *in, int mask)
+{
+    using St = Store<PREC>;
+    import_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
+        in, (typename St::S *)c->buf.dist[c->cur], (typename St::TauS *)c->buf.tau[c->cur], c->nx, c->ny,
+        c->pitch, c->plane, mask);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t export_t(lbm_ctx *c, double *out)
+{
+    using St = Store<PREC>;
+    export_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
+        out, (const typename St::S *)c->buf.dist[c->cur], (const typename St::TauS *)c->buf.tau[c->cur],
+        c->nx, c->ny, c->pitch, c->plane);
+    return cudaGetLastError();
+}
+
+#define LBM_DISPATCH(fn, ...)                                      \
+    switch (c->opts.prec) {                                        \
+    case LBM_F64: return fn<LBM_F64>(__VA_ARGS__);                 \
+    case LBM_F32: return fn<LBM_F32>(__VA_ARGS__);                 \
+    case LBM_BF16D: return fn<LBM_BF16D>(__VA_ARGS__);             \
+    case LBM_F16D: return fn<LBM_F16D>(__VA_ARGS__);               \
+    default: return cudaErrorInvalidValue;                         \
+    }
+
+cudaError_t launch_init(lbm_ctx *c) { LBM_DISPATCH(init_t, c) }
+cudaError_t launch_step(lbm_ctx *c) { LBM_DISPATCH(step_t, c) }
+cudaError_t launch_fields(lbm_ctx *c, double *out) { LBM_DISPATCH(fields_t, c, out) }
+cudaError_t launch_nusselt(lbm_ctx *c) { LBM_DISPATCH(nusselt_t, c) }
+cudaError_t launch_residual(lbm_ctx *c, bool first) { LBM_DISPATCH(residual_t, c, first) }
+cudaError_t launch_import_f64(lbm_ctx *c, const double *in, int mask) { LBM_DISPATCH(import_t, c, in, mask) }
+cudaError_t launch_export_f64(lbm_ctx *c, double *out) { LBM_DISPATCH(export_t, c, out) }
+
+}  // namespace lbm

@@ -1,0 +1,279 @@
+"""Thin ctypes binding of ``include/lbm.h`` (argument marshalling only).
+
+Every function here has the name of the C call it wraps, without the
+``lbm_`` prefix.  All computation happens in ``libmrtlbm.so``; if the library
+is missing or cannot be loaded, :func:`lib` raises -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+F64, F32, BF16D, F16D = 0, 1, 2, 3
+PREC_NAMES = {"f64": F64, "f32": F32, "bf16d": BF16D, "f16d": F16D}
+STORE_DTYPE = {F64: np.float64, F32: np.float32, BF16D: np.uint16, F16D: np.float16}
+TAU_DTYPE = {F64: np.float64, F32: np.float32, BF16D: np.float32, F16D: np.float32}
+
+ERRORS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_UNSTABLE", -3: "LBM_ERR_NONFINITE",
+          -4: "LBM_ERR_CUDA", -5: "LBM_ERR_OOM", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_UNSUPPORTED"}
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = f"{what}: {ERRORS.get(code, code)}"
+        if code == -4 or code == -5:
+            msg += f" ({lib().lbm_last_cuda_error().decode()})"
+        super().__init__(msg)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("Ma", ctypes.c_double), ("clamp_mode", ctypes.c_int),
+                ("porous_model", ctypes.c_int), ("s_e", ctypes.c_double), ("s_p", ctypes.c_double),
+                ("resid_interval", ctypes.c_int), ("layout", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("n", ctypes.c_double),
+                ("nu_ref", ctypes.c_double), ("gamma_scale", ctypes.c_double),
+                ("gamma1", ctypes.c_double), ("gamma2", ctypes.c_double),
+                ("clamp_mode", ctypes.c_int), ("K", ctypes.c_double), ("eps", ctypes.c_double),
+                ("Feps", ctypes.c_double), ("gbeta", ctypes.c_double), ("Tm", ctypes.c_double),
+                ("tauT", ctypes.c_double), ("s_e", ctypes.c_double), ("s_p", ctypes.c_double),
+                ("T_hot", ctypes.c_double), ("T_cold", ctypes.c_double), ("L", ctypes.c_double),
+                ("tau0", ctypes.c_double), ("prec", ctypes.c_int), ("pitch", ctypes.c_int64)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/lbm.h
+SIGNATURES = [
+    ("lbm_default_opts", None, [ctypes.POINTER(Opts)]),
+    ("lbm_init", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.POINTER(Opts)]),
+    ("lbm_destroy", None, [_VP]),
+    ("lbm_get_lattice", ctypes.c_int, [_VP, ctypes.POINTER(Lattice)]),
+    ("lbm_step", ctypes.c_int, [_VP, ctypes.c_int64]),
+    ("lbm_synchronize", ctypes.c_int, [_VP]),
+    ("lbm_fields", ctypes.c_int, [_VP, _D, _D, _D, _D, _D]),
+    ("lbm_nusselt", ctypes.c_int, [_VP, _D, _D, _D]),
+    ("lbm_residual", ctypes.c_int, [_VP, _D]),
+    ("lbm_run_to_steady", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int64), _D,
+                                         ctypes.POINTER(ctypes.c_int)]),
+    ("lbm_state_bytes", ctypes.c_size_t, [_VP]),
+    ("lbm_get_state", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    ("lbm_set_state", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    ("lbm_get_state_f64", ctypes.c_int, [_VP, _D, _D, _D]),
+    ("lbm_set_state_f64", ctypes.c_int, [_VP, _D, _D, _D]),
+    ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("lbm_last_cuda_error", ctypes.c_char_p, []),
+]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load ``libmrtlbm.so`` (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not _build.up_to_date():
+                _build.build()
+            L = ctypes.CDLL(_build.LIB)
+            for name, res, args in SIGNATURES:
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise LBMError(rc, what)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)   # torch.cuda.Stream
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().lbm_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = PREC_NAMES[v]
+        if k == "cuda_stream":
+            v = _stream_handle(v)
+        setattr(o, k, v)
+    return o
+
+
+def init(nx, ny, n, Da, Ra, Pr, porosity=0.6, **opts):
+    """Create a cavity run; returns an opaque context handle (int)."""
+    h = _VP()
+    o = default_opts(**opts)
+    _check(lib().lbm_init(ctypes.byref(h), nx, ny, n, Da, Ra, Pr, porosity, ctypes.byref(o)), "lbm_init")
+    return h.value
+
+
+def destroy(ctx):
+    lib().lbm_destroy(ctx)
+
+
+def get_lattice(ctx) -> Lattice:
+    L = Lattice()
+    _check(lib().lbm_get_lattice(ctx, ctypes.byref(L)), "lbm_get_lattice")
+    return L
+
+
+def step(ctx, k: int):
+    _check(lib().lbm_step(ctx, int(k)), "lbm_step")
+
+
+def synchronize(ctx):
+    _check(lib().lbm_synchronize(ctx), "lbm_synchronize")
+
+
+def fields(ctx, nx, ny):
+    """Streamed fields as a dict of [ny][nx] float64 arrays (rho, ux, uy, T, nu)."""
+    out = {k: np.empty((ny, nx)) for k in ("rho", "ux", "uy", "T", "nu")}
+    _check(lib().lbm_fields(ctx, *[_ptr(out[k]) for k in ("rho", "ux", "uy", "T", "nu")]), "lbm_fields")
+    return out
+
+
+def nusselt(ctx, ny=None):
+    """(hot-wall average Nu, cold-wall average Nu, local hot-wall Nu or None)."""
+    h = ctypes.c_double(); c = ctypes.c_double()
+    loc = np.empty(ny) if ny else None
+    _check(lib().lbm_nusselt(ctx, ctypes.byref(h), ctypes.byref(c), _ptr(loc)), "lbm_nusselt")
+    return h.value, c.value, loc
+
+
+def residual(ctx) -> float:
+    r = ctypes.c_double()
+    _check(lib().lbm_residual(ctx, ctypes.byref(r)), "lbm_residual")
+    return r.value
+
+
+def run_to_steady(ctx, tol: float, max_steps: int):
+    """Returns (steps_done, residual, reason) with reason 0 tol, 1 stagnated, 2 max_steps."""
+    s = ctypes.c_int64(); r = ctypes.c_double(); why = ctypes.c_int()
+    _check(lib().lbm_run_to_steady(ctx, tol, int(max_steps), ctypes.byref(s), ctypes.byref(r),
+                                   ctypes.byref(why)), "lbm_run_to_steady")
+    return s.value, r.value, why.value
+
+
+def state_bytes(ctx) -> int:
+    return int(lib().lbm_state_bytes(ctx))
+
+
+def get_state(ctx, host):
+    """Copy the native state into ``host`` (numpy array or torch CPU tensor)."""
+    ptr = host.ctypes.data if isinstance(host, np.ndarray) else host.data_ptr()
+    nbytes = host.nbytes if isinstance(host, np.ndarray) else host.numel() * host.element_size()
+    _check(lib().lbm_get_state(ctx, ptr, nbytes), "lbm_get_state")
+
+
+def set_state(ctx, host):
+    ptr = host.ctypes.data if isinstance(host, np.ndarray) else host.data_ptr()
+    nbytes = host.nbytes if isinstance(host, np.ndarray) else host.numel() * host.element_size()
+    _check(lib().lbm_set_state(ctx, ptr, nbytes), "lbm_set_state")
+
+
+def get_state_f64(ctx, nx, ny):
+    f = np.empty((9, ny, nx)); g = np.empty((5, ny, nx)); tau = np.empty((ny, nx))
+    _check(lib().lbm_get_state_f64(ctx, _ptr(f), _ptr(g), _ptr(tau)), "lbm_get_state_f64")
+    return f, g, tau
+
+
+def set_state_f64(ctx, f=None, g=None, tau=None):
+    conv = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (f, g, tau)]
+    _check(lib().lbm_set_state_f64(ctx, *[_ptr(a) for a in conv]), "lbm_set_state_f64")
+
+
+def strerror(code: int) -> str:
+    return lib().lbm_strerror(code).decode()
+
+
+class Cavity:
+    """Owning wrapper of one context with the calls above as methods."""
+
+    def __init__(self, nx, ny, n, Da, Ra, Pr, porosity=0.6, **opts):
+        self.nx, self.ny = nx, ny
+        self.prec = PREC_NAMES.get(opts.get("prec"), opts.get("prec", F64))
+        self.ctx = init(nx, ny, n, Da, Ra, Pr, porosity, **opts)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def lattice(self):
+        return get_lattice(self.ctx)
+
+    def step(self, k):
+        step(self.ctx, k)
+
+    def synchronize(self):
+        synchronize(self.ctx)
+
+    def fields(self):
+        return fields(self.ctx, self.nx, self.ny)
+
+    def nusselt(self, local=False):
+        return nusselt(self.ctx, self.ny if local else None)
+
+    def residual(self):
+        return residual(self.ctx)
+
+    def run_to_steady(self, tol, max_steps):
+        return run_to_steady(self.ctx, tol, max_steps)
+
+    def get_state_f64(self):
+        return get_state_f64(self.ctx, self.nx, self.ny)
+
+    def set_state_f64(self, f=None, g=None, tau=None):
+        set_state_f64(self.ctx, f, g, tau)
+
+    def state_bytes(self):
+        return state_bytes(self.ctx)
+
+    def get_state(self, host):
+        get_state(self.ctx, host)
+
+    def set_state(self, host):
+        set_state(self.ctx, host)

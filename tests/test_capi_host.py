@@ -1,0 +1,97 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, it exports
+every entry point ``include/lbm.h`` declares, and argument validation rejects
+bad input before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names.update(re.findall(r"\b(lbm_\w+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2011_15073_gb300 import lbm
+    return lbm.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("lbm_init", "lbm_step", "lbm_fields", "lbm_nusselt", "lbm_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2011_15073_gb300 import lbm
+    bound = {name for name, _, _ in lbm.SIGNATURES}
+    assert set(declared_functions()) <= bound
+
+
+def test_default_opts(L):
+    from paper_2011_15073_gb300 import lbm
+    o = lbm.default_opts()
+    assert (o.prec, o.Ma, o.clamp_mode, o.porous_model, o.s_e, o.s_p, o.resid_interval, o.layout) == \
+        (0, 0.1, 0, 1, 1.5, 1.5, 1000, 0)
+    assert not o.cuda_stream and o.device == -1
+
+
+@pytest.mark.parametrize("args,code", [
+    ((1, 8, 0.6, 1e-2, 1e5, 6.2, 0.6), -1),      # nx < 2
+    ((8, 1, 0.6, 1e-2, 1e5, 6.2, 0.6), -1),      # ny < 2
+    ((8, 65536, 0.6, 1e-2, 1e5, 6.2, 0.6), -1),  # ny above the launch-grid limit
+    ((8, 8, 0.0, 1e-2, 1e5, 6.2, 0.6), -1),      # n <= 0
+    ((8, 8, 0.6, -1.0, 1e5, 6.2, 0.6), -1),      # Da <= 0
+    ((8, 8, 0.6, 1e-2, 0.0, 6.2, 0.6), -1),      # Ra <= 0
+    ((8, 8, 0.6, 1e-2, 1e5, float("nan"), 0.6), -1),
+    ((8, 8, 0.6, 1e-2, 1e5, 6.2, 1.5), -1),      # porosity > 1
+    ((8, 8, 0.6, 1e-2, 1e5, 6.2, 0.0), -1),      # porosity <= 0
+    ((8, 8, 1.0, 1e-2, 1e5, 1e-12, 0.6), -2),    # tau0 -> 1/2: unstable
+])
+def test_init_rejects_bad_arguments(L, args, code):
+    from paper_2011_15073_gb300 import lbm
+    h = ctypes.c_void_p(123)
+    o = lbm.default_opts()
+    rc = L.lbm_init(ctypes.byref(h), *args, ctypes.byref(o))
+    assert rc == code and h.value is None
+
+
+@pytest.mark.parametrize("field,value,code", [
+    ("prec", 7, -1), ("Ma", 0.0, -1), ("clamp_mode", 2, -1), ("porous_model", 3, -1),
+    ("s_e", 2.5, -1), ("s_p", 0.0, -1), ("resid_interval", 0, -1), ("layout", 1, -7),
+    ("device", -2, -1),
+])
+def test_init_rejects_bad_options(L, field, value, code):
+    from paper_2011_15073_gb300 import lbm
+    h = ctypes.c_void_p()
+    o = lbm.default_opts()
+    setattr(o, field, value)
+    assert L.lbm_init(ctypes.byref(h), 8, 8, 0.6, 1e-2, 1e5, 6.2, 0.6, ctypes.byref(o)) == code
+
+
+def test_null_context_is_rejected(L):
+    assert L.lbm_step(None, 1) == -1
+    assert L.lbm_nusselt(None, None, None, None) == -1
+    assert L.lbm_state_bytes(None) == 0
+    L.lbm_destroy(None)
+
+
+def test_strerror_names_codes(L):
+    from paper_2011_15073_gb300 import lbm
+    for code, name in lbm.ERRORS.items():
+        assert lbm.strerror(code).startswith(name)

@@ -1,0 +1,300 @@
+"""GPU parity: the CUDA library against the FP64 oracle on the same seeded inputs.
+
+Tolerances (element by element):
+* FP64 storage and arithmetic: relative 1e-12 on f, g, tau after 100 steps and
+  1e-10 on the average Nusselt number (the stated FP64 bar).  Both sides
+  compute the same real-number expression in a different order, so the gap
+  is a few ulps per step and does not grow in a dissipative scheme.
+* FP32 storage and arithmetic: the input is rounded to FP32 before either side
+  sees it.  Each step rounds every population once on store and about ten
+  times in the arithmetic (unit roundoff 6e-8), so after 100 steps the
+  population error is bounded by 100 x 10 x 6e-8 = 6e-5 relative in the
+  worst (all-aligned) case; the test uses 5e-5 relative to the population
+  scale (rest weight) -- observed errors are far smaller.  The wall Nusselt
+  number amplifies the temperature error by about 3 L (a one-sided
+  difference times L), so Nu gets 1e-4 relative.
+* 16-bit deviation storage (FP32 arithmetic): each store rounds the deviation
+  f - w_i to 8 (BF16) or 11 (FP16) significant bits; with deviations below
+  ~1e-2 w_i the per-step error is below 1e-2 x 2^-8 ~ 4e-5 (BF16) and
+  5e-6 (FP16) of w_i; after 100 steps (no more than linear growth) the test
+  allows 4e-3 (BF16) and 5e-4 (FP16) of the rest weight.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    # sweep corner of the paper's abstract: shear-thinning, porous, high Ra
+    "thinning": dict(n=0.6, Da=1e-2, Ra=1e5, Pr=6.2, porosity=0.6, porous_model=1, clamp_mode=0),
+    # the plain Newtonian cavity at low Ra, porosity 0.6, Pr 10
+    "newtonian": dict(n=1.0, Da=1e-1, Ra=1e3, Pr=10.0, porosity=0.6, porous_model=1, clamp_mode=0),
+    # the paper's own Darcy model, continuous clamp
+    "darcy": dict(n=0.8, Da=1e-3, Ra=1e4, Pr=6.2, porosity=1.0, porous_model=0, clamp_mode=1),
+    # shear-thickening case of the paper's tables
+    "thickening": dict(n=1.4, Da=1e-3, Ra=1e5, Pr=6.2, porosity=0.6, porous_model=1, clamp_mode=0),
+}
+SIZES = [(8, 8), (17, 13), (64, 64), (130, 67), (2, 2), (3, 70)]
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import oracle
+    from paper_2011_15073_gb300 import inputs, lbm
+    oracle.build()
+    lbm.lib()
+    return oracle, inputs, lbm
+
+
+def oracle_for(oracle, nx, ny, c):
+    return oracle.Cavity.from_params(nx, ny, c["n"], c["Da"], c["Ra"], c["Pr"], porosity=c["porosity"],
+                                     porous_model=c["porous_model"], clamp_mode=c["clamp_mode"])
+
+
+def gpu_for(lbm, nx, ny, c, prec):
+    return lbm.Cavity(nx, ny, c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec=prec,
+                      porous_model=c["porous_model"], clamp_mode=c["clamp_mode"])
+
+
+def rel_err(a, b, scale):
+    return float(np.max(np.abs(a - b) / scale))
+
+
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+W5 = np.array([1 / 3] + [1 / 6] * 4)[:, None, None]
+
+
+def test_lattice_mapping_matches_oracle(mods):
+    oracle, _, lbm = mods
+    for c in CASES.values():
+        ref = oracle_for(oracle, 64, 48, c).lat
+        with gpu_for(lbm, 64, 48, c, "f64") as cav:
+            L = cav.lattice()
+        for k in ("nu_ref", "gamma_scale", "gamma1", "gamma2", "K", "eps", "Feps", "gbeta", "Tm",
+                  "tauT", "s_e", "s_p", "T_hot", "T_cold", "L", "tau0", "n"):
+            a, b = getattr(L, k), getattr(ref, k)
+            assert a == pytest.approx(b, rel=1e-15, abs=0), k
+        assert L.clamp_mode == ref.clamp_mode
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16d", "f16d"])
+def test_initial_state_is_rest_state(mods, prec):
+    oracle, _, lbm = mods
+    c = CASES["thinning"]
+    f0, g0, t0 = oracle_for(oracle, 17, 13, c).get_state()
+    with gpu_for(lbm, 17, 13, c, prec) as cav:
+        f, g, tau = cav.get_state_f64()
+    tol = 0 if prec == "f64" else 1e-7
+    assert rel_err(f, f0, W9) <= tol and rel_err(g, g0, W5) <= tol
+    assert np.max(np.abs(tau - t0) / t0) <= tol
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("size", SIZES, ids=lambda s: f"{s[0]}x{s[1]}")
+def test_fp64_step_parity(mods, case, size):
+    oracle, inputs, lbm = mods
+    nx, ny = size
+    c = CASES[case]
+    ref = oracle_for(oracle, nx, ny, c)
+    state = inputs.perturbed_state(ref.get_state(), seed=nx * 1000 + ny)
+    ref.set_state(*state)
+    ref.step(100)
+    f_r, g_r, t_r = ref.get_state()
+    with gpu_for(lbm, nx, ny, c, "f64") as cav:
+        cav.set_state_f64(*state)
+        cav.step(100)
+        f, g, tau = cav.get_state_f64()
+        hot, cold, loc = cav.nusselt(local=True)
+        fl = cav.fields()
+    assert np.max(np.abs(f - f_r) / np.abs(f_r)) < 1e-12
+    assert np.max(np.abs(g - g_r) / np.abs(g_r)) < 1e-12
+    assert np.max(np.abs(tau - t_r) / t_r) < 1e-12
+    h_r, c_r, loc_r = ref.nusselt()
+    assert abs(hot - h_r) <= 1e-10 * abs(h_r) and abs(cold - c_r) <= 1e-10 * abs(c_r)
+    assert np.max(np.abs(loc - loc_r)) <= 1e-10 * np.max(np.abs(loc_r))
+    fr = ref.fields()
+    for k in ("rho", "T", "nu"):
+        assert np.max(np.abs(fl[k] - fr[k]) / np.abs(fr[k])) < 1e-12, k
+    for k in ("ux", "uy"):
+        assert np.max(np.abs(fl[k] - fr[k])) <= 1e-12 * max(np.max(np.abs(fr[k])), 1e-300), k
+
+
+def test_fp64_parity_covers_both_clamp_branches(mods):
+    """The thinning case at 64x64 must see nodes on both sides of gamma_1,
+    otherwise the parity above would not exercise the literal clamp."""
+    oracle, inputs, _ = mods
+    c = CASES["thinning"]
+    ref = oracle_for(oracle, 64, 64, c)
+    ref.set_state(*inputs.perturbed_state(ref.get_state(), seed=64 * 1000 + 64))
+    seen_low = seen_high = False
+    for _ in range(10):
+        ref.step(10)
+        gs = ref.fields()["gamma"] * ref.lat.gamma_scale
+        seen_low |= bool((gs < ref.lat.gamma1).any())
+        seen_high |= bool((gs >= ref.lat.gamma1).any())
+    assert seen_low and seen_high
+
+
+@pytest.mark.parametrize("case", ["thinning", "darcy", "thickening"])
+@pytest.mark.parametrize("size", [(17, 13), (130, 67)], ids=lambda s: f"{s[0]}x{s[1]}")
+def test_fp32_step_parity(mods, case, size):
+    oracle, inputs, lbm = mods
+    nx, ny = size
+    c = CASES[case]
+    ref = oracle_for(oracle, nx, ny, c)
+    state = [a.astype(np.float32).astype(np.float64) for a in
+             inputs.perturbed_state(ref.get_state(), seed=7 + nx)]
+    ref.set_state(*state)
+    ref.step(100)
+    f_r, g_r, t_r = ref.get_state()
+    with gpu_for(lbm, nx, ny, c, "f32") as cav:
+        cav.set_state_f64(*state)
+        cav.step(100)
+        f, g, tau = cav.get_state_f64()
+        hot = cav.nusselt()[0]
+    assert rel_err(f, f_r, W9) < 5e-5
+    assert rel_err(g, g_r, W5) < 5e-5
+    assert np.max(np.abs(tau - t_r) / t_r) < 5e-5
+    h_r = ref.nusselt()[0]
+    assert abs(hot - h_r) <= 1e-4 * abs(h_r)
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16d", 4e-3), ("f16d", 5e-4)])
+def test_deviation_storage_parity(mods, prec, tol):
+    oracle, inputs, lbm = mods
+    nx, ny = 130, 67
+    c = CASES["thinning"]
+    ref = oracle_for(oracle, nx, ny, c)
+    state = inputs.perturbed_state(ref.get_state(), seed=11)
+    ref.set_state(*state)
+    ref.step(100)
+    f_r, g_r, t_r = ref.get_state()
+    with gpu_for(lbm, nx, ny, c, prec) as cav:
+        cav.set_state_f64(*state)
+        cav.step(100)
+        f, g, tau = cav.get_state_f64()
+    assert rel_err(f, f_r, W9) < tol
+    assert rel_err(g, g_r, W5) < tol
+    assert np.max(np.abs(tau - t_r) / t_r) < 10 * tol
+
+
+def test_zero_steps_and_repeat_calls(mods):
+    oracle, inputs, lbm = mods
+    c = CASES["thinning"]
+    ref = oracle_for(oracle, 17, 13, c)
+    state = inputs.perturbed_state(ref.get_state(), seed=5)
+    with gpu_for(lbm, 17, 13, c, "f64") as cav:
+        cav.set_state_f64(*state)
+        cav.step(0)
+        f, g, tau = cav.get_state_f64()
+        assert np.array_equal(f, state[0]) and np.array_equal(g, state[1])
+        cav.step(3)
+        cav.step(4)
+        a = cav.get_state_f64()
+    ref.set_state(*state)
+    ref.step(7)
+    b = ref.get_state()
+    for x, y in zip(a, b):
+        assert np.max(np.abs(x - y) / np.abs(y)) < 1e-13
+
+
+def test_native_state_roundtrip(mods):
+    _, inputs, lbm = mods
+    c = CASES["thinning"]
+    for prec in ("f64", "f32", "bf16d", "f16d"):
+        with gpu_for(lbm, 33, 21, c, prec) as cav:
+            cav.step(5)
+            buf = np.empty(cav.state_bytes(), dtype=np.uint8)
+            cav.get_state(buf)
+            cav.step(5)
+            after = np.empty_like(buf)
+            cav.get_state(after)
+            cav.set_state(buf)
+            cav.step(5)
+            again = np.empty_like(buf)
+            cav.get_state(again)
+            assert np.array_equal(after, again), prec
+
+
+def test_residual_matches_definition(mods):
+    oracle, inputs, lbm = mods
+    c = CASES["thinning"]
+    nx, ny = 40, 30
+    ref = oracle_for(oracle, nx, ny, c)
+    state = inputs.perturbed_state(ref.get_state(), seed=9)
+    ref.set_state(*state)
+    with gpu_for(lbm, nx, ny, c, "f64") as cav:
+        cav.set_state_f64(*state)
+        assert math.isinf(cav.residual())
+        cav.step(50)
+        r = cav.residual()
+    a = ref.fields()
+    ref.step(50)
+    b = ref.fields()
+    expect = max(np.linalg.norm(b[k] - a[k]) / np.linalg.norm(b[k]) for k in ("ux", "uy", "T"))
+    assert r == pytest.approx(expect, rel=1e-9)
+
+
+def test_nonfinite_state_is_reported(mods):
+    oracle, inputs, lbm = mods
+    c = CASES["thinning"]
+    ref = oracle_for(oracle, 16, 16, c)
+    f, g, tau = ref.get_state()
+    f = f.copy()
+    f[3, 7, 9] = np.nan
+    with gpu_for(lbm, 16, 16, c, "f32") as cav:
+        cav.set_state_f64(f, g, tau)
+        with pytest.raises(lbm.LBMError) as e:
+            cav.residual()
+        assert e.value.code == -3
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_full_size_sampled_parity(mods, prec):
+    """4096 x 4096, the benchmark's launch configuration: the state after k
+    steps at a node depends only on the (2k+1)^2 nodes around it, so the
+    oracle recomputes sampled nodes one window at a time.  A window that
+    touches a real wall keeps it; its artificial edges stay more than k nodes
+    away from the sampled node."""
+    oracle, inputs, lbm = mods
+    N, k, h = 4096, 3, 5
+    c = CASES["thinning"]
+    dt = np.float64 if prec == "f64" else np.float32
+    lat_full = oracle.map_params(N, N, c["n"], c["Da"], c["Ra"], c["Pr"], porosity=c["porosity"])
+    rest = oracle.Cavity(oracle.map_params(4, 4, 1.0, 1e-2, 1e5, 6.2))
+    f0, g0, t0 = rest.get_state()
+    rng = np.random.default_rng(4096)
+    f = (f0[:, :1, :1] * (1 + rng.uniform(-1e-3, 1e-3, (9, N, N)))).astype(dt)
+    g = (g0[:, :1, :1] * (1 + rng.uniform(-1e-3, 1e-3, (5, N, N)))).astype(dt)
+    tau = np.full((N, N), lat_full.tau0, dtype=dt)
+    with gpu_for(lbm, N, N, c, prec) as cav:
+        host = np.concatenate([f.reshape(-1), g.reshape(-1), tau.reshape(-1)])
+        cav.set_state(host.view(np.uint8))
+        cav.step(k)
+        out = np.empty_like(host)
+        cav.get_state(out.view(np.uint8))
+    nn = N * N
+    fo = out[:9 * nn].reshape(9, N, N)
+    go = out[9 * nn:14 * nn].reshape(5, N, N)
+    to = out[14 * nn:].reshape(N, N)
+    samples = [(0, 0), (N - 1, 0), (0, N - 1), (N - 1, N - 1), (N // 2, 0), (0, N // 2),
+               (N - 1, N // 2), (N // 2, N - 1)] + [tuple(rng.integers(0, N, 2)) for _ in range(24)]
+    tol = 1e-12 if prec == "f64" else 2e-6
+    for (x, y) in samples:
+        x0 = 0 if x < h + k else (N - (2 * h + 1) if x > N - 1 - h - k else x - h)
+        y0 = 0 if y < h + k else (N - (2 * h + 1) if y > N - 1 - h - k else y - h)
+        w = 2 * h + 1
+        lat = lat_full.copy()
+        lat.nx = lat.ny = w
+        win = oracle.Cavity(lat)
+        win.set_state(f[:, y0:y0 + w, x0:x0 + w].astype(np.float64),
+                      g[:, y0:y0 + w, x0:x0 + w].astype(np.float64),
+                      tau[y0:y0 + w, x0:x0 + w].astype(np.float64))
+        win.step(k)
+        fw, gw, tw = win.get_state()
+        lx, ly = x - x0, y - y0
+        assert np.max(np.abs(fo[:, y, x] - fw[:, ly, lx]) / W9[:, 0, 0]) < tol, (x, y)
+        assert np.max(np.abs(go[:, y, x] - gw[:, ly, lx]) / W5[:, 0, 0]) < tol, (x, y)
+        assert abs(to[y, x] - tw[ly, lx]) / tw[ly, lx] < tol, (x, y)
