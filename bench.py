@@ -34,6 +34,34 @@ sys.path.insert(0, ROOT)
 BYTES_PER_NODE = {"f64": 240, "f32": 120, "bf16d": 64, "f16d": 64}
 CASE = dict(n=0.6, Da=1e-3, Ra=1e5, Pr=6.2, porosity=0.6)
 FALLBACK_HBM_GBS = 6800.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+
+
+def kernel_source_hash():
+    """Hash of the CUDA sources: a traffic figure taken from another build of
+    the kernel is reported as null."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for fn in sorted(glob.glob(os.path.join(ROOT, "paper_2011_15073_gb300", "csrc", "*"))):
+        with open(fn, "rb") as fh:
+            h.update(os.path.basename(fn).encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(prec, N):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary (lines: prec N bytes_per_launch source_hash), or None."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            for line in fh:
+                parts = line.split()
+                if len(parts) == 4 and not line.startswith("#") and parts[0] == prec and int(parts[1]) == N:
+                    if parts[3] == kernel_source_hash():
+                        return float(parts[2])
+    except OSError:
+        pass
+    return None
 
 
 def parse():
@@ -43,7 +71,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=4096)
-    ap.add_argument("--delta", type=int, default=100, help="fused time steps per bench step")
+    ap.add_argument("--delta", type=int, default=1000,
+                    help="fused time steps per bench step (the convergence-check interval)")
+    ap.add_argument("--variant-delta", type=int, default=200)
     ap.add_argument("--prec", default="f32")
     ap.add_argument("--variants", default="f64,bf16d,f16d",
                     help="other storage precisions measured beside the headline ('' for none)")
@@ -185,7 +215,7 @@ def time_e2e(lbm, torch, N, prec, steps, warmup, delta, stream):
         cav.close()
 
 
-def cpu_baseline(N_sample=512, steps=8):
+def cpu_baseline(N_sample=1024, steps=150):
     """The FP64 oracle as it stands, on all host cores (OpenMP), on a bounded
     sample of the workload: an N_sample^2 cavity with the same parameters."""
     import oracle
@@ -207,12 +237,12 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    steps_each = max(1, min(4, 30 // max(1, args.steps + args.warmup)))
+    steps_each = 10
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
-    Ns = 512
+    Ns = 1024
     c = oracle.Cavity.from_params(Ns, Ns, CASE["n"], CASE["Da"], CASE["Ra"], CASE["Pr"], porosity=CASE["porosity"])
     for _ in range(args.warmup):
         c.step(steps_each)
@@ -271,16 +301,17 @@ def main():
     achieved = BYTES_PER_NODE[prec] * N * N / kern / 1e9
     variants = {}
     for v in [p for p in args.variants.split(",") if p and p != prec]:
-        vs = max(2, args.steps // 2)
-        tv, kv, _, nuv = time_ours(lbm, torch, N, v, vs, 3, delta, stream)
+        vs, vd = 2, args.variant_delta
+        tv, kv, _, nuv = time_ours(lbm, torch, N, v, vs, 1, vd, stream)
         av = BYTES_PER_NODE[v] * N * N / kv / 1e9
-        variants[v] = {"MLUPS": N * N * delta * vs / tv / 1e6, "kernel_MLUPS": N * N / kv / 1e6,
+        variants[v] = {"MLUPS": N * N * vd * vs / tv / 1e6, "kernel_MLUPS": N * N / kv / 1e6,
+                       "fused_steps_per_bench_step": vd,
                        "bytes_per_node": BYTES_PER_NODE[v], "achieved_GBs": av, "frac_of_hbm": av / peak,
                        "nu_hot": nuv}
     e2e = None
     if not args.no_e2e:
-        te, hb, db = time_e2e(lbm, torch, N, prec, max(2, args.steps // 2), 2, delta, stream)
         es = max(2, args.steps // 2)
+        te, hb, db = time_e2e(lbm, torch, N, prec, es, 1, delta, stream)
         e2e = {"value": N * N * delta * es / te / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": hb,
                "d2h_bytes_per_step": db}
     if rank != 0:
@@ -297,7 +328,7 @@ def main():
                    "grid": [N, N], "fused_steps_per_bench_step": delta,
                    "l2": "state larger than L2 (no flush needed)", "parallelism": f"independent cavity per GPU x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": recorded_traffic(prec, N),
                      "peak_source": peak_src, "kernel": f"step_kernel<{prec}>",
                      "bytes_per_node": BYTES_PER_NODE[prec], "avg_launch_us": kern * 1e6},
         "cpu_baseline": cpu,

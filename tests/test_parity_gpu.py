@@ -1,8 +1,8 @@
 """GPU parity: the CUDA library against the FP64 oracle on the same seeded inputs.
 
 Tolerances (element by element):
-* FP64 storage and arithmetic: relative 1e-12 on f, g, tau after 100 steps and
-  1e-10 on the average Nusselt number (the stated FP64 bar).  Both sides
+* FP64 storage and arithmetic: relative 1e-12 on f and g after 100 steps and
+  1e-10 on the average Nusselt number (the stated FP64 bar); tau below.  Both sides
   compute the same real-number expression in a different order, so the gap
   is a few ulps per step and does not grow in a dissipative scheme.
 * FP32 storage and arithmetic: the input is rounded to FP32 before either side
@@ -18,11 +18,19 @@ Tolerances (element by element):
   ~1e-2 w_i the per-step error is below 1e-2 x 2^-8 ~ 4e-5 (BF16) and
   5e-6 (FP16) of w_i; after 100 steps (no more than linear growth) the test
   allows 4e-3 (BF16) and 5e-4 (FP16) of the rest weight.
+* The relaxation time tau and the apparent viscosity are not populations:
+  they come from the strain rate, a small difference of O(1) moments, through
+  the modified power law, whose literal form jumps at gamma_1.  They are
+  checked node by node with ``parity_util.check_tau``: unique (to the
+  propagated strain-rate error) where the oracle's strain rate is resolved,
+  and otherwise the law's value at a strain rate within the error band.
 """
 import math
 
 import numpy as np
 import pytest
+
+from parity_util import check_tau
 
 pytestmark = pytest.mark.gpu
 
@@ -100,23 +108,31 @@ def test_fp64_step_parity(mods, case, size):
     ref = oracle_for(oracle, nx, ny, c)
     state = inputs.perturbed_state(ref.get_state(), seed=nx * 1000 + ny)
     ref.set_state(*state)
-    ref.step(100)
+    ref.step(99)
+    f99_r, g99_r, _ = ref.get_state()
+    gam_r = ref.fields()["gamma"]
+    ref.step(1)
     f_r, g_r, t_r = ref.get_state()
     with gpu_for(lbm, nx, ny, c, "f64") as cav:
         cav.set_state_f64(*state)
-        cav.step(100)
+        cav.step(99)
+        f99, g99, _ = cav.get_state_f64()
+        cav.step(1)
         f, g, tau = cav.get_state_f64()
         hot, cold, loc = cav.nusselt(local=True)
         fl = cav.fields()
     assert np.max(np.abs(f - f_r) / np.abs(f_r)) < 1e-12
     assert np.max(np.abs(g - g_r) / np.abs(g_r)) < 1e-12
-    assert np.max(np.abs(tau - t_r) / t_r) < 1e-12
+    df = max(np.abs(f99 - f99_r).max(), np.abs(g99 - g99_r).max())
+    check_tau(tau, t_r, gam_r, ref.lat, "f64", df)
     h_r, c_r, loc_r = ref.nusselt()
     assert abs(hot - h_r) <= 1e-10 * abs(h_r) and abs(cold - c_r) <= 1e-10 * abs(c_r)
     assert np.max(np.abs(loc - loc_r)) <= 1e-10 * np.max(np.abs(loc_r))
     fr = ref.fields()
-    for k in ("rho", "T", "nu"):
+    for k in ("rho", "T"):
         assert np.max(np.abs(fl[k] - fr[k]) / np.abs(fr[k])) < 1e-12, k
+    df = max(np.abs(f - f_r).max(), np.abs(g - g_r).max())
+    check_tau(3 * fl["nu"] + 0.5, 3 * fr["nu"] + 0.5, fr["gamma"], ref.lat, "f64", df)
     for k in ("ux", "uy"):
         assert np.max(np.abs(fl[k] - fr[k])) <= 1e-12 * max(np.max(np.abs(fr[k])), 1e-300), k
 
@@ -147,16 +163,22 @@ def test_fp32_step_parity(mods, case, size):
     state = [a.astype(np.float32).astype(np.float64) for a in
              inputs.perturbed_state(ref.get_state(), seed=7 + nx)]
     ref.set_state(*state)
-    ref.step(100)
+    ref.step(99)
+    f99_r, g99_r, _ = ref.get_state()
+    gam_r = ref.fields()["gamma"]
+    ref.step(1)
     f_r, g_r, t_r = ref.get_state()
     with gpu_for(lbm, nx, ny, c, "f32") as cav:
         cav.set_state_f64(*state)
-        cav.step(100)
+        cav.step(99)
+        f99, g99, _ = cav.get_state_f64()
+        cav.step(1)
         f, g, tau = cav.get_state_f64()
         hot = cav.nusselt()[0]
     assert rel_err(f, f_r, W9) < 5e-5
     assert rel_err(g, g_r, W5) < 5e-5
-    assert np.max(np.abs(tau - t_r) / t_r) < 5e-5
+    df = max(np.abs(f99 - f99_r).max(), np.abs(g99 - g99_r).max())
+    check_tau(tau, t_r, gam_r, ref.lat, "f32", df)
     h_r = ref.nusselt()[0]
     assert abs(hot - h_r) <= 1e-4 * abs(h_r)
 
@@ -169,15 +191,21 @@ def test_deviation_storage_parity(mods, prec, tol):
     ref = oracle_for(oracle, nx, ny, c)
     state = inputs.perturbed_state(ref.get_state(), seed=11)
     ref.set_state(*state)
-    ref.step(100)
+    ref.step(99)
+    f99_r, g99_r, _ = ref.get_state()
+    gam_r = ref.fields()["gamma"]
+    ref.step(1)
     f_r, g_r, t_r = ref.get_state()
     with gpu_for(lbm, nx, ny, c, prec) as cav:
         cav.set_state_f64(*state)
-        cav.step(100)
+        cav.step(99)
+        f99, g99, _ = cav.get_state_f64()
+        cav.step(1)
         f, g, tau = cav.get_state_f64()
     assert rel_err(f, f_r, W9) < tol
     assert rel_err(g, g_r, W5) < tol
-    assert np.max(np.abs(tau - t_r) / t_r) < 10 * tol
+    df = max(np.abs(f99 - f99_r).max(), np.abs(g99 - g99_r).max())
+    check_tau(tau, t_r, gam_r, ref.lat, prec, df)
 
 
 def test_zero_steps_and_repeat_calls(mods):
@@ -196,8 +224,9 @@ def test_zero_steps_and_repeat_calls(mods):
     ref.set_state(*state)
     ref.step(7)
     b = ref.get_state()
-    for x, y in zip(a, b):
+    for x, y in zip(a[:2], b[:2]):
         assert np.max(np.abs(x - y) / np.abs(y)) < 1e-13
+    assert np.max(np.abs(a[2] - b[2]) / b[2]) < 1e-10   # tau: see check_tau
 
 
 def test_native_state_roundtrip(mods):
@@ -292,9 +321,12 @@ def test_full_size_sampled_parity(mods, prec):
         win.set_state(f[:, y0:y0 + w, x0:x0 + w].astype(np.float64),
                       g[:, y0:y0 + w, x0:x0 + w].astype(np.float64),
                       tau[y0:y0 + w, x0:x0 + w].astype(np.float64))
-        win.step(k)
+        win.step(k - 1)
+        gam_w = win.fields()["gamma"]
+        win.step(1)
         fw, gw, tw = win.get_state()
         lx, ly = x - x0, y - y0
         assert np.max(np.abs(fo[:, y, x] - fw[:, ly, lx]) / W9[:, 0, 0]) < tol, (x, y)
         assert np.max(np.abs(go[:, y, x] - gw[:, ly, lx]) / W5[:, 0, 0]) < tol, (x, y)
-        assert abs(to[y, x] - tw[ly, lx]) / tw[ly, lx] < tol, (x, y)
+        df = max(np.max(np.abs(fo[:, y, x] - fw[:, ly, lx])), np.max(np.abs(go[:, y, x] - gw[:, ly, lx])))
+        check_tau(np.array([to[y, x]], float), tw[ly, lx:lx + 1], gam_w[ly, lx:lx + 1], lat, prec, df)
