@@ -10,6 +10,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <math.h>
 #include <stdint.h>
 
 #include "lbm_internal.h"
@@ -17,7 +18,7 @@
 namespace lbm {
 
 // Per-case constants in the compute type R (built on the host from
-// lbm_lattice; see make_params in lbm_capi.cu).
+// lbm_lattice by make_params below).
 template <class R>
 struct Phys {
     int nx, ny;
@@ -34,6 +35,39 @@ struct Phys {
     R omegaT, s_e, s_p;
     R abb_hot, abb_cold;   // 2 w T_wall for the anti-bounce-back (w = 1/6)
 };
+
+// ------------------------------------------------------------ parameters
+template <class R>
+inline Phys<R> make_params(const lbm_ctx *c)
+{
+    const lbm_lattice &L = c->lat;
+    Phys<R> p;
+    p.nx = c->nx;
+    p.ny = c->ny;
+    p.pitch = c->pitch;
+    p.plane = c->plane;
+    p.nu_ref = R(L.nu_ref);
+    p.gamma_scale = R(L.gamma_scale);
+    p.gamma1 = R(L.gamma1);
+    p.gamma2 = R(L.gamma2);
+    p.nm1 = R(L.n - 1.0);
+    p.D_hi = R(pow(L.gamma2, L.n - 1.0));
+    p.clamp_mode = L.clamp_mode;
+    p.eps = R(L.eps);
+    p.inv_eps = R(1.0 / L.eps);
+    p.half_eps_invK = R(L.eps / (4.0 * L.K));
+    p.eps_invK = R(L.eps / L.K);
+    p.c1 = R(L.eps * L.Feps / (2.0 * sqrt(L.K)));
+    p.eFe_isqK = R(L.eps * L.Feps / sqrt(L.K));
+    p.gbeta = R(L.gbeta);
+    p.Tm = R(L.Tm);
+    p.omegaT = R(1.0 / L.tauT);
+    p.s_e = R(L.s_e);
+    p.s_p = R(L.s_p);
+    p.abb_hot = R(2.0 / 6.0 * L.T_hot);
+    p.abb_cold = R(2.0 / 6.0 * L.T_cold);
+    return p;
+}
 
 // Rest-state values used by the deviation storage forms.
 __host__ __device__ constexpr double rest_f(int i)
@@ -93,13 +127,6 @@ struct Store<LBM_F16D> {
         p[k] = __float2half_rn(v - rest);
     }
 };
-
-template <class R>
-__device__ __forceinline__ R rsqrt_(R x);
-template <>
-__device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
-template <>
-__device__ __forceinline__ float rsqrt_(float x) { return 1.0f / sqrtf(x); }
 
 // D = (gamma*)^(n-1) in the compute precision.
 __device__ __forceinline__ double powD(double x, double e) { return pow(x, e); }

@@ -7,39 +7,6 @@
 
 namespace lbm {
 
-// ------------------------------------------------------------ parameters
-template <class R>
-static Phys<R> make_params(const lbm_ctx *c)
-{
-    const lbm_lattice &L = c->lat;
-    Phys<R> p;
-    p.nx = c->nx;
-    p.ny = c->ny;
-    p.pitch = c->pitch;
-    p.plane = c->plane;
-    p.nu_ref = R(L.nu_ref);
-    p.gamma_scale = R(L.gamma_scale);
-    p.gamma1 = R(L.gamma1);
-    p.gamma2 = R(L.gamma2);
-    p.nm1 = R(L.n - 1.0);
-    p.D_hi = R(pow(L.gamma2, L.n - 1.0));
-    p.clamp_mode = L.clamp_mode;
-    p.eps = R(L.eps);
-    p.inv_eps = R(1.0 / L.eps);
-    p.half_eps_invK = R(L.eps / (4.0 * L.K));
-    p.eps_invK = R(L.eps / L.K);
-    p.c1 = R(L.eps * L.Feps / (2.0 * sqrt(L.K)));
-    p.eFe_isqK = R(L.eps * L.Feps / sqrt(L.K));
-    p.gbeta = R(L.gbeta);
-    p.Tm = R(L.Tm);
-    p.omegaT = R(1.0 / L.tauT);
-    p.s_e = R(L.s_e);
-    p.s_p = R(L.s_p);
-    p.abb_hot = R(2.0 / 6.0 * L.T_hot);
-    p.abb_cold = R(2.0 / 6.0 * L.T_cold);
-    return p;
-}
-
 // ---------------------------------------------------------------- kernels
 template <int PREC>
 __global__ void init_kernel(typename Store<PREC>::S *__restrict__ dist,

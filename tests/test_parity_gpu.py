@@ -133,8 +133,11 @@ def test_fp64_step_parity(mods, case, size):
         assert np.max(np.abs(fl[k] - fr[k]) / np.abs(fr[k])) < 1e-12, k
     df = max(np.abs(f - f_r).max(), np.abs(g - g_r).max())
     check_tau(3 * fl["nu"] + 0.5, 3 * fr["nu"] + 0.5, fr["gamma"], ref.lat, "f64", df)
+    # u = sum f e / rho + ...: a sum of O(0.1) populations that nearly cancel,
+    # so its error is absolute: six populations within 1e-12 relative give
+    # |du| <= 6 x 1e-12 x 0.11 < 1e-12 (lattice units; U_c = 0.058).
     for k in ("ux", "uy"):
-        assert np.max(np.abs(fl[k] - fr[k])) <= 1e-12 * max(np.max(np.abs(fr[k])), 1e-300), k
+        assert np.max(np.abs(fl[k] - fr[k])) <= 1e-12, k
 
 
 def test_fp64_parity_covers_both_clamp_branches(mods):
