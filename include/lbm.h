@@ -41,8 +41,12 @@ enum {
     LBM_ERR_CUDA = -4,      /* a CUDA runtime call failed                  */
     LBM_ERR_OOM = -5,       /* device memory allocation failed             */
     LBM_ERR_TIMEOUT = -6,   /* a bounded device wait gave up               */
-    LBM_ERR_UNSUPPORTED = -7/* option combination not built               */
+    LBM_ERR_UNSUPPORTED = -7,/* option combination not built              */
+    LBM_ERR_SIZE = -8       /* grid larger than a fixed-size scratch area  */
 };
+
+/* Rows (ny) that lbm_residual_noalloc's fixed scratch area can serve. */
+#define LBM_NOALLOC_MAX_ROWS 16384
 
 /* Storage precision of the distributions.  Arithmetic is FP64 for LBM_F64
  * and FP32 otherwise.  The *D forms store the deviation of each population
@@ -171,6 +175,37 @@ int lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
 int lbm_get_state_f64(lbm_ctx *ctx, double *f, double *g, double *tau);
 int lbm_set_state_f64(lbm_ctx *ctx, const double *f, const double *g,
                       const double *tau);
+
+/* Allocation-free form of lbm_residual, for callers that cannot call
+ * cudaMalloc at the point where they check convergence: host code that must
+ * not block (cudaMalloc and cudaFree can synchronise the device and stall
+ * work already queued), and applications whose device memory is handed out
+ * by their own pool allocator, where a stray allocation can fail or fragment
+ * the pool.  The paper has no counterpart; it is an interface addition.
+ *
+ * It computes the same quantity as lbm_residual -- for phi in {u_x, u_y, T},
+ * ||phi - phi_prev||_2 / ||phi||_2 accumulated in FP64 -- but every buffer
+ * is the caller's and nothing is allocated, freed or synchronised:
+ *   d_snapshot  device memory of the context's device, 3*nx*ny doubles
+ *               ([3][ny][nx]: u_x, u_y, T); read as the previous fields
+ *               unless `first` is non-zero, then overwritten with the
+ *               current ones;
+ *   first       non-zero: only store the snapshot (results are +inf);
+ *   d_result    device memory, 4 doubles, written on the context's stream:
+ *               [0..2] the relative change of u_x, u_y, T, [3] the number of
+ *               non-finite values seen.
+ * The work is queued on the context's stream; synchronise before reading
+ * d_result.  The partial sums live in a fixed device array of
+ * LBM_NOALLOC_MAX_ROWS rows (1 MiB) inside the library, kept on every GPU
+ * that loaded it until the process exits; grids with more rows are refused
+ * with LBM_ERR_SIZE.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress), so make it before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (every slot a call reads is written earlier in the same call); calls that
+ * overlap on the GPU, e.g. on two streams, race on it.
+ * Errors: LBM_ERR_ARG (NULL pointer), LBM_ERR_SIZE, LBM_ERR_CUDA. */
+int lbm_residual_noalloc(lbm_ctx *ctx, double *d_snapshot, int first,
+                         double *d_result);
 
 /* Name of an LBM_* code (static storage). */
 const char *lbm_strerror(int code);

@@ -395,6 +395,7 @@ const char *lbm_strerror(int code)
     case LBM_ERR_OOM: return "LBM_ERR_OOM: device allocation failed";
     case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT: bounded device wait gave up";
     case LBM_ERR_UNSUPPORTED: return "LBM_ERR_UNSUPPORTED: option not built";
+    case LBM_ERR_SIZE: return "LBM_ERR_SIZE: grid larger than the fixed scratch area";
     default: return "unknown lbm error";
     }
 }

@@ -20,7 +20,9 @@ STORE_DTYPE = {F64: np.float64, F32: np.float32, BF16D: np.uint16, F16D: np.floa
 TAU_DTYPE = {F64: np.float64, F32: np.float32, BF16D: np.float32, F16D: np.float32}
 
 ERRORS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_UNSTABLE", -3: "LBM_ERR_NONFINITE",
-          -4: "LBM_ERR_CUDA", -5: "LBM_ERR_OOM", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_UNSUPPORTED"}
+          -4: "LBM_ERR_CUDA", -5: "LBM_ERR_OOM", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_UNSUPPORTED",
+          -8: "LBM_ERR_SIZE"}
+NOALLOC_MAX_ROWS = 16384
 
 
 class LBMError(RuntimeError):
@@ -76,6 +78,7 @@ SIGNATURES = [
     ("lbm_set_state", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     ("lbm_get_state_f64", ctypes.c_int, [_VP, _D, _D, _D]),
     ("lbm_set_state_f64", ctypes.c_int, [_VP, _D, _D, _D]),
+    ("lbm_residual_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("lbm_last_cuda_error", ctypes.c_char_p, []),
 ]
@@ -175,6 +178,11 @@ def residual(ctx) -> float:
     r = ctypes.c_double()
     _check(lib().lbm_residual(ctx, ctypes.byref(r)), "lbm_residual")
     return r.value
+
+
+def residual_noalloc(ctx, d_snapshot: int, first: bool, d_result: int):
+    """Allocation-free residual: device pointers in, results left on the device."""
+    _check(lib().lbm_residual_noalloc(ctx, d_snapshot, 1 if first else 0, d_result), "lbm_residual_noalloc")
 
 
 def run_to_steady(ctx, tol: float, max_steps: int):
