@@ -49,19 +49,31 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(prec, N):
-    """DRAM bytes per launch of the step kernel from the committed ncu
-    summary (lines: prec N bytes_per_launch source_hash), or None."""
+def recorded(key, N=None):
+    """A figure from the committed ncu summary ``profiles/traffic.txt``
+    (lines: key N value source_hash), or None if absent or taken from other
+    CUDA sources.  N=None accepts any grid size."""
     try:
         with open(TRAFFIC_FILE) as fh:
             for line in fh:
                 parts = line.split()
-                if len(parts) == 4 and not line.startswith("#") and parts[0] == prec and int(parts[1]) == N:
+                if len(parts) == 4 and not line.startswith("#") and parts[0] == key and \
+                        (N is None or int(parts[1]) == N):
                     if parts[3] == kernel_source_hash():
                         return float(parts[2])
     except OSError:
         pass
     return None
+
+
+def recorded_traffic(prec, N):
+    """DRAM bytes per launch of the step kernel at this grid, or None."""
+    return recorded(prec, N)
+
+
+# FP64 pipe of this part: 2 FP64 lanes per SM per cycle (measured in
+# profiles/step_kernel_f64_1536.md), 152 SMs.
+FP64_LANES_PER_SM, N_SM = 2, 152
 
 
 def parse():
@@ -148,6 +160,13 @@ class Clocks:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def clk_summary_max(clk):
+    try:
+        return clk.summary()["sm_max_mhz"]
+    except Exception:
+        return None
 
 
 def dist_env():
@@ -308,6 +327,16 @@ def main():
                        "fused_steps_per_bench_step": vd,
                        "bytes_per_node": BYTES_PER_NODE[v], "achieved_GBs": av, "frac_of_hbm": av / peak,
                        "nu_hot": nuv}
+        if v == "f64":
+            ipn = recorded("f64_fp64_inst_per_node")
+            clk = clk_summary_max(clk)
+            if ipn and clk:
+                peak_inst = FP64_LANES_PER_SM * N_SM * clk * 1e6
+                ach = N * N / kv * ipn
+                variants[v]["roofline"] = {"bound": "alu", "unit": "FP64 inst/s", "achieved": ach,
+                                           "peak": peak_inst, "frac": ach / peak_inst,
+                                           "fp64_inst_per_node": ipn,
+                                           "peak_source": "2 FP64 lanes/SM/cycle x 152 SMs x max SM clock"}
     e2e = None
     if not args.no_e2e:
         es = max(2, args.steps // 2)
