@@ -91,202 +91,118 @@ def parse():
                     help="other storage precisions measured beside the headline ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--study", choices=["tables", "precision"], default=None,
+                    help="physics studies instead of the throughput bench (one JSON line per case)")
+    ap.add_argument("--study-N", type=int, default=None)
+    ap.add_argument("--study-max-steps", type=int, default=3_000_000)
     return ap.parse_args()
 
 
-def hbm_peak():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    try:
-        with open(path) as fh:
-            d = json.load(fh)
-        for k in ("hbm_gbs", "hbm_GBps", "hbm"):
-            if k in d:
-                return float(d[k]), "measured"
-    except (OSError, ValueError):
-        pass
-    return FALLBACK_HBM_GBS, "fallback"
+# Average Nusselt numbers the paper prints (Table 1: clear fluid, Ra = 1e5,
+# Pr = 100; Table 2: 160 x 160 grid, Pr = 6.2).
+PAPER_TABLES = [
+    ("table1", dict(n=0.6, Da=None, Ra=1e5, Pr=100.0), 12.95289),
+    ("table1", dict(n=1.0, Da=None, Ra=1e5, Pr=100.0), 4.69148),
+    ("table1", dict(n=1.4, Da=None, Ra=1e5, Pr=100.0), 2.44821),
+    ("case1", dict(n=0.6, Da=1e-3, Ra=1e5, Pr=6.2), 9.249539),
+    ("case1", dict(n=1.0, Da=1e-3, Ra=1e5, Pr=6.2), 2.430419),
+    ("case1", dict(n=1.4, Da=1e-3, Ra=1e5, Pr=6.2), 1.300101),
+    ("case2", dict(n=0.6, Da=1e-2, Ra=1e5, Pr=6.2), 12.835687),
+    ("case2", dict(n=0.6, Da=1e-1, Ra=1e5, Pr=6.2), 13.316177),
+    ("case3", dict(n=0.6, Da=1e-2, Ra=1e3, Pr=6.2), 1.068697),
+    ("case3", dict(n=0.6, Da=1e-2, Ra=1e4, Pr=6.2), 4.411946),
+]
 
 
-class Clocks:
-    """nvidia-smi sampler for the SM clock and throttle reasons (read-only)."""
-
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, index):
-        self.index = index
-        self.proc = None
-        self.lines = []
-
-    def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except OSError:
-            self.proc = None
-        return self
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
-    def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-
-    def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                mx = float(parts[1])
-            except ValueError:
-                continue
-            for name, v in zip(names, parts[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
+def run_until_nu_settles(cav, max_steps, chunk=20000, window=6, rel=1e-6):
+    """Advance until the residual falls below 1e-10 or the hot-wall Nu of the
+    last `window` chunks spreads by less than `rel` (the literal power law can
+    leave a small limit cycle at nodes sitting on the gamma_1 jump, so the
+    residual need not vanish), or until max_steps."""
+    cav.residual()
+    hist, done = [], 0
+    while done < max_steps:
+        cav.step(chunk)
+        done += chunk
+        r = cav.residual()
+        nu = cav.nusselt()[0]
+        hist.append(nu)
+        if r < 1e-10:
+            return done, r, "tol"
+        last = hist[-window:]
+        if len(last) == window and (max(last) - min(last)) <= rel * abs(last[-1]):
+            return done, r, "nu_settled"
+    return done, r, "max_steps"
 
 
-def clk_summary_max(clk):
-    try:
-        return clk.summary()["sm_max_mhz"]
-    except Exception:
-        return None
-
-
-def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
-
-
-def time_ours(lbm, torch, N, prec, steps, warmup, delta, stream):
-    """Device-resident run: returns (seconds for `steps` bench steps, avg fused
-    kernel seconds, kernels launched in the timed region, Nu)."""
-    cav = lbm.Cavity(N, N, prec=prec, cuda_stream=stream, **CASE)
-    try:
-        cav.residual()   # first call stores the snapshot
-        for _ in range(warmup):
-            cav.step(delta)
-            cav.nusselt()
-            cav.residual()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(steps)]
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        t0.record(stream)
-        nu = None
-        for s in range(steps):
-            ev[s][0].record(stream)
-            cav.step(delta)
-            ev[s][1].record(stream)
-            nu = cav.nusselt()[0]
-            cav.residual()
-        t1.record(stream)
-        torch.cuda.synchronize()
-        total = t0.elapsed_time(t1) / 1e3
-        kern = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / (steps * delta)
-        launches = steps * (delta + 1 + 2)
-        return total, kern, launches, nu
-    finally:
-        cav.close()
-
-
-def time_e2e(lbm, torch, N, prec, steps, warmup, delta, stream):
-    """End to end through the C ABI with host buffers: each bench step uploads
-    the state from pinned host memory, runs `delta` fused steps and reads the
-    hot-wall Nusselt number back."""
-    cav = lbm.Cavity(N, N, prec=prec, cuda_stream=stream, **CASE)
-    try:
-        nbytes = cav.state_bytes()
-        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
-        cav.get_state(host)
-        for _ in range(warmup):
-            cav.set_state(host)
-            cav.step(delta)
-            cav.nusselt()
-        torch.cuda.synchronize()
+def study_tables(args):
+    """The paper's cases with its own Darcy model (porosity 1, no Forchheimer
+    term) and its literal modified power law on its 160 x 160 grid, FP64, run
+    until the Nusselt number settles; the clear-fluid cases of Table 1 use a
+    permeability large enough that the drag vanishes."""
+    from paper_2011_15073_gb300 import lbm
+    N = args.study_N or 160
+    for table, c, nu_paper in PAPER_TABLES:
+        Da = c["Da"] if c["Da"] is not None else 1e12
         t = time.perf_counter()
-        for _ in range(steps):
-            cav.set_state(host)
-            cav.step(delta)
-            cav.nusselt()
-        dt = time.perf_counter() - t
-        return dt, nbytes, 8
-    finally:
-        cav.close()
+        with lbm.Cavity(N, N, c["n"], Da, c["Ra"], c["Pr"], 1.0, prec="f64", porous_model=0) as cav:
+            steps, resid, why = run_until_nu_settles(cav, args.study_max_steps)
+            hot, cold, _ = cav.nusselt()
+            L = cav.lattice()
+        print(json.dumps({"study": "tables", "table": table, "N": N, **{k: v for k, v in c.items()},
+                          "nu_hot": hot, "nu_cold": cold, "nu_paper": nu_paper,
+                          "rel_diff": (hot - nu_paper) / nu_paper, "steps": steps, "residual": resid,
+                          "stop": why, "tau0": L.tau0, "tauT": L.tauT,
+                          "seconds": time.perf_counter() - t}), flush=True)
 
 
-def cpu_baseline(N_sample=1024, steps=150):
-    """The FP64 oracle as it stands, on all host cores (OpenMP), on a bounded
-    sample of the workload: an N_sample^2 cavity with the same parameters."""
-    import oracle
-    cores = os.cpu_count() or 1
-    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
-    oracle.build()
-    c = oracle.Cavity.from_params(N_sample, N_sample, CASE["n"], CASE["Da"], CASE["Ra"], CASE["Pr"],
-                                  porosity=CASE["porosity"])
-    c.step(1)
-    t = time.perf_counter()
-    c.step(steps)
-    dt = time.perf_counter() - t
-    mlups = N_sample * N_sample * steps / dt / 1e6
-    return {"value": mlups, "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
-            "sample": f"FP64 oracle, {N_sample}x{N_sample} cavity, {steps} steps, same (n, Da, Ra, Pr, porosity)"}
-
-
-def run_reference(args):
-    rank, world, _ = dist_env()
-    if rank != 0:
-        return
-    steps_each = 10
-    import oracle
-    oracle.build()
-    cores = os.cpu_count() or 1
-    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
-    Ns = 1024
-    c = oracle.Cavity.from_params(Ns, Ns, CASE["n"], CASE["Da"], CASE["Ra"], CASE["Pr"], porosity=CASE["porosity"])
-    for _ in range(args.warmup):
-        c.step(steps_each)
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        c.step(steps_each)
-    dt = time.perf_counter() - t
-    mlups = Ns * Ns * steps_each * args.steps / dt / 1e6
-    line = {"impl": "reference", "metric": "fused MRT step MLUPS", "value": mlups, "unit": "MLUPS",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"cavity {args.N}x{args.N} (timed on a {Ns}x{Ns} sample), "
-                                   f"n={CASE['n']}, Da={CASE['Da']}, Ra={CASE['Ra']}, Pr={CASE['Pr']}, "
-                                   f"porosity={CASE['porosity']}",
-                       "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
-                             "kind": "oracle",
-                             "sample": f"{Ns}x{Ns} cavity, {steps_each} steps per bench step"},
-            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+def study_precision(args):
+    """FP32 and 16-bit deviation storage against FP64 storage at the FP64 steady
+    state: the FP64 run goes to a residual of 1e-10 in S steps (continuous
+    power law, so the steady state is unique), every other storage then runs
+    the same S steps from the same rest state; reported are the relative L2
+    errors of u_x, u_y, T and the relative hot-wall Nu difference."""
+    import numpy as np
+    from paper_2011_15073_gb300 import lbm
+    N = args.study_N or 512
+    for n in (0.6, 1.0):
+        case = dict(n=n, Da=1e-2, Ra=1e5, Pr=6.2, porosity=0.6)
+        res = {}
+        S = None
+        for prec in ("f64", "f32", "f16d", "bf16d"):
+            t = time.perf_counter()
+            with lbm.Cavity(N, N, prec=prec, resid_interval=1000, clamp_mode=1, **case) as cav:
+                if prec == "f64":
+                    S, resid, why = cav.run_to_steady(1e-10, args.study_max_steps)
+                    stop = ["tol", "stagnated", "max_steps"][why]
+                else:
+                    cav.step(S - 1000)
+                    cav.residual()
+                    cav.step(1000)
+                    resid, stop = cav.residual(), "same_steps"
+                hot, cold, _ = cav.nusselt()
+                fl = cav.fields()
+            res[prec] = dict(nu=hot, nu_cold=cold, fl=fl, steps=S, resid=resid, stop=stop,
+                             sec=time.perf_counter() - t)
+        ref = res["f64"]
+        for prec, r in res.items():
+            err = {k: float(np.linalg.norm(r["fl"][k] - ref["fl"][k]) / np.linalg.norm(ref["fl"][k]))
+                   for k in ("ux", "uy", "T")}
+            print(json.dumps({"study": "precision", "N": N, **case, "clamp_mode": 1, "prec": prec,
+                              "nu_hot": r["nu"], "nu_cold": r["nu_cold"],
+                              "dnu_rel": (r["nu"] - ref["nu"]) / ref["nu"], "l2_rel": err,
+                              "steps": r["steps"], "residual": r["resid"], "stop": r["stop"],
+                              "seconds": r["sec"]}), flush=True)
 
 
 def main():
     args = parse()
+    if args.study == "tables":
+        study_tables(args)
+        return
+    if args.study == "precision":
+        study_precision(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -329,9 +245,9 @@ def main():
                        "nu_hot": nuv}
         if v == "f64":
             ipn = recorded("f64_fp64_inst_per_node")
-            clk = clk_summary_max(clk)
-            if ipn and clk:
-                peak_inst = FP64_LANES_PER_SM * N_SM * clk * 1e6
+            mhz = clk_summary_max(clk)
+            if ipn and mhz:
+                peak_inst = FP64_LANES_PER_SM * N_SM * mhz * 1e6
                 ach = N * N / kv * ipn
                 variants[v]["roofline"] = {"bound": "alu", "unit": "FP64 inst/s", "achieved": ach,
                                            "peak": peak_inst, "frac": ach / peak_inst,

@@ -65,12 +65,18 @@ typedef struct {
                           Forchheimer model with the porosity        [1]    */
     double s_e, s_p;   /* free thermal MRT rates (4th, 5th moment)   [1.5]  */
     int resid_interval;/* steps between convergence checks           [1000] */
-    int layout;        /* 0: two-buffer pull scheme                  [0]    */
+    int layout;        /* 0: two-buffer pull scheme; 1: one buffer,
+                          in-place AA-pattern streaming (half the
+                          memory, same bytes per update)             [0]    */
     void *cuda_stream; /* cudaStream_t to run on; NULL: the library
                           creates and owns one                       [NULL] */
     int device;        /* CUDA device ordinal the context lives on and
                           every call selects; -1: the device current
                           in the calling thread at lbm_init          [-1]   */
+    double stag_floor; /* lbm_run_to_steady stops on stagnation only
+                          below this residual (the storage's noise
+                          floor); < 0: 0 for F64 (never), 1e-6 for
+                          F32, 1e-2 for F16D, 1e-1 for BF16D         [-1]   */
 } lbm_opts;
 
 /* Lattice-unit parameters the library derived from the problem groups
@@ -150,7 +156,8 @@ int lbm_nusselt(lbm_ctx *ctx, double *nu_hot, double *nu_cold,
 int lbm_residual(lbm_ctx *ctx, double *resid);
 
 /* Run until the residual (checked every resid_interval steps) falls below
- * tol, stagnates (no new minimum over 10 checks), or max_steps is reached.
+ * tol, stagnates (below stag_floor with no new minimum over 10 checks), or
+ * max_steps is reached.
  * *steps_done, *resid and *reason (0 tol reached, 1 stagnated, 2 max_steps)
  * may be NULL.  Returns LBM_ERR_NONFINITE on NaN or Inf. */
 int lbm_run_to_steady(lbm_ctx *ctx, double tol, int64_t max_steps,
@@ -203,7 +210,9 @@ int lbm_set_state_f64(lbm_ctx *ctx, const double *f, const double *g,
  * capture.  All calls share the array and it keeps the last call's contents
  * (every slot a call reads is written earlier in the same call); calls that
  * overlap on the GPU, e.g. on two streams, race on it.
- * Errors: LBM_ERR_ARG (NULL pointer), LBM_ERR_SIZE, LBM_ERR_CUDA. */
+ * Contexts with the in-place layout (layout = 1) get LBM_ERR_UNSUPPORTED.
+ * Errors: LBM_ERR_ARG (NULL pointer), LBM_ERR_SIZE, LBM_ERR_UNSUPPORTED,
+ * LBM_ERR_CUDA. */
 int lbm_residual_noalloc(lbm_ctx *ctx, double *d_snapshot, int first,
                          double *d_result);
 

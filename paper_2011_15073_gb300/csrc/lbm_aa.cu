@@ -1,0 +1,300 @@
+// lbm_aa.cu -- in-place (AA-pattern) streaming: one buffer instead of two.
+//
+// The single array A holds, per node x and direction i, one population; its
+// meaning alternates between two forms:
+//   form E (after an even step, and at start): A[opp(i)][x] = f*_i(x), the
+//     post-collision population of node x moving along e_i;
+//   form O (after an odd step): A[i][x] = f_i(x), the population that has
+//     arrived at x and enters its next collision.
+// Even step (O -> E): each node reads its own slots i, collides and writes
+//   f*_i into its own slot opp(i).  No neighbour is touched.
+// Odd step (E -> O): each node gathers f_i(x) = f*_i(x - e_i) from slot
+//   opp(i) of node x - e_i (its own slot i across a wall, with the thermal
+//   wall rules), collides and pushes f*_i(x) into slot i of node x + e_i;
+//   a link that leaves the cavity writes the returning population into the
+//   node's own slot opp(i) (bounce-back; anti-bounce-back -g* + 2 w T_w on
+//   the isothermal walls).
+// Every slot a step writes is one the same node read in that step, so the
+// update is race-free in place.  The bytes moved per node update are the
+// same as with two buffers; the footprint is halved.
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// Push node (x, y)'s post-collision populations for the odd step.
+template <int PREC, class R>
+__device__ __forceinline__ void push(typename Store<PREC>::S *__restrict__ A, const Phys<R> &p, int x, int y,
+                                     const R f[9], const R g[5])
+{
+    using St = Store<PREC>;
+    const int64_t P = p.plane, W = p.pitch;
+    const int64_t k = (int64_t)y * W + x;
+    const bool xl = x > 0, xr = x < p.nx - 1, yb = y > 0, yt = y < p.ny - 1;
+    // target x + e_i: e1 (1,0) e2 (0,1) e3 (-1,0) e4 (0,-1) e5 (1,1) e6 (-1,1) e7 (-1,-1) e8 (1,-1)
+    St::st(A, 0 * P + k, f[0], R(rest_f(0)));
+    if (xr) St::st(A, 1 * P + k + 1, f[1], R(rest_f(1))); else St::st(A, 3 * P + k, f[1], R(rest_f(3)));
+    if (yt) St::st(A, 2 * P + k + W, f[2], R(rest_f(2))); else St::st(A, 4 * P + k, f[2], R(rest_f(4)));
+    if (xl) St::st(A, 3 * P + k - 1, f[3], R(rest_f(3))); else St::st(A, 1 * P + k, f[3], R(rest_f(1)));
+    if (yb) St::st(A, 4 * P + k - W, f[4], R(rest_f(4))); else St::st(A, 2 * P + k, f[4], R(rest_f(2)));
+    if (xr && yt) St::st(A, 5 * P + k + W + 1, f[5], R(rest_f(5))); else St::st(A, 7 * P + k, f[5], R(rest_f(7)));
+    if (xl && yt) St::st(A, 6 * P + k + W - 1, f[6], R(rest_f(6))); else St::st(A, 8 * P + k, f[6], R(rest_f(8)));
+    if (xl && yb) St::st(A, 7 * P + k - W - 1, f[7], R(rest_f(7))); else St::st(A, 5 * P + k, f[7], R(rest_f(5)));
+    if (xr && yb) St::st(A, 8 * P + k - W + 1, f[8], R(rest_f(8))); else St::st(A, 6 * P + k, f[8], R(rest_f(6)));
+    typename Store<PREC>::S *G = A + 9 * P;
+    St::st(G, 0 * P + k, g[0], R(rest_g(0)));
+    if (xr) St::st(G, 1 * P + k + 1, g[1], R(rest_g(1))); else St::st(G, 3 * P + k, p.abb_cold - g[1], R(rest_g(3)));
+    if (yt) St::st(G, 2 * P + k + W, g[2], R(rest_g(2))); else St::st(G, 4 * P + k, g[2], R(rest_g(4)));
+    if (xl) St::st(G, 3 * P + k - 1, g[3], R(rest_g(3))); else St::st(G, 1 * P + k, p.abb_hot - g[3], R(rest_g(1)));
+    if (yb) St::st(G, 4 * P + k - W, g[4], R(rest_g(4))); else St::st(G, 2 * P + k, g[4], R(rest_g(2)));
+}
+
+// ------------------------------------------------------- one node / thread
+template <int PREC>
+__global__ void __launch_bounds__(128)
+aa_even_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::TauS *__restrict__ tau,
+               Phys<typename Store<PREC>::R> p)
+{
+    using St = Store<PREC>;
+    using R = typename St::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= p.nx) return;
+    const int64_t P = p.plane, k = (int64_t)y * p.pitch + x;
+    R f[9], g[5];
+#pragma unroll
+    for (int i = 0; i < 9; i++) f[i] = St::ld(A, i * P + k, R(rest_f(i)));
+#pragma unroll
+    for (int i = 0; i < 5; i++) g[i] = St::ld(A + 9 * P, i * P + k, R(rest_g(i)));
+    Macro<R> m;
+    const R t = collide<R>(p, f, g, R(tau[k]), m);
+#pragma unroll
+    for (int i = 0; i < 9; i++) St::st(A, opp(i) * P + k, f[i], R(rest_f(opp(i))));
+#pragma unroll
+    for (int i = 0; i < 5; i++) St::st(A + 9 * P, opp(i) * P + k, g[i], R(rest_g(opp(i))));
+    tau[k] = typename St::TauS(t);
+}
+
+template <int PREC, class R>
+__device__ __forceinline__ void odd_node(typename Store<PREC>::S *__restrict__ A,
+                                         typename Store<PREC>::TauS *__restrict__ tau, const Phys<R> &p, int x,
+                                         int y)
+{
+    const int64_t k = (int64_t)y * p.pitch + x;
+    R f[9], g[5];
+    pull<PREC, R, true>(A, p, x, y, f, g);
+    Macro<R> m;
+    const R t = collide<R>(p, f, g, R(tau[k]), m);
+    push<PREC, R>(A, p, x, y, f, g);
+    tau[k] = typename Store<PREC>::TauS(t);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(128)
+aa_odd_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::TauS *__restrict__ tau,
+              Phys<typename Store<PREC>::R> p)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= p.nx) return;
+    odd_node<PREC, typename Store<PREC>::R>(A, tau, p, x, y);
+}
+
+// ------------------------------------------------------ two nodes / thread
+template <int PREC>
+__global__ void __launch_bounds__(128)
+aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
+{
+    using St = Store<PREC>;
+    const int x0 = (blockIdx.x * 128 + threadIdx.x) * 2, y = blockIdx.y;
+    if (x0 >= p.nx) return;
+    const int64_t P = p.plane, k = (int64_t)y * p.pitch + x0;
+    if (x0 + 1 >= p.nx) {   // ragged end of the row: one node
+        float f[9], g[5];
+        for (int i = 0; i < 9; i++) f[i] = St::ld(A, i * P + k, float(rest_f(i)));
+        for (int i = 0; i < 5; i++) g[i] = St::ld(A + 9 * P, i * P + k, float(rest_g(i)));
+        Macro<float> m;
+        const float t = collide<float>(p, f, g, tau[k], m);
+        for (int i = 0; i < 9; i++) St::st(A, opp(i) * P + k, f[i], float(rest_f(opp(i))));
+        for (int i = 0; i < 5; i++) St::st(A + 9 * P, opp(i) * P + k, g[i], float(rest_g(opp(i))));
+        tau[k] = t;
+        return;
+    }
+    F2 f[9], g[5];
+#pragma unroll
+    for (int i = 0; i < 9; i++) f[i] = St::ld2(A + i * P, k, float(rest_f(i)));
+#pragma unroll
+    for (int i = 0; i < 5; i++) g[i] = St::ld2(A + (9 + i) * P, k, float(rest_g(i)));
+    Macro<F2> m;
+    const F2 t = collide<F2>(p2, f, g, F2(*reinterpret_cast<const float2 *>(tau + k)), m);
+#pragma unroll
+    for (int i = 0; i < 9; i++) St::st2(A + opp(i) * P, k, f[i], float(rest_f(opp(i))));
+#pragma unroll
+    for (int i = 0; i < 5; i++) St::st2(A + (9 + opp(i)) * P, k, g[i], float(rest_g(opp(i))));
+    *reinterpret_cast<float2 *>(tau + k) = t.v;
+}
+
+// Odd-step pushes of a pair (nodes x0, x0 + 1) one node to the right / left
+// within one row of a plane; the aligned pair at x0 is assembled with a warp
+// shuffle, and the lanes at the warp's ends store the element that belongs
+// to the neighbouring warp's pair on their own.
+template <int PREC>
+__device__ __forceinline__ void push_right(typename Store<PREC>::S *base, int64_t kr, F2 v, float rest, int lane)
+{
+    using St = Store<PREC>;
+    const float prev = __shfl_up_sync(0xffffffffu, v.v.y, 1);
+    if (lane != 0) St::st2(base, kr, F2(prev, v.v.x), rest);
+    else St::st(base, kr + 1, v.v.x, rest);
+    if (lane == 31) St::st(base, kr + 2, v.v.y, rest);
+}
+template <int PREC>
+__device__ __forceinline__ void push_left(typename Store<PREC>::S *base, int64_t kr, F2 v, float rest, int lane)
+{
+    using St = Store<PREC>;
+    const float next = __shfl_down_sync(0xffffffffu, v.v.x, 1);
+    if (lane != 31) St::st2(base, kr, F2(v.v.y, next), rest);
+    else St::st(base, kr, v.v.y, rest);
+    if (lane == 0) St::st(base, kr - 1, v.v.x, rest);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(128)
+aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
+{
+    using St = Store<PREC>;
+    using S = typename St::S;
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * 128 + threadIdx.x) * 2, y = blockIdx.y;
+    const int wx = (blockIdx.x * 128 + (threadIdx.x & ~31)) * 2;
+    const bool fast = y > 0 && y < p.ny - 1 && wx > 0 && wx + 64 < p.nx;
+    if (!fast) {
+        for (int j = 0; j < 2; j++)
+            if (x0 + j < p.nx) odd_node<PREC, float>(A, tau, p, x0 + j, y);
+        return;
+    }
+    const int64_t P = p.plane, W = p.pitch;
+    const int64_t k = (int64_t)y * W + x0;
+    S *fs = A;
+    S *gs = A + 9 * P;
+    const bool l0 = lane == 0, l31 = lane == 31;
+    // gather f_i(x) = f*_i(x - e_i), kept in slot opp(i) of node x - e_i
+    F2 f[9], g[5];
+    f[0] = St::ld2(fs, k, float(rest_f(0)));
+    f[1] = from_left(St::ld2(fs + 3 * P, k, float(rest_f(3))), l0 ? St::ld(fs + 3 * P, k - 1, float(rest_f(3))) : 0.f, lane);
+    f[2] = St::ld2(fs + 4 * P, k - W, float(rest_f(4)));
+    f[3] = from_right(St::ld2(fs + P, k, float(rest_f(1))), l31 ? St::ld(fs + P, k + 2, float(rest_f(1))) : 0.f, lane);
+    f[4] = St::ld2(fs + 2 * P, k + W, float(rest_f(2)));
+    f[5] = from_left(St::ld2(fs + 7 * P, k - W, float(rest_f(7))),
+                     l0 ? St::ld(fs + 7 * P, k - W - 1, float(rest_f(7))) : 0.f, lane);
+    f[6] = from_right(St::ld2(fs + 8 * P, k - W, float(rest_f(8))),
+                      l31 ? St::ld(fs + 8 * P, k - W + 2, float(rest_f(8))) : 0.f, lane);
+    f[7] = from_right(St::ld2(fs + 5 * P, k + W, float(rest_f(5))),
+                      l31 ? St::ld(fs + 5 * P, k + W + 2, float(rest_f(5))) : 0.f, lane);
+    f[8] = from_left(St::ld2(fs + 6 * P, k + W, float(rest_f(6))),
+                     l0 ? St::ld(fs + 6 * P, k + W - 1, float(rest_f(6))) : 0.f, lane);
+    g[0] = St::ld2(gs, k, float(rest_g(0)));
+    g[1] = from_left(St::ld2(gs + 3 * P, k, float(rest_g(3))), l0 ? St::ld(gs + 3 * P, k - 1, float(rest_g(3))) : 0.f, lane);
+    g[2] = St::ld2(gs + 4 * P, k - W, float(rest_g(4)));
+    g[3] = from_right(St::ld2(gs + P, k, float(rest_g(1))), l31 ? St::ld(gs + P, k + 2, float(rest_g(1))) : 0.f, lane);
+    g[4] = St::ld2(gs + 2 * P, k + W, float(rest_g(2)));
+    Macro<F2> m;
+    const F2 t = collide<F2>(p2, f, g, F2(*reinterpret_cast<const float2 *>(tau + k)), m);
+    // push f*_i(x) into slot i of node x + e_i
+    St::st2(fs, k, f[0], float(rest_f(0)));
+    push_right<PREC>(fs + P, k, f[1], float(rest_f(1)), lane);
+    St::st2(fs + 2 * P, k + W, f[2], float(rest_f(2)));
+    push_left<PREC>(fs + 3 * P, k, f[3], float(rest_f(3)), lane);
+    St::st2(fs + 4 * P, k - W, f[4], float(rest_f(4)));
+    push_right<PREC>(fs + 5 * P, k + W, f[5], float(rest_f(5)), lane);
+    push_left<PREC>(fs + 6 * P, k + W, f[6], float(rest_f(6)), lane);
+    push_left<PREC>(fs + 7 * P, k - W, f[7], float(rest_f(7)), lane);
+    push_right<PREC>(fs + 8 * P, k - W, f[8], float(rest_f(8)), lane);
+    St::st2(gs, k, g[0], float(rest_g(0)));
+    push_right<PREC>(gs + P, k, g[1], float(rest_g(1)), lane);
+    St::st2(gs + 2 * P, k + W, g[2], float(rest_g(2)));
+    push_left<PREC>(gs + 3 * P, k, g[3], float(rest_g(3)), lane);
+    St::st2(gs + 4 * P, k - W, g[4], float(rest_g(4)));
+    *reinterpret_cast<float2 *>(tau + k) = t.v;
+}
+
+// Form O -> form E in place, without a collision: each interior link
+// (x, x + e_i), i in {1, 2, 5, 6} (one of each opposite pair), swaps slot i of
+// x + e_i with slot opp(i) of x; a thermal link that left through an
+// isothermal wall turns its stored -g*_i + 2 w T_w back into g*_i.  Every slot
+// belongs to exactly one such link.
+template <int PREC>
+__global__ void __launch_bounds__(128)
+aa_normalize_kernel(typename Store<PREC>::S *__restrict__ A, Phys<typename Store<PREC>::R> p)
+{
+    using St = Store<PREC>;
+    using R = typename St::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= p.nx) return;
+    const int64_t P = p.plane, W = p.pitch, k = (int64_t)y * W + x;
+    const bool xl = x > 0, xr = x < p.nx - 1, yb = y > 0, yt = y < p.ny - 1;
+    auto swap = [&](typename Store<PREC>::S *base, int i, int64_t kt, bool flow) {
+        const R ri = R(flow ? rest_f(i) : rest_g(i)), ro = R(flow ? rest_f(opp(i)) : rest_g(opp(i)));
+        const R a = St::ld(base, i * P + kt, ri);
+        const R b = St::ld(base, opp(i) * P + k, ro);
+        St::st(base, i * P + kt, b, ri);
+        St::st(base, opp(i) * P + k, a, ro);
+    };
+    if (xr) swap(A, 1, k + 1, true);
+    if (yt) swap(A, 2, k + W, true);
+    if (xr && yt) swap(A, 5, k + W + 1, true);
+    if (xl && yt) swap(A, 6, k + W - 1, true);
+    typename Store<PREC>::S *G = A + 9 * P;
+    if (xr) swap(G, 1, k + 1, false);
+    if (yt) swap(G, 2, k + W, false);
+    if (!xl) St::st(G, 1 * P + k, p.abb_hot - St::ld(G, 1 * P + k, R(rest_g(1))), R(rest_g(1)));
+    if (!xr) St::st(G, 3 * P + k, p.abb_cold - St::ld(G, 3 * P + k, R(rest_g(3))), R(rest_g(3)));
+}
+
+// ------------------------------------------------------------- launchers
+template <int PREC>
+static cudaError_t aa_step_t(lbm_ctx *c)
+{
+    using St = Store<PREC>;
+    auto *A = (typename St::S *)c->buf.dist[0];
+    if constexpr (PREC == LBM_F64) {
+        const dim3 grid((c->nx + 127) / 128, c->ny);
+        if (c->aa_form_o)
+            aa_even_kernel<PREC><<<grid, 128, 0, c->stream>>>(A, (double *)c->buf.tau[0], make_params<double>(c));
+        else
+            aa_odd_kernel<PREC><<<grid, 128, 0, c->stream>>>(A, (double *)c->buf.tau[0], make_params<double>(c));
+    } else {
+        const dim3 grid((c->nx + 255) / 256, c->ny);
+        if (c->aa_form_o)
+            aa_even2_kernel<PREC><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0], make_params<float>(c),
+                                                             make_params<F2>(c));
+        else
+            aa_odd2_kernel<PREC><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0], make_params<float>(c),
+                                                            make_params<F2>(c));
+    }
+    c->aa_form_o = !c->aa_form_o;
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t aa_normalize_t(lbm_ctx *c)
+{
+    using St = Store<PREC>;
+    if (!c->aa_form_o) return cudaSuccess;
+    const dim3 grid((c->nx + 127) / 128, c->ny);
+    aa_normalize_kernel<PREC><<<grid, 128, 0, c->stream>>>((typename St::S *)c->buf.dist[0],
+                                                          make_params<typename St::R>(c));
+    c->aa_form_o = false;
+    return cudaGetLastError();
+}
+
+#define LBM_DISPATCH(fn, ...)                                      \
+    switch (c->opts.prec) {                                        \
+    case LBM_F64: return fn<LBM_F64>(__VA_ARGS__);                 \
+    case LBM_F32: return fn<LBM_F32>(__VA_ARGS__);                 \
+    case LBM_BF16D: return fn<LBM_BF16D>(__VA_ARGS__);             \
+    case LBM_F16D: return fn<LBM_F16D>(__VA_ARGS__);               \
+    default: return cudaErrorInvalidValue;                         \
+    }
+
+cudaError_t launch_aa_step(lbm_ctx *c) { LBM_DISPATCH(aa_step_t, c) }
+cudaError_t launch_aa_normalize(lbm_ctx *c) { LBM_DISPATCH(aa_normalize_t, c) }
+
+}  // namespace lbm

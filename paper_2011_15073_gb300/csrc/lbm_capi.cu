@@ -50,7 +50,7 @@ int map_lattice(int nx, int ny, double n, double Da, double Ra, double Pr, doubl
         !(o.s_e > 0) || !(o.s_e < 2) || !(o.s_p > 0) || !(o.s_p < 2) || o.resid_interval < 1 ||
         o.device < -1)
         return LBM_ERR_ARG;
-    if (o.layout != 0) return LBM_ERR_UNSUPPORTED;
+    if (o.layout != 0 && o.layout != 1) return LBM_ERR_UNSUPPORTED;
     memset(L, 0, sizeof(*L));
     const double Uc = o.Ma / sqrt(3.0);
     const double len = (double)nx;
@@ -99,6 +99,56 @@ void free_ctx(lbm_ctx *c)
     delete c;
 }
 
+// The in-place layout leaves the state in its odd-step form after an odd
+// number of steps; every call that reads or writes the state first brings it
+// back to the canonical form (one in-place pass, no allocation).
+int canonical(lbm_ctx *c)
+{
+    if (c->opts.layout == 1 && c->aa_form_o) CK(lbm::launch_aa_normalize(c));
+    return LBM_OK;
+}
+
+double stag_floor(const lbm_ctx *c)
+{
+    if (c->opts.stag_floor >= 0) return c->opts.stag_floor;
+    switch (c->opts.prec) {
+    case LBM_F64: return 0.0;
+    case LBM_F32: return 1e-6;
+    case LBM_F16D: return 1e-2;
+    default: return 1e-1;
+    }
+}
+
+// Copy the 14 distribution planes between host (canonical order, unpadded)
+// and device.  In the in-place layout's canonical form population i of a
+// node lives in plane opp(i).
+int copy_planes(lbm_ctx *c, void *host, bool to_host)
+{
+    const size_t es = c->dist_elem, n = (size_t)c->nx * c->ny;
+    if (c->opts.layout == 0) {
+        if (to_host)
+            CK(cudaMemcpy2DAsync(host, c->nx * es, c->buf.dist[c->cur], c->pitch * es, c->nx * es,
+                                 14 * (size_t)c->ny, cudaMemcpyDeviceToHost, c->stream));
+        else
+            CK(cudaMemcpy2DAsync(c->buf.dist[c->cur], c->pitch * es, host, c->nx * es, c->nx * es,
+                                 14 * (size_t)c->ny, cudaMemcpyHostToDevice, c->stream));
+        return LBM_OK;
+    }
+    static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    for (int i = 0; i < 14; i++) {
+        const int j = i < 9 ? OPP[i] : 9 + OPP[i - 9];
+        char *h = (char *)host + (size_t)i * n * es;
+        char *d = (char *)c->buf.dist[0] + (size_t)j * c->plane * es;
+        if (to_host)
+            CK(cudaMemcpy2DAsync(h, c->nx * es, d, c->pitch * es, c->nx * es, c->ny, cudaMemcpyDeviceToHost,
+                                 c->stream));
+        else
+            CK(cudaMemcpy2DAsync(d, c->pitch * es, h, c->nx * es, c->nx * es, c->ny, cudaMemcpyHostToDevice,
+                                 c->stream));
+    }
+    return LBM_OK;
+}
+
 int ensure_stage(lbm_ctx *c)
 {
     if (c->d_stage) return LBM_OK;
@@ -125,7 +175,8 @@ int init_ctx(lbm_ctx *c)
         CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
         c->own_stream = true;
     }
-    for (int b = 0; b < 2; b++) {
+    const int nbuf = c->opts.layout == 1 ? 1 : 2;   // in-place layout: one buffer
+    for (int b = 0; b < nbuf; b++) {
         CK(cudaMalloc(&c->buf.dist[b], es * 14 * (size_t)c->plane));
         CK(cudaMalloc(&c->buf.tau[b], ts * (size_t)c->plane));
         CK(cudaMemsetAsync(c->buf.dist[b], 0, es * 14 * (size_t)c->plane, c->stream));
@@ -160,6 +211,7 @@ void lbm_default_opts(lbm_opts *o)
     o->layout = 0;
     o->cuda_stream = nullptr;
     o->device = -1;
+    o->stag_floor = -1.0;
 }
 
 int lbm_init(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra, double Pr,
@@ -225,6 +277,7 @@ int lbm_fields(lbm_ctx *c, double *rho, double *ux, double *uy, double *T, doubl
 {
     if (!c) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
+    if (int rc0 = canonical(c)) return rc0;
     int rc = ensure_stage(c);
     if (rc) return rc;
     CK(lbm::launch_fields(c, c->d_stage));
@@ -242,6 +295,7 @@ int lbm_nusselt(lbm_ctx *c, double *hot, double *cold, double *local)
 {
     if (!c) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
+    if (int rc0 = canonical(c)) return rc0;
     CK(lbm::launch_nusselt(c));
     CK(cudaMemcpyAsync(c->h_small, c->d_small, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
     if (local)
@@ -256,6 +310,7 @@ int lbm_residual(lbm_ctx *c, double *resid)
 {
     if (!c) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
+    if (int rc0 = canonical(c)) return rc0;
     if (!c->d_snap) CK(cudaMalloc(&c->d_snap, sizeof(double) * 3 * (size_t)c->nx * c->ny));
     const bool first = !c->have_snap;
     CK(lbm::launch_residual(c, first));
@@ -296,7 +351,7 @@ int lbm_run_to_steady(lbm_ctx *c, double tol, int64_t max_steps, int64_t *steps_
         if (r < best) {
             best = r;
             since_best = 0;
-        } else if (++since_best >= 10) {
+        } else if (++since_best >= 10 && r < stag_floor(c)) {
             why = 1;
             break;
         }
@@ -318,9 +373,9 @@ int lbm_get_state(lbm_ctx *c, void *host, size_t bytes)
 {
     if (!c || !host || bytes != lbm_state_bytes(c)) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
+    if (int rc0 = canonical(c)) return rc0;
     const size_t es = c->dist_elem, ts = c->tau_elem, n = (size_t)c->nx * c->ny;
-    CK(cudaMemcpy2DAsync(host, c->nx * es, c->buf.dist[c->cur], c->pitch * es, c->nx * es, 14 * (size_t)c->ny,
-                         cudaMemcpyDeviceToHost, c->stream));
+    if (int rc0 = copy_planes(c, host, true)) return rc0;
     CK(cudaMemcpy2DAsync((char *)host + 14 * n * es, c->nx * ts, c->buf.tau[c->cur], c->pitch * ts,
                          c->nx * ts, c->ny, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -332,8 +387,8 @@ int lbm_set_state(lbm_ctx *c, const void *host, size_t bytes)
     if (!c || !host || bytes != lbm_state_bytes(c)) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
     const size_t es = c->dist_elem, ts = c->tau_elem, n = (size_t)c->nx * c->ny;
-    CK(cudaMemcpy2DAsync(c->buf.dist[c->cur], c->pitch * es, host, c->nx * es, c->nx * es, 14 * (size_t)c->ny,
-                         cudaMemcpyHostToDevice, c->stream));
+    c->aa_form_o = false;   // the whole state is replaced by a canonical one
+    if (int rc0 = copy_planes(c, const_cast<void *>(host), false)) return rc0;
     CK(cudaMemcpy2DAsync(c->buf.tau[c->cur], c->pitch * ts, (const char *)host + 14 * n * es, c->nx * ts,
                          c->nx * ts, c->ny, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -345,6 +400,7 @@ int lbm_get_state_f64(lbm_ctx *c, double *f, double *g, double *tau)
 {
     if (!c) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
+    if (int rc0 = canonical(c)) return rc0;
     int rc = ensure_stage(c);
     if (rc) return rc;
     CK(lbm::launch_export_f64(c, c->d_stage));
@@ -362,6 +418,7 @@ int lbm_set_state_f64(lbm_ctx *c, const double *f, const double *g, const double
 {
     if (!c) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
+    if (int rc0 = canonical(c)) return rc0;
     int rc = ensure_stage(c);
     if (rc) return rc;
     const size_t n = (size_t)c->nx * c->ny;

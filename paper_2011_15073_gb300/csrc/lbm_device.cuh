@@ -6,6 +6,14 @@
 // written out with those integer coefficients instead of a matrix multiply.
 // The strain-rate double sum of the power-law section collapses to the three
 // non-equilibrium moments that carry second velocity moments (e, p_xx, p_xy).
+//
+// The node physics is written once over a value type V:
+//   double -- FP64 arithmetic (IEEE division, square root and pow);
+//   float  -- FP32 arithmetic with the approximate special-function unit
+//             (rcp/sqrt/ex2/lg2 .approx, about 1-2 ulp);
+//   F2     -- two nodes in one register pair, the arithmetic on the packed
+//             FP32x2 pipe (fma/add/mul .f32x2) and the special functions
+//             per lane as for float.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -17,55 +25,106 @@
 
 namespace lbm {
 
-// Per-case constants in the compute type R (built on the host from
+// ------------------------------------------------------------ packed FP32x2
+struct F2 {
+    float2 v;
+    __host__ __device__ F2() {}
+    __host__ __device__ F2(float a) : v(make_float2(a, a)) {}
+    __host__ __device__ F2(double a) : v(make_float2((float)a, (float)a)) {}
+    __host__ __device__ F2(int a) : v(make_float2((float)a, (float)a)) {}
+    __host__ __device__ F2(float a, float b) : v(make_float2(a, b)) {}
+    __host__ __device__ explicit F2(float2 w) : v(w) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b)
+{
+    return F2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v));  // exact: b * -1 is exact
+}
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
+
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+
+// Special functions.
+__device__ __forceinline__ double vrcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ double vsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ double vpow(double x, double e) { return pow(x, e); }
+
+__device__ __forceinline__ float vrcp(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float vsqrt(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float vexp2(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float vpow(float x, float e) { return vexp2(e * __log2f(x)); }
+
+__device__ __forceinline__ F2 vrcp(F2 a) { return F2(vrcp(a.v.x), vrcp(a.v.y)); }
+__device__ __forceinline__ F2 vsqrt(F2 a) { return F2(vsqrt(a.v.x), vsqrt(a.v.y)); }
+
+// Per-case constants in the compute type V (built on the host from
 // lbm_lattice by make_params below).
-template <class R>
+template <class V>
 struct Phys {
     int nx, ny;
     int64_t pitch;   // elements between rows of a plane
     int64_t plane;   // elements between planes
-    R nu_ref, gamma_scale, gamma1, gamma2, nm1, D_hi;
+    V nu_ref, gamma_scale, gamma1, gamma2, nm1, D_hi;
     int clamp_mode;
-    R eps, inv_eps;
-    R half_eps_invK;   // eps / (2 K) / 2 -> c0 = 1/2 + half_eps_invK * nu
-    R eps_invK;        // eps / K
-    R c1;              // eps F_eps / (2 sqrt K)
-    R eFe_isqK;        // eps F_eps / sqrt K
-    R gbeta, Tm;
-    R omegaT, s_e, s_p;
-    R abb_hot, abb_cold;   // 2 w T_wall for the anti-bounce-back (w = 1/6)
+    V eps, half_eps, inv_eps;
+    V half_eps_invK;   // eps / (4 K): c0 = 1/2 + half_eps_invK * nu
+    V eps_invK;        // eps / K
+    V c1;              // eps F_eps / (2 sqrt K)
+    V eFe_isqK;        // eps F_eps / sqrt K
+    V gbeta, Tm;
+    V omegaT, s_e, s_p;
+    V abb_hot, abb_cold;   // 2 w T_wall for the anti-bounce-back (w = 1/6)
 };
 
 // ------------------------------------------------------------ parameters
-template <class R>
-inline Phys<R> make_params(const lbm_ctx *c)
+template <class V>
+inline Phys<V> make_params(const lbm_ctx *c)
 {
     const lbm_lattice &L = c->lat;
-    Phys<R> p;
+    Phys<V> p;
     p.nx = c->nx;
     p.ny = c->ny;
     p.pitch = c->pitch;
     p.plane = c->plane;
-    p.nu_ref = R(L.nu_ref);
-    p.gamma_scale = R(L.gamma_scale);
-    p.gamma1 = R(L.gamma1);
-    p.gamma2 = R(L.gamma2);
-    p.nm1 = R(L.n - 1.0);
-    p.D_hi = R(pow(L.gamma2, L.n - 1.0));
+    p.nu_ref = V(L.nu_ref);
+    p.gamma_scale = V(L.gamma_scale);
+    p.gamma1 = V(L.gamma1);
+    p.gamma2 = V(L.gamma2);
+    p.nm1 = V(L.n - 1.0);
+    p.D_hi = V(pow(L.gamma2, L.n - 1.0));
     p.clamp_mode = L.clamp_mode;
-    p.eps = R(L.eps);
-    p.inv_eps = R(1.0 / L.eps);
-    p.half_eps_invK = R(L.eps / (4.0 * L.K));
-    p.eps_invK = R(L.eps / L.K);
-    p.c1 = R(L.eps * L.Feps / (2.0 * sqrt(L.K)));
-    p.eFe_isqK = R(L.eps * L.Feps / sqrt(L.K));
-    p.gbeta = R(L.gbeta);
-    p.Tm = R(L.Tm);
-    p.omegaT = R(1.0 / L.tauT);
-    p.s_e = R(L.s_e);
-    p.s_p = R(L.s_p);
-    p.abb_hot = R(2.0 / 6.0 * L.T_hot);
-    p.abb_cold = R(2.0 / 6.0 * L.T_cold);
+    p.eps = V(L.eps);
+    p.half_eps = V(0.5 * L.eps);
+    p.inv_eps = V(1.0 / L.eps);
+    p.half_eps_invK = V(L.eps / (4.0 * L.K));
+    p.eps_invK = V(L.eps / L.K);
+    p.c1 = V(L.eps * L.Feps / (2.0 * sqrt(L.K)));
+    p.eFe_isqK = V(L.eps * L.Feps / sqrt(L.K));
+    p.gbeta = V(L.gbeta);
+    p.Tm = V(L.Tm);
+    p.omegaT = V(1.0 / L.tauT);
+    p.s_e = V(L.s_e);
+    p.s_p = V(L.s_p);
+    p.abb_hot = V(2.0 / 6.0 * L.T_hot);
+    p.abb_cold = V(2.0 / 6.0 * L.T_cold);
     return p;
 }
 
@@ -80,6 +139,7 @@ __host__ __device__ constexpr double rest_g(int i)  // w_i T_m with T_m = 1/2
 }
 
 // ---------------------------------------------------------------- storage
+// ld/st move one node's value; ld2/st2 move the aligned pair (k, k+1) as F2.
 template <int PREC>
 struct Store;
 
@@ -98,6 +158,14 @@ struct Store<LBM_F32> {
     using TauS = float;
     static __device__ __forceinline__ R ld(const S *p, int64_t k, R) { return p[k]; }
     static __device__ __forceinline__ void st(S *p, int64_t k, R v, R) { p[k] = v; }
+    static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float)
+    {
+        return F2(*reinterpret_cast<const float2 *>(p + k));
+    }
+    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float)
+    {
+        *reinterpret_cast<float2 *>(p + k) = v.v;
+    }
 };
 template <>
 struct Store<LBM_BF16D> {
@@ -111,6 +179,15 @@ struct Store<LBM_BF16D> {
     static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest)
     {
         p[k] = __float2bfloat16_rn(v - rest);
+    }
+    static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float rest)
+    {
+        const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(p + k);
+        return F2(__bfloat1622float2(h)) + F2(rest);
+    }
+    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p + k) = __float22bfloat162_rn((v - F2(rest)).v);
     }
 };
 template <>
@@ -126,13 +203,24 @@ struct Store<LBM_F16D> {
     {
         p[k] = __float2half_rn(v - rest);
     }
+    static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float rest)
+    {
+        const __half2 h = *reinterpret_cast<const __half2 *>(p + k);
+        return F2(__half22float2(h)) + F2(rest);
+    }
+    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest)
+    {
+        *reinterpret_cast<__half2 *>(p + k) = __float22half2_rn((v - F2(rest)).v);
+    }
 };
 
-// D = (gamma*)^(n-1) in the compute precision.
-__device__ __forceinline__ double powD(double x, double e) { return pow(x, e); }
-__device__ __forceinline__ float powD(float x, float e) { return exp2f(e * __log2f(x)); }
-
 // ----------------------------------------------------------- pull streaming
+// Opposite directions: 1<->3, 2<->4, 5<->7, 6<->8 (D2Q5 uses the first five).
+__host__ __device__ constexpr int opp(int i)
+{
+    return i == 0 ? 0 : (i <= 4 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5);
+}
+
 // Streamed populations of node (x, y): f_i(x) = f*_i(x - e_i) when the source
 // node exists, otherwise the link crossed a wall halfway between the node and
 // the wall and the population comes back reversed from the node itself
@@ -140,7 +228,9 @@ __device__ __forceinline__ float powD(float x, float e) { return exp2f(e * __log
 // left/right walls and bounce-back on the adiabatic top/bottom walls for the
 // heat).  Velocity order: e0 (0,0), e1 (1,0), e2 (0,1), e3 (-1,0), e4 (0,-1),
 // e5 (1,1), e6 (-1,1), e7 (-1,-1), e8 (1,-1).
-template <int PREC, class R>
+// REV = true reads a state whose post-collision population f*_i(x) is kept
+// in plane opp(i) (the in-place AA layout after an even step).
+template <int PREC, class R, bool REV = false>
 __device__ __forceinline__ void pull(const typename Store<PREC>::S *__restrict__ src,
                                      const Phys<R> &p, int x, int y, R f[9], R g[5])
 {
@@ -148,28 +238,46 @@ __device__ __forceinline__ void pull(const typename Store<PREC>::S *__restrict__
     const int64_t P = p.plane, W = p.pitch;
     const int64_t k = (int64_t)y * W + x;
     const bool xl = x > 0, xr = x < p.nx - 1, yb = y > 0, yt = y < p.ny - 1;
-    f[0] = St::ld(src, 0 * P + k, R(rest_f(0)));
-    f[1] = xl ? St::ld(src, 1 * P + k - 1, R(rest_f(1))) : St::ld(src, 3 * P + k, R(rest_f(3)));
-    f[2] = yb ? St::ld(src, 2 * P + k - W, R(rest_f(2))) : St::ld(src, 4 * P + k, R(rest_f(4)));
-    f[3] = xr ? St::ld(src, 3 * P + k + 1, R(rest_f(3))) : St::ld(src, 1 * P + k, R(rest_f(1)));
-    f[4] = yt ? St::ld(src, 4 * P + k + W, R(rest_f(4))) : St::ld(src, 2 * P + k, R(rest_f(2)));
-    f[5] = (xl && yb) ? St::ld(src, 5 * P + k - W - 1, R(rest_f(5))) : St::ld(src, 7 * P + k, R(rest_f(7)));
-    f[6] = (xr && yb) ? St::ld(src, 6 * P + k - W + 1, R(rest_f(6))) : St::ld(src, 8 * P + k, R(rest_f(8)));
-    f[7] = (xr && yt) ? St::ld(src, 7 * P + k + W + 1, R(rest_f(7))) : St::ld(src, 5 * P + k, R(rest_f(5)));
-    f[8] = (xl && yt) ? St::ld(src, 8 * P + k + W - 1, R(rest_f(8))) : St::ld(src, 6 * P + k, R(rest_f(6)));
+#define PL(i) ((REV ? opp(i) : (i)) * P)
+    f[0] = St::ld(src, PL(0) + k, R(rest_f(0)));
+    f[1] = xl ? St::ld(src, PL(1) + k - 1, R(rest_f(1))) : St::ld(src, PL(3) + k, R(rest_f(3)));
+    f[2] = yb ? St::ld(src, PL(2) + k - W, R(rest_f(2))) : St::ld(src, PL(4) + k, R(rest_f(4)));
+    f[3] = xr ? St::ld(src, PL(3) + k + 1, R(rest_f(3))) : St::ld(src, PL(1) + k, R(rest_f(1)));
+    f[4] = yt ? St::ld(src, PL(4) + k + W, R(rest_f(4))) : St::ld(src, PL(2) + k, R(rest_f(2)));
+    f[5] = (xl && yb) ? St::ld(src, PL(5) + k - W - 1, R(rest_f(5))) : St::ld(src, PL(7) + k, R(rest_f(7)));
+    f[6] = (xr && yb) ? St::ld(src, PL(6) + k - W + 1, R(rest_f(6))) : St::ld(src, PL(8) + k, R(rest_f(8)));
+    f[7] = (xr && yt) ? St::ld(src, PL(7) + k + W + 1, R(rest_f(7))) : St::ld(src, PL(5) + k, R(rest_f(5)));
+    f[8] = (xl && yt) ? St::ld(src, PL(8) + k + W - 1, R(rest_f(8))) : St::ld(src, PL(6) + k, R(rest_f(6)));
     const typename Store<PREC>::S *gs = src + 9 * P;
-    g[0] = St::ld(gs, 0 * P + k, R(rest_g(0)));
-    g[1] = xl ? St::ld(gs, 1 * P + k - 1, R(rest_g(1))) : p.abb_hot - St::ld(gs, 3 * P + k, R(rest_g(3)));
-    g[2] = yb ? St::ld(gs, 2 * P + k - W, R(rest_g(2))) : St::ld(gs, 4 * P + k, R(rest_g(4)));
-    g[3] = xr ? St::ld(gs, 3 * P + k + 1, R(rest_g(3))) : p.abb_cold - St::ld(gs, 1 * P + k, R(rest_g(1)));
-    g[4] = yt ? St::ld(gs, 4 * P + k + W, R(rest_g(4))) : St::ld(gs, 2 * P + k, R(rest_g(2)));
+    g[0] = St::ld(gs, PL(0) + k, R(rest_g(0)));
+    g[1] = xl ? St::ld(gs, PL(1) + k - 1, R(rest_g(1))) : p.abb_hot - St::ld(gs, PL(3) + k, R(rest_g(3)));
+    g[2] = yb ? St::ld(gs, PL(2) + k - W, R(rest_g(2))) : St::ld(gs, PL(4) + k, R(rest_g(4)));
+    g[3] = xr ? St::ld(gs, PL(3) + k + 1, R(rest_g(3))) : p.abb_cold - St::ld(gs, PL(1) + k, R(rest_g(1)));
+    g[4] = yt ? St::ld(gs, PL(4) + k + W, R(rest_g(4))) : St::ld(gs, PL(2) + k, R(rest_g(2)));
+#undef PL
+}
+
+// Pairs of nodes along x for the two-nodes-per-thread paths.  A value taken
+// from x - 1 is the previous lane's upper element (lane 0 supplies its own
+// halo value); one taken from x + 1 is the next lane's lower element.
+__device__ __forceinline__ F2 from_left(F2 a, float halo, int lane)
+{
+    float l = __shfl_up_sync(0xffffffffu, a.v.y, 1);
+    if (lane == 0) l = halo;
+    return F2(l, a.v.x);
+}
+__device__ __forceinline__ F2 from_right(F2 a, float halo, int lane)
+{
+    float r = __shfl_down_sync(0xffffffffu, a.v.x, 1);
+    if (lane == 31) r = halo;
+    return F2(a.v.y, r);
 }
 
 // ------------------------------------------------------ macroscopic moments
-template <class R>
+template <class V>
 struct Macro {
-    R rho, irho, jx, jy, T, ux, uy, Fx, Fy, nu_prev;
-    R nu;  // apparent viscosity chosen by the collision (set by collide)
+    V rho, irho, T, ux, uy, Fx, Fy, nu_prev;
+    V nu;  // apparent viscosity chosen by the collision (set by collide)
 };
 
 // Density and temperature (Eqs. macro_fluid_density and the D2Q5 zeroth
@@ -178,103 +286,114 @@ struct Macro {
 // u = v / (c0 + sqrt(c0^2 + c1 |v|)), c0 = (1 + eps nu / (2K)) / 2, with the
 // apparent viscosity of the lagged relaxation time; then the total force
 // F = -eps nu u / K - eps F_eps |u| u / sqrt K + eps G.
-template <class R>
-__device__ __forceinline__ Macro<R> macro(const Phys<R> &p, const R f[9], const R g[5], R tau_prev)
+template <class V>
+__device__ __forceinline__ Macro<V> macro(const Phys<V> &p, const V f[9], const V g[5], V tau_prev)
 {
-    Macro<R> m;
-    const R sax = (f[1] + f[2]) + (f[3] + f[4]);
-    const R sdg = (f[5] + f[6]) + (f[7] + f[8]);
+    Macro<V> m;
+    const V sax = (f[1] + f[2]) + (f[3] + f[4]);
+    const V sdg = (f[5] + f[6]) + (f[7] + f[8]);
     m.rho = f[0] + sax + sdg;
-    m.jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    m.jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const V jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const V jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
     m.T = g[0] + (g[1] + g[2]) + (g[3] + g[4]);
-    const R Gy = p.gbeta * (m.T - p.Tm);
-    m.irho = R(1) / m.rho;
-    const R vx = m.jx * m.irho;
-    const R vy = m.jy * m.irho + R(0.5) * p.eps * Gy;
-    m.nu_prev = (tau_prev - R(0.5)) * R(1.0 / 3.0);
-    const R c0 = R(0.5) + p.half_eps_invK * m.nu_prev;
-    const R vmag = sqrt(vx * vx + vy * vy);
-    const R iden = R(1) / (c0 + sqrt(c0 * c0 + p.c1 * vmag));
+    const V Gy = p.gbeta * (m.T - p.Tm);
+    m.irho = vrcp(m.rho);
+    const V vx = jx * m.irho;
+    const V vy = vfma(p.half_eps, Gy, jy * m.irho);
+    m.nu_prev = (tau_prev - V(0.5)) * V(1.0 / 3.0);
+    const V c0 = vfma(p.half_eps_invK, m.nu_prev, V(0.5));
+    const V vmag = vsqrt(vfma(vx, vx, vy * vy));
+    const V iden = vrcp(c0 + vsqrt(vfma(c0, c0, p.c1 * vmag)));
     m.ux = vx * iden;
     m.uy = vy * iden;
-    const R umag = sqrt(m.ux * m.ux + m.uy * m.uy);
-    const R drag = -(p.eps_invK * m.nu_prev + p.eFe_isqK * umag);
+    const V umag = vmag * iden;  // |u| = |v| / den
+    const V drag = -vfma(p.eps_invK, m.nu_prev, p.eFe_isqK * umag);
     m.Fx = drag * m.ux;
-    m.Fy = drag * m.uy + p.eps * Gy;
+    m.Fy = vfma(drag, m.uy, p.eps * Gy);
     return m;
 }
 
 // Apparent-viscosity factor of Eq. (MPL) for the non-dimensional shear rate.
 template <class R>
-__device__ __forceinline__ R apparent(const Phys<R> &p, R gs)
+__device__ __forceinline__ R apparent_s(int mode, R gs, R g1, R g2, R nm1, R Dhi)
 {
-    if (p.clamp_mode == 0)
-        return gs < p.gamma1 ? R(1) : (gs <= p.gamma2 ? powD(gs, p.nm1) : p.D_hi);
-    const R gc = gs < p.gamma1 ? p.gamma1 : (gs > p.gamma2 ? p.gamma2 : gs);
-    return powD(gc, p.nm1);
+    if (mode == 0) return gs < g1 ? R(1) : (gs <= g2 ? vpow(gs, nm1) : Dhi);
+    const R gc = gs < g1 ? g1 : (gs > g2 ? g2 : gs);
+    return vpow(gc, nm1);
+}
+template <class V>
+__device__ __forceinline__ V apparent(const Phys<V> &p, V gs)
+{
+    return apparent_s(p.clamp_mode, gs, p.gamma1, p.gamma2, p.nm1, p.D_hi);
+}
+template <>
+__device__ __forceinline__ F2 apparent(const Phys<F2> &p, F2 gs)
+{
+    return F2(apparent_s(p.clamp_mode, gs.v.x, p.gamma1.v.x, p.gamma2.v.x, p.nm1.v.x, p.D_hi.v.x),
+              apparent_s(p.clamp_mode, gs.v.y, p.gamma1.v.x, p.gamma2.v.x, p.nm1.v.x, p.D_hi.v.x));
 }
 
 // Full node update in place: f, g become the post-collision populations.
 // Returns the new relaxation time; m receives the macroscopic moments and the
 // apparent lattice viscosity of this collision.
-template <class R>
-__device__ __forceinline__ R collide(const Phys<R> &p, R f[9], R g[5], R tau_prev, Macro<R> &m)
+template <class V>
+__device__ __forceinline__ V collide(const Phys<V> &p, V f[9], V g[5], V tau_prev, Macro<V> &m)
 {
-    m = macro<R>(p, f, g, tau_prev);
-    const R rho = m.rho, ux = m.ux, uy = m.uy;
+    m = macro<V>(p, f, g, tau_prev);
+    const V rho = m.rho, ux = m.ux, uy = m.uy;
     // raw moments
-    const R sax = (f[1] + f[2]) + (f[3] + f[4]);
-    const R sdg = (f[5] + f[6]) + (f[7] + f[8]);
-    const R e = R(-4) * f[0] - sax + R(2) * sdg;
-    const R ep = R(4) * f[0] - R(2) * sax + sdg;
-    const R qx = R(-2) * (f[1] - f[3]) + ((f[5] - f[6]) + (f[8] - f[7]));
-    const R qy = R(-2) * (f[2] - f[4]) + ((f[5] + f[6]) - (f[7] + f[8]));
-    const R pxx = (f[1] + f[3]) - (f[2] + f[4]);
-    const R pxy = (f[5] + f[7]) - (f[6] + f[8]);
+    const V sax = (f[1] + f[2]) + (f[3] + f[4]);
+    const V sdg = (f[5] + f[6]) + (f[7] + f[8]);
+    const V e = vfma(V(2), sdg, vfma(V(-4), f[0], -sax));
+    const V ep = vfma(V(4), f[0], vfma(V(-2), sax, sdg));
+    const V qx = vfma(V(-2), f[1] - f[3], (f[5] - f[6]) + (f[8] - f[7]));
+    const V qy = vfma(V(-2), f[2] - f[4], (f[5] + f[6]) - (f[7] + f[8]));
+    const V pxx = (f[1] + f[3]) - (f[2] + f[4]);
+    const V pxy = (f[5] + f[7]) - (f[6] + f[8]);
     // equilibria
-    const R u2e = (ux * ux + uy * uy) * p.inv_eps;
-    const R e_eq = rho * (R(-2) + R(3) * u2e);
-    const R ep_eq = rho * (R(1) - R(3) * u2e);
-    const R pxx_eq = rho * (ux * ux - uy * uy) * p.inv_eps;
-    const R pxy_eq = rho * ux * uy * p.inv_eps;
+    const V rie = rho * p.inv_eps;
+    const V u2e3 = V(3) * vfma(ux, ux, uy * uy) * p.inv_eps;
+    const V e_eq = vfma(rho, u2e3, V(-2) * rho);
+    const V ep_eq = rho - rho * u2e3;
+    const V pxx_eq = rie * vfma(ux, ux, -(uy * uy));
+    const V pxy_eq = rie * (ux * uy);
     // strain rate from the non-equilibrium moments with the lagged tau:
     // gamma_xx,yy = -3/(2 rho) (s1 e_neq / 6 +- w pxx_neq / 2),
     // gamma_xy = -3/(2 rho) w pxy_neq, |gamma| = sqrt(2 gamma:gamma)
-    const R wp = R(1) / tau_prev;
-    const R A = R(1.4 / 6.0) * (e - e_eq);
-    const R B = R(0.5) * wp * (pxx - pxx_eq);
-    const R C = wp * (pxy - pxy_eq);
-    const R gam = R(3) * m.irho * sqrt(A * A + B * B + C * C);
-    const R nu = p.nu_ref * apparent<R>(p, gam * p.gamma_scale);
-    const R tau = R(3) * nu + R(0.5);
-    const R w = R(1) / tau;
+    //          = (3 / rho) sqrt(A^2 + B^2 + C^2)
+    const V wp = vrcp(tau_prev);
+    const V A = V(1.4 / 6.0) * (e - e_eq);
+    const V B = V(0.5) * wp * (pxx - pxx_eq);
+    const V C = wp * (pxy - pxy_eq);
+    const V gam = V(3) * m.irho * vsqrt(vfma(A, A, vfma(B, B, C * C)));
+    const V nu = p.nu_ref * apparent<V>(p, gam * p.gamma_scale);
+    const V tau = vfma(V(3), nu, V(0.5));
+    const V w = vrcp(tau);
     m.nu = nu;
     // forcing moments (M applied to the velocity-space porous force term)
-    const R uF = ux * m.Fx + uy * m.Fy;
-    const R Fe = R(6) * rho * uF * p.inv_eps;
-    const R Fxx = R(2) * rho * (ux * m.Fx - uy * m.Fy) * p.inv_eps;
-    const R Fxy = rho * (ux * m.Fy + uy * m.Fx) * p.inv_eps;
+    const V Fe = V(6) * rie * vfma(ux, m.Fx, uy * m.Fy);
+    const V Fxx = V(2) * rie * vfma(ux, m.Fx, -(uy * m.Fy));
+    const V Fxy = rie * vfma(ux, m.Fy, uy * m.Fx);
     // post-collision moments, m* = m - S (m - m_eq) + (I - S/2) F
-    const R es = e - R(1.4) * (e - e_eq) + R(0.3) * Fe;
-    const R eps_s = ep - R(1.4) * (ep - ep_eq) - R(0.3) * Fe;
-    const R jxs = rho * (ux + R(0.5) * m.Fx);
-    const R jys = rho * (uy + R(0.5) * m.Fy);
-    const R qxs = qx - R(1.2) * (qx + rho * ux) - R(0.4) * rho * m.Fx;
-    const R qys = qy - R(1.2) * (qy + rho * uy) - R(0.4) * rho * m.Fy;
-    const R hw = R(1) - R(0.5) * w;
-    const R pxxs = pxx - w * (pxx - pxx_eq) + hw * Fxx;
-    const R pxys = pxy - w * (pxy - pxy_eq) + hw * Fxy;
+    const V es = vfma(V(0.3), Fe, vfma(V(-1.4), e - e_eq, e));
+    const V eps_s = vfma(V(-0.3), Fe, vfma(V(-1.4), ep - ep_eq, ep));
+    const V jxs = rho * vfma(V(0.5), m.Fx, ux);
+    const V jys = rho * vfma(V(0.5), m.Fy, uy);
+    const V qxs = vfma(V(-0.4) * rho, m.Fx, vfma(V(-1.2), vfma(rho, ux, qx), qx));
+    const V qys = vfma(V(-0.4) * rho, m.Fy, vfma(V(-1.2), vfma(rho, uy, qy), qy));
+    const V hw = vfma(V(-0.5), w, V(1));
+    const V pxxs = vfma(hw, Fxx, vfma(-w, pxx - pxx_eq, pxx));
+    const V pxys = vfma(hw, Fxy, vfma(-w, pxy - pxy_eq, pxy));
     // f* = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m*
-    const R a0 = rho * R(1.0 / 9.0), a1 = es * R(1.0 / 36.0), a2 = eps_s * R(1.0 / 36.0);
-    const R a3 = jxs * R(1.0 / 6.0), a4 = qxs * R(1.0 / 12.0);
-    const R a5 = jys * R(1.0 / 6.0), a6 = qys * R(1.0 / 12.0);
-    const R a7 = pxxs * R(0.25), a8 = pxys * R(0.25);
-    const R b_ax = a0 - a1 - R(2) * a2;  // common part of f1..f4
-    const R b_dg = a0 + R(2) * a1 + a2;  // common part of f5..f8
-    const R xa = a3 - R(2) * a4, ya = a5 - R(2) * a6;
-    const R xd = a3 + a4, yd = a5 + a6;
-    f[0] = a0 - R(4) * a1 + R(4) * a2;
+    const V a0 = rho * V(1.0 / 9.0), a1 = es * V(1.0 / 36.0), a2 = eps_s * V(1.0 / 36.0);
+    const V a3 = jxs * V(1.0 / 6.0), a4 = qxs * V(1.0 / 12.0);
+    const V a5 = jys * V(1.0 / 6.0), a6 = qys * V(1.0 / 12.0);
+    const V a7 = pxxs * V(0.25), a8 = pxys * V(0.25);
+    const V b_ax = vfma(V(-2), a2, a0 - a1);  // common part of f1..f4
+    const V b_dg = vfma(V(2), a1, a0 + a2);   // common part of f5..f8
+    const V xa = vfma(V(-2), a4, a3), ya = vfma(V(-2), a6, a5);
+    const V xd = a3 + a4, yd = a5 + a6;
+    f[0] = vfma(V(4), a2 - a1, a0);
     f[1] = b_ax + xa + a7;
     f[2] = b_ax + ya - a7;
     f[3] = b_ax - xa + a7;
@@ -284,22 +403,23 @@ __device__ __forceinline__ R collide(const Phys<R> &p, R f[9], R g[5], R tau_pre
     f[7] = b_dg - xd - yd + a8;
     f[8] = b_dg + xd - yd - a8;
     // thermal MRT: n = N g, n* = n - S_T (n - n_eq), n_eq = (T, T u, -2T/3, 0)
-    const R T = m.T;
-    const R n1 = g[1] - g[3], n2 = g[2] - g[4];
-    const R n3 = R(-4) * g[0] + (g[1] + g[2]) + (g[3] + g[4]);
-    const R n4 = (g[1] + g[3]) - (g[2] + g[4]);
-    const R n1s = n1 - p.omegaT * (n1 - T * ux);
-    const R n2s = n2 - p.omegaT * (n2 - T * uy);
-    const R n3s = n3 - p.s_e * (n3 + R(2.0 / 3.0) * T);
-    const R n4s = n4 - p.s_p * n4;
+    const V T = m.T;
+    const V n1 = g[1] - g[3], n2 = g[2] - g[4];
+    const V n3 = vfma(V(-4), g[0], (g[1] + g[2]) + (g[3] + g[4]));
+    const V n4 = (g[1] + g[3]) - (g[2] + g[4]);
+    const V n1s = vfma(-p.omegaT, vfma(-T, ux, n1), n1);
+    const V n2s = vfma(-p.omegaT, vfma(-T, uy, n2), n2);
+    const V n3s = vfma(-p.s_e, vfma(V(2.0 / 3.0), T, n3), n3);
+    const V n4s = vfma(-p.s_p, n4, n4);
     // g* = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4) n*
-    const R t0 = T * R(0.2), t3 = n3s * R(0.05), t4 = n4s * R(0.25);
-    const R h1 = n1s * R(0.5), h2 = n2s * R(0.5);
-    g[0] = t0 - n3s * R(0.2);
-    g[1] = t0 + h1 + t3 + t4;
-    g[2] = t0 + h2 + t3 - t4;
-    g[3] = t0 - h1 + t3 + t4;
-    g[4] = t0 - h2 + t3 - t4;
+    const V t0 = T * V(0.2), t3 = n3s * V(0.05), t4 = n4s * V(0.25);
+    const V h1 = n1s * V(0.5), h2 = n2s * V(0.5);
+    const V t03 = t0 + t3;
+    g[0] = vfma(V(-0.2), n3s, t0);
+    g[1] = t03 + h1 + t4;
+    g[2] = t03 + h2 - t4;
+    g[3] = t03 - h1 + t4;
+    g[4] = t03 - h2 - t4;
     return tau;
 }
 

@@ -45,6 +45,7 @@ struct lbm_ctx {
     int n_part = 0;
     double *d_nuloc = nullptr;   // local hot-wall Nu [ny]
     bool have_snap = false;
+    bool aa_form_o = false;      // in-place layout: state in the odd-step form
     int64_t steps = 0;
 };
 
@@ -59,6 +60,10 @@ cudaError_t launch_nusselt(lbm_ctx *c);  // -> d_small[0..1], d_nuloc
 cudaError_t launch_residual(lbm_ctx *c, bool first);  // -> d_small[2..5]
 cudaError_t launch_import_f64(lbm_ctx *c, const double *d_src15, int mask);
 cudaError_t launch_export_f64(lbm_ctx *c, double *d_dst15);
+// In-place (AA) layout (lbm_aa.cu): one step, and the conversion of the
+// odd-step form back to the canonical one (no-op if already canonical).
+cudaError_t launch_aa_step(lbm_ctx *c);
+cudaError_t launch_aa_normalize(lbm_ctx *c);
 int residual_blocks(const lbm_ctx *c);
 
 }  // namespace lbm

@@ -4,6 +4,7 @@
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "lbm_step.cuh"
 
 namespace lbm {
 
@@ -26,32 +27,31 @@ __global__ void init_kernel(typename Store<PREC>::S *__restrict__ dist,
     tau[k] = typename St::TauS(tau0);
 }
 
-// One time step of the whole cavity: pull streaming with the wall rules,
-// collision, store to the other buffer.  One thread per node.
+// One time step of the whole cavity (pull scheme, two buffers); the node
+// and tile bodies are in lbm_step.cuh.
 template <int PREC>
 __global__ void __launch_bounds__(128)
 step_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
             const typename Store<PREC>::TauS *__restrict__ tsrc, typename Store<PREC>::TauS *__restrict__ tdst,
             Phys<typename Store<PREC>::R> p)
 {
-    using St = Store<PREC>;
-    using R = typename St::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= p.nx) return;
-    const int64_t k = (int64_t)y * p.pitch + x;
-    R f[9], g[5];
-    pull<PREC, R>(src, p, x, y, f, g);
-    Macro<R> m;
-    const R tau = collide<R>(p, f, g, R(tsrc[k]), m);
-#pragma unroll
-    for (int i = 0; i < 9; i++) St::st(dst, i * p.plane + k, f[i], R(rest_f(i)));
-#pragma unroll
-    for (int i = 0; i < 5; i++) St::st(dst + 9 * p.plane, i * p.plane + k, g[i], R(rest_g(i)));
-    tdst[k] = typename St::TauS(tau);
+    step_node<PREC, typename Store<PREC>::R>(src, dst, tsrc, tdst, p, x, y);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(128)
+step2_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
+             const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
+{
+    step2_tile<PREC>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
 }
 
 // Streamed macroscopic fields: rho, u_x, u_y, T, nu -> out[5][ny][nx].
-template <int PREC>
+// REV: the state is in the in-place layout's canonical form (f*_i in plane
+// opp(i)).
+template <int PREC, bool REV>
 __global__ void fields_kernel(const typename Store<PREC>::S *__restrict__ src,
                               const typename Store<PREC>::TauS *__restrict__ tsrc,
                               Phys<typename Store<PREC>::R> p, double *__restrict__ out)
@@ -63,7 +63,7 @@ __global__ void fields_kernel(const typename Store<PREC>::S *__restrict__ src,
     const int64_t k = (int64_t)y * p.pitch + x;
     const int64_t q = (int64_t)y * p.nx + x, n = (int64_t)p.nx * p.ny;
     R f[9], g[5];
-    pull<PREC, R>(src, p, x, y, f, g);
+    pull<PREC, R, REV>(src, p, x, y, f, g);
     Macro<R> m;
     collide<R>(p, f, g, R(tsrc[k]), m);
     out[q] = double(m.rho);
@@ -91,20 +91,20 @@ __device__ double block_sum(double v, double *sh)
 }
 
 // Streamed temperature of node (x, y) in FP64 (thermal part of the pull).
-template <int PREC>
+template <int PREC, bool REV>
 __device__ double streamed_T(const typename Store<PREC>::S *__restrict__ src,
                              const Phys<typename Store<PREC>::R> &p, int x, int y)
 {
     using R = typename Store<PREC>::R;
     R f[9], g[5];
-    pull<PREC, R>(src, p, x, y, f, g);
+    pull<PREC, R, REV>(src, p, x, y, f, g);
     return (double)g[0] + (double)g[1] + (double)g[2] + (double)g[3] + (double)g[4];
 }
 
 // Wall Nusselt numbers: one block; row j of the hot wall gets
 // Nu_j = -L (9 theta_0 - theta_1 - 8) / 3, the cold wall the outward
 // L (9 theta_{nx-1} - theta_{nx-2}) / 3, theta = (T - T_c) / (T_h - T_c).
-template <int PREC>
+template <int PREC, bool REV>
 __global__ void __launch_bounds__(256)
 nusselt_kernel(const typename Store<PREC>::S *__restrict__ src, Phys<typename Store<PREC>::R> p,
                double T_hot, double T_cold, double Lw, double *__restrict__ small,
@@ -114,10 +114,10 @@ nusselt_kernel(const typename Store<PREC>::S *__restrict__ src, Phys<typename St
     const double dT = T_hot - T_cold;
     double sh_hot = 0.0, sh_cold = 0.0;
     for (int j = threadIdx.x; j < p.ny; j += blockDim.x) {
-        const double t0 = (streamed_T<PREC>(src, p, 0, j) - T_cold) / dT;
-        const double t1 = (streamed_T<PREC>(src, p, 1, j) - T_cold) / dT;
-        const double ta = (streamed_T<PREC>(src, p, p.nx - 1, j) - T_cold) / dT;
-        const double tb = (streamed_T<PREC>(src, p, p.nx - 2, j) - T_cold) / dT;
+        const double t0 = (streamed_T<PREC, REV>(src, p, 0, j) - T_cold) / dT;
+        const double t1 = (streamed_T<PREC, REV>(src, p, 1, j) - T_cold) / dT;
+        const double ta = (streamed_T<PREC, REV>(src, p, p.nx - 1, j) - T_cold) / dT;
+        const double tb = (streamed_T<PREC, REV>(src, p, p.nx - 2, j) - T_cold) / dT;
         const double nh = -Lw * (9.0 * t0 - t1 - 8.0) / 3.0;
         const double nc = Lw * (9.0 * ta - tb) / 3.0;
         nuloc[j] = nh;
@@ -136,7 +136,7 @@ nusselt_kernel(const typename Store<PREC>::S *__restrict__ src, Phys<typename St
 // grid-stride set of nodes, sum (phi - phi_prev)^2 and sum phi^2 for
 // phi in {u_x, u_y, T} plus a count of non-finite values, and writes its
 // seven partial sums to part[blockIdx.x * 8 + 0..6].  The snapshot is updated.
-template <int PREC>
+template <int PREC, bool REV>
 __global__ void __launch_bounds__(256)
 residual_kernel(const typename Store<PREC>::S *__restrict__ src,
                 const typename Store<PREC>::TauS *__restrict__ tsrc, Phys<typename Store<PREC>::R> p,
@@ -150,7 +150,7 @@ residual_kernel(const typename Store<PREC>::S *__restrict__ src,
          q += (int64_t)gridDim.x * blockDim.x) {
         const int y = (int)(q / p.nx), x = (int)(q - (int64_t)y * p.nx);
         R f[9], g[5];
-        pull<PREC, R>(src, p, x, y, f, g);
+        pull<PREC, R, REV>(src, p, x, y, f, g);
         const Macro<R> m = macro<R>(p, f, g, R(tsrc[(int64_t)y * p.pitch + x]));
         const double v[3] = {double(m.ux), double(m.uy), double(m.T)};
         for (int c = 0; c < 3; c++) {
@@ -190,7 +190,7 @@ residual_final_kernel(const double *__restrict__ part, int nb, double *__restric
 }
 
 // FP64 staging [15][ny][nx] (f0..f8, g0..g4, tau) <-> device state.
-template <int PREC>
+template <int PREC, bool REV>
 __global__ void import_kernel(const double *__restrict__ in, typename Store<PREC>::S *__restrict__ dist,
                               typename Store<PREC>::TauS *__restrict__ tau, int nx, int ny,
                               int64_t pitch, int64_t plane, int mask)
@@ -201,14 +201,19 @@ __global__ void import_kernel(const double *__restrict__ in, typename Store<PREC
     if (x >= nx) return;
     const int64_t k = (int64_t)y * pitch + x, q = (int64_t)y * nx + x, n = (int64_t)nx * ny;
     if (mask & 1)
-        for (int i = 0; i < 9; i++) St::st(dist, i * plane + k, R(in[i * n + q]), R(rest_f(i)));
+        for (int i = 0; i < 9; i++) {
+            const int j = REV ? opp(i) : i;
+            St::st(dist, j * plane + k, R(in[i * n + q]), R(rest_f(j)));
+        }
     if (mask & 2)
-        for (int i = 0; i < 5; i++)
-            St::st(dist + 9 * plane, i * plane + k, R(in[(9 + i) * n + q]), R(rest_g(i)));
+        for (int i = 0; i < 5; i++) {
+            const int j = REV ? opp(i) : i;
+            St::st(dist + 9 * plane, j * plane + k, R(in[(9 + i) * n + q]), R(rest_g(j)));
+        }
     if (mask & 4) tau[k] = typename St::TauS(in[14 * n + q]);
 }
 
-template <int PREC>
+template <int PREC, bool REV>
 __global__ void export_kernel(double *__restrict__ out, const typename Store<PREC>::S *__restrict__ dist,
                               const typename Store<PREC>::TauS *__restrict__ tau, int nx, int ny,
                               int64_t pitch, int64_t plane)
@@ -218,9 +223,14 @@ __global__ void export_kernel(double *__restrict__ out, const typename Store<PRE
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= nx) return;
     const int64_t k = (int64_t)y * pitch + x, q = (int64_t)y * nx + x, n = (int64_t)nx * ny;
-    for (int i = 0; i < 9; i++) out[i * n + q] = double(St::ld(dist, i * plane + k, R(rest_f(i))));
-    for (int i = 0; i < 5; i++)
-        out[(9 + i) * n + q] = double(St::ld(dist + 9 * plane, i * plane + k, R(rest_g(i))));
+    for (int i = 0; i < 9; i++) {
+        const int j = REV ? opp(i) : i;
+        out[i * n + q] = double(St::ld(dist, j * plane + k, R(rest_f(j))));
+    }
+    for (int i = 0; i < 5; i++) {
+        const int j = REV ? opp(i) : i;
+        out[(9 + i) * n + q] = double(St::ld(dist + 9 * plane, j * plane + k, R(rest_g(j))));
+    }
     out[14 * n + q] = double(tau[k]);
 }
 
@@ -240,6 +250,7 @@ static cudaError_t init_t(lbm_ctx *c)
 {
     using St = Store<PREC>;
     for (int b = 0; b < 2; b++)
+        if (c->buf.dist[b])
         init_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
             (typename St::S *)c->buf.dist[b], (typename St::TauS *)c->buf.tau[b],
             make_params<typename St::R>(c), c->lat.tau0, 0.5 * (c->lat.T_hot + c->lat.T_cold));
@@ -250,11 +261,18 @@ template <int PREC>
 static cudaError_t step_t(lbm_ctx *c)
 {
     using St = Store<PREC>;
+    if (c->opts.layout == 1) return launch_aa_step(c);
     const int s = c->cur, d = 1 - c->cur;
-    step_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
-        (const typename St::S *)c->buf.dist[s], (typename St::S *)c->buf.dist[d],
-        (const typename St::TauS *)c->buf.tau[s], (typename St::TauS *)c->buf.tau[d],
-        make_params<typename St::R>(c));
+    if constexpr (PREC == LBM_F64) {
+        step_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
+            (const typename St::S *)c->buf.dist[s], (typename St::S *)c->buf.dist[d],
+            (const typename St::TauS *)c->buf.tau[s], (typename St::TauS *)c->buf.tau[d],
+            make_params<typename St::R>(c));
+    } else {
+        step2_kernel<PREC><<<node_grid(c, 256), 128, 0, c->stream>>>(
+            (const typename St::S *)c->buf.dist[s], (typename St::S *)c->buf.dist[d],
+            (const float *)c->buf.tau[s], (float *)c->buf.tau[d], make_params<float>(c), make_params<F2>(c));
+    }
     c->cur = d;
     return cudaGetLastError();
 }
@@ -263,7 +281,8 @@ template <int PREC>
 static cudaError_t fields_t(lbm_ctx *c, double *out)
 {
     using St = Store<PREC>;
-    fields_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
+    auto *kern = c->opts.layout == 1 ? fields_kernel<PREC, true> : fields_kernel<PREC, false>;
+    kern<<<node_grid(c, 128), 128, 0, c->stream>>>(
         (const typename St::S *)c->buf.dist[c->cur], (const typename St::TauS *)c->buf.tau[c->cur],
         make_params<typename St::R>(c), out);
     return cudaGetLastError();
@@ -273,7 +292,8 @@ template <int PREC>
 static cudaError_t nusselt_t(lbm_ctx *c)
 {
     using St = Store<PREC>;
-    nusselt_kernel<PREC><<<1, 256, 0, c->stream>>>(
+    auto *kern = c->opts.layout == 1 ? nusselt_kernel<PREC, true> : nusselt_kernel<PREC, false>;
+    kern<<<1, 256, 0, c->stream>>>(
         (const typename St::S *)c->buf.dist[c->cur], make_params<typename St::R>(c), c->lat.T_hot,
         c->lat.T_cold, c->lat.L, c->d_small, c->d_nuloc);
     return cudaGetLastError();
@@ -284,7 +304,8 @@ static cudaError_t residual_t(lbm_ctx *c, bool first)
 {
     using St = Store<PREC>;
     const int nb = residual_blocks(c);
-    residual_kernel<PREC><<<nb, 256, 0, c->stream>>>(
+    auto *kern = c->opts.layout == 1 ? residual_kernel<PREC, true> : residual_kernel<PREC, false>;
+    kern<<<nb, 256, 0, c->stream>>>(
         (const typename St::S *)c->buf.dist[c->cur], (const typename St::TauS *)c->buf.tau[c->cur],
         make_params<typename St::R>(c), c->d_snap, c->d_part, first ? 1 : 0);
     residual_final_kernel<<<1, 256, 0, c->stream>>>(c->d_part, nb, c->d_small);
@@ -295,7 +316,8 @@ template <int PREC>
 static cudaError_t import_t(lbm_ctx *c, const double *in, int mask)
 {
     using St = Store<PREC>;
-    import_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
+    auto *kern = c->opts.layout == 1 ? import_kernel<PREC, true> : import_kernel<PREC, false>;
+    kern<<<node_grid(c, 128), 128, 0, c->stream>>>(
         in, (typename St::S *)c->buf.dist[c->cur], (typename St::TauS *)c->buf.tau[c->cur], c->nx, c->ny,
         c->pitch, c->plane, mask);
     return cudaGetLastError();
@@ -305,7 +327,8 @@ template <int PREC>
 static cudaError_t export_t(lbm_ctx *c, double *out)
 {
     using St = Store<PREC>;
-    export_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
+    auto *kern = c->opts.layout == 1 ? export_kernel<PREC, true> : export_kernel<PREC, false>;
+    kern<<<node_grid(c, 128), 128, 0, c->stream>>>(
         out, (const typename St::S *)c->buf.dist[c->cur], (const typename St::TauS *)c->buf.tau[c->cur],
         c->nx, c->ny, c->pitch, c->plane);
     return cudaGetLastError();

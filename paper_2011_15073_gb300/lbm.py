@@ -38,7 +38,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("Ma", ctypes.c_double), ("clamp_mode", ctypes.c_int),
                 ("porous_model", ctypes.c_int), ("s_e", ctypes.c_double), ("s_p", ctypes.c_double),
                 ("resid_interval", ctypes.c_int), ("layout", ctypes.c_int),
-                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
+                ("stag_floor", ctypes.c_double)]
 
 
 class Lattice(ctypes.Structure):

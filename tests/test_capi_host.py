@@ -48,7 +48,7 @@ def test_default_opts(L):
     o = lbm.default_opts()
     assert (o.prec, o.Ma, o.clamp_mode, o.porous_model, o.s_e, o.s_p, o.resid_interval, o.layout) == \
         (0, 0.1, 0, 1, 1.5, 1.5, 1000, 0)
-    assert not o.cuda_stream and o.device == -1
+    assert not o.cuda_stream and o.device == -1 and o.stag_floor == -1.0
 
 
 @pytest.mark.parametrize("args,code", [
@@ -73,7 +73,7 @@ def test_init_rejects_bad_arguments(L, args, code):
 
 @pytest.mark.parametrize("field,value,code", [
     ("prec", 7, -1), ("Ma", 0.0, -1), ("clamp_mode", 2, -1), ("porous_model", 3, -1),
-    ("s_e", 2.5, -1), ("s_p", 0.0, -1), ("resid_interval", 0, -1), ("layout", 1, -7),
+    ("s_e", 2.5, -1), ("s_p", 0.0, -1), ("resid_interval", 0, -1), ("layout", 2, -7),
     ("device", -2, -1),
 ])
 def test_init_rejects_bad_options(L, field, value, code):

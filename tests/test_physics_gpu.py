@@ -1,0 +1,64 @@
+"""Physics checks of the CUDA path at steady state (GPU, FP64 storage).
+
+These cover what the paper states about its results and what holds for any
+converged cavity.  They are not parity tests.  They use the continuous clamp
+of the power law (clamp_mode 1): with the literal law, nodes whose shear rate
+sits at gamma_1 switch branch from step to step and the flow settles into a
+small limit cycle instead of a steady state.
+* Trends (results section and conclusion): the average Nusselt number falls
+  as n grows, rises with Da, and rises with Ra.
+* Energy balance: at steady state the heat entering through the hot wall
+  leaves through the cold wall, so the hot- and cold-wall averages agree to
+  within the discretisation error.
+* Centro-symmetry of the steady cavity: theta(x, y) = 1 - theta(L-x, L-y) and
+  u(x, y) = -u(L-x, L-y), broken only by compressibility (O(Ma^2) = 1e-2 at
+  Ma = 0.1): the test allows 5e-3 on theta and 5 % of max|u| on u.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+N = 48
+
+
+def steady(lbm, n, Da, Ra, Pr=6.2, porous_model=0, porosity=1.0):
+    with lbm.Cavity(N, N, n, Da, Ra, Pr, porosity, prec="f64", porous_model=porous_model,
+                    clamp_mode=1, resid_interval=500) as cav:
+        steps, resid, why = cav.run_to_steady(1e-9, 3_000_000)
+        hot, cold, _ = cav.nusselt()
+        fl = cav.fields()
+    assert why == 0, (steps, resid, why)
+    return hot, cold, fl
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_2011_15073_gb300 import lbm as m
+    m.lib()
+    return m
+
+
+def test_nusselt_falls_with_power_law_index(lbm):
+    nus = [steady(lbm, n, 1e-3, 1e5)[0] for n in (0.6, 1.0, 1.4)]
+    assert nus[0] > nus[1] > nus[2], nus
+
+
+def test_nusselt_rises_with_darcy_number(lbm):
+    nus = [steady(lbm, 0.6, Da, 1e5)[0] for Da in (1e-3, 1e-2, 1e-1)]
+    assert nus[0] < nus[1] < nus[2], nus
+
+
+def test_nusselt_rises_with_rayleigh_number(lbm):
+    nus = [steady(lbm, 0.6, 1e-2, Ra)[0] for Ra in (1e3, 1e4, 1e5)]
+    assert nus[0] < nus[1] < nus[2], nus
+
+
+@pytest.mark.parametrize("porous_model,porosity", [(0, 1.0), (1, 0.6)])
+def test_energy_balance_and_centro_symmetry(lbm, porous_model, porosity):
+    hot, cold, fl = steady(lbm, 0.8, 1e-2, 1e4, porous_model=porous_model, porosity=porosity)
+    assert abs(hot - cold) < 1e-2 * hot, (hot, cold)
+    T = fl["T"]
+    assert np.max(np.abs(T + T[::-1, ::-1] - 1.0)) < 5e-3
+    u = fl["ux"]
+    assert np.max(np.abs(u + u[::-1, ::-1])) < 5e-2 * np.max(np.abs(u))
