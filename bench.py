@@ -91,7 +91,7 @@ def parse():
                     help="other storage precisions measured beside the headline ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", choices=["tables", "precision"], default=None,
+    ap.add_argument("--study", choices=["tables", "precision", "batch", "adjoint"], default=None,
                     help="physics studies instead of the throughput bench (one JSON line per case)")
     ap.add_argument("--study-N", type=int, default=None)
     ap.add_argument("--study-max-steps", type=int, default=3_000_000)
@@ -195,8 +195,130 @@ def study_precision(args):
                               "seconds": r["sec"]}), flush=True)
 
 
+def study_batch(args):
+    """The paper's kind of sweep (27 cases, n x Da x Ra, grids 128^2-512^2 drawn
+    by seed) run to steady state as one batched workload -- one CUDA graph
+    launch looping on the device, block size from the autotuner -- against
+    the same cases run one after another with lbm_run_to_steady."""
+    from paper_2011_15073_gb300 import inputs, lbm
+    max_steps = args.study_max_steps if args.study_max_steps != 3_000_000 else 1_000_000
+    cl = [dict(nx=c["N"], ny=c["N"], n=c["n"], Da=c["Da"], Ra=c["Ra"], Pr=6.2, porosity=0.6)
+          for c in inputs.sweep_cases(2011)]
+    opts = dict(prec="f32", clamp_mode=1, resid_interval=1000)
+    with lbm.Batch(cl, **opts) as b:
+        t = time.perf_counter()
+        threads = b.tune(200)
+        t_tune = time.perf_counter() - t
+        t = time.perf_counter()
+        steps, res, why = b.run_to_steady(1e-8, max_steps, graph_mode=1)
+        t_batch = time.perf_counter() - t
+        hot, _ = b.nusselt()
+    t = time.perf_counter()
+    seq = []
+    for c in cl:
+        with lbm.Cavity(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], **opts) as cav:
+            s, r, w = cav.run_to_steady(1e-8, max_steps)
+            seq.append((s, r, w, cav.nusselt()[0]))
+    t_seq = time.perf_counter() - t
+    updates = sum(c["nx"] * c["ny"] * s for c, s in zip(cl, steps))
+    print(json.dumps({
+        "study": "batch", "cases": len(cl), "prec": "f32", "tol": 1e-8, "max_steps": max_steps,
+        "tuned_threads": threads, "tune_seconds": t_tune,
+        "batched": {"seconds": t_batch, "cases_per_s": len(cl) / t_batch, "MLUPS": updates / t_batch / 1e6,
+                    "graph_launches": 1},
+        "sequential": {"seconds": t_seq, "cases_per_s": len(cl) / t_seq,
+                       "MLUPS": sum(c["nx"] * c["ny"] * q[0] for c, q in zip(cl, seq)) / t_seq / 1e6},
+        "speedup": t_seq / t_batch,
+        "same_steps": all(s == q[0] for s, q in zip(steps, seq)),
+        "max_rel_nu_diff": max(abs(h - q[3]) / abs(q[3]) for h, q in zip(hot, seq)),
+        "stop_reasons": {k: sum(1 for w in why if w == k) for k in (0, 1, 2, 3)},
+        "per_case": [dict(N=c["nx"], n=c["n"], Da=c["Da"], Ra=c["Ra"], steps=s, resid=float(r), stop=w,
+                          nu=float(h)) for c, s, r, w, h in zip(cl, steps, res, why, hot)],
+    }), flush=True)
+
+
+def study_adjoint(args):
+    """Gradient of the hot-wall Nusselt number after 10,000 FP32 steps of a
+    256^2 cavity (n = 0.8, Ra = 1e4, Pr = 6.2, porosity 0.6) with a per-node
+    Darcy field log-uniform in [1e-3, 1e-1] (seed 2011), by the discrete
+    adjoint with checkpoints every 500 steps; checked against FP64 central
+    differences (h = 1e-4 in log Da) on 16 random nodes and one random
+    direction, and against the FP64 adjoint."""
+    import numpy as np
+    from paper_2011_15073_gb300 import inputs, lbm
+    N = args.study_N or 256
+    steps, ckpt = 10_000, 500
+    case = dict(n=0.8, Ra=1e4, Pr=6.2, porosity=0.6)
+    Da = inputs.darcy_field(2011, N, N)
+
+    def cav(prec):
+        c = lbm.Cavity(N, N, case["n"], 1e-2, case["Ra"], case["Pr"], case["porosity"], prec=prec)
+        c.set_darcy_field(Da)
+        return c
+
+    res = {}
+    for prec in ("f32", "f64"):
+        with cav(prec) as c:       # forward alone, same steps
+            c.step(10)
+            c.synchronize()
+            t = time.perf_counter()
+            c.step(steps)
+            c.synchronize()
+            t_fwd = time.perf_counter() - t
+        with cav(prec) as c:
+            t = time.perf_counter()
+            J, dDa, dn, dRa, peak = c.adjoint_nu(steps, ckpt, from_rest=True)
+            t_adj = time.perf_counter() - t
+        res[prec] = dict(J=J, dDa=dDa, dn=dn, dRa=dRa, peak=peak, t_fwd=t_fwd, t_adj=t_adj)
+
+    def J_of(D):
+        with lbm.Cavity(N, N, case["n"], 1e-2, case["Ra"], case["Pr"], case["porosity"], prec="f64") as c:
+            c.set_darcy_field(D)
+            c.step(steps)
+            return c.nusselt()[0]
+
+    h = 1e-4
+    rng = np.random.default_rng(2011)
+    nodes = [(int(rng.integers(0, N)), int(rng.integers(0, N))) for _ in range(16)]
+    fd_rel = []
+    for (j, i) in nodes:
+        Dp, Dm = Da.copy(), Da.copy()
+        Dp[j, i] *= np.exp(h)
+        Dm[j, i] *= np.exp(-h)
+        fd = (J_of(Dp) - J_of(Dm)) / (2 * h)
+        for prec in ("f64", "f32"):
+            ad = res[prec]["dDa"][j, i] * Da[j, i]
+            fd_rel.append(dict(node=[j, i], prec=prec, fd=fd, adjoint=ad,
+                               rel=abs(ad - fd) / max(abs(fd), 1e-300)))
+    v = rng.standard_normal((N, N))
+    fd_dir = (J_of(Da * np.exp(h * v)) - J_of(Da * np.exp(-h * v))) / (2 * h)
+    dir_ad = {p_: float(np.sum(res[p_]["dDa"] * Da * v)) for p_ in ("f64", "f32")}
+    f32, f64 = res["f32"], res["f64"]
+    print(json.dumps({
+        "study": "adjoint", "N": N, "steps": steps, "ckpt_every": ckpt, **case,
+        "J": {"f32": f32["J"], "f64": f64["J"]},
+        "dJ_dn": {"f32": f32["dn"], "f64": f64["dn"]}, "dJ_dRa": {"f32": f32["dRa"], "f64": f64["dRa"]},
+        "time_forward_s": {"f32": f32["t_fwd"], "f64": f64["t_fwd"]},
+        "time_adjoint_s": {"f32": f32["t_adj"], "f64": f64["t_adj"]},
+        "adjoint_over_forward": {"f32": f32["t_adj"] / f32["t_fwd"], "f64": f64["t_adj"] / f64["t_fwd"]},
+        "peak_device_bytes": {"f32": f32["peak"], "f64": f64["peak"]},
+        "fd_nodes_max_rel": {p_: max(r["rel"] for r in fd_rel if r["prec"] == p_) for p_ in ("f64", "f32")},
+        "fd_direction": {"fd": fd_dir, "adjoint_f64": dir_ad["f64"], "adjoint_f32": dir_ad["f32"],
+                         "rel_f64": abs(dir_ad["f64"] - fd_dir) / abs(fd_dir),
+                         "rel_f32": abs(dir_ad["f32"] - fd_dir) / abs(fd_dir)},
+        "f32_vs_f64_dDa_rel_l2": float(np.linalg.norm(f32["dDa"] - f64["dDa"]) / np.linalg.norm(f64["dDa"])),
+        "fd_nodes": fd_rel,
+    }), flush=True)
+
+
 def main():
     args = parse()
+    if args.study == "adjoint":
+        study_adjoint(args)
+        return
+    if args.study == "batch":
+        study_batch(args)
+        return
     if args.study == "tables":
         study_tables(args)
         return

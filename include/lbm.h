@@ -116,6 +116,14 @@ int lbm_init(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra,
 /* Release every device and host resource of ctx (NULL is ignored). */
 void lbm_destroy(lbm_ctx *ctx);
 
+/* Set a per-node Darcy number Da(x) (host array of nx*ny doubles, [ny][nx],
+ * caller-owned, copied): the permeability K(x) = Da(x) L^2 then replaces the
+ * uniform K of lbm_init in the drag of the momentum equations (the term
+ * -U D / Da of Eqs. par_sim_u/v:momentum, node by node).  NULL returns to the
+ * uniform Da.  Errors: LBM_ERR_ARG (a value not finite or <= 0), LBM_ERR_OOM,
+ * LBM_ERR_CUDA.  Synchronous. */
+int lbm_set_darcy_field(lbm_ctx *ctx, const double *Da_xy);
+
 /* Copy the lattice-unit parameters of ctx into *out. */
 int lbm_get_lattice(const lbm_ctx *ctx, lbm_lattice *out);
 
@@ -182,6 +190,74 @@ int lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
 int lbm_get_state_f64(lbm_ctx *ctx, double *f, double *g, double *tau);
 int lbm_set_state_f64(lbm_ctx *ctx, const double *f, const double *g,
                       const double *tau);
+
+/* Discrete adjoint (reverse mode) of the hot-wall average Nusselt number J
+ * (Eq. avgNu) after `steps` fused steps, with respect to the per-node Darcy
+ * number Da(x) (the field of lbm_set_darcy_field, or the uniform Da seen as
+ * a field), the power-law index n and the Rayleigh number Ra.  The forward
+ * run keeps a checkpoint every ckpt_every steps; the reverse sweep
+ * recomputes one segment of states at a time from its checkpoint and runs
+ * the hand-written reverse of the fused step over it.  from_rest = 1 first
+ * resets the state to the rest state of lbm_init and includes the
+ * dependence of its relaxation time tau_0 on n and Ra; from_rest = 0 starts
+ * from the current state, held fixed.  Afterwards the context holds s_T.
+ * Outputs (any may be NULL): *J, dDa (host, nx*ny doubles, [ny][nx]), *dn,
+ * *dRa, and *peak_bytes, the device memory the run used (state buffers,
+ * checkpoints, one segment of states, two adjoint buffers, FP64 gradient
+ * planes).  Parameter gradients accumulate in FP64.  Two-buffer layout with
+ * FP64 or FP32 storage; other storages get LBM_ERR_UNSUPPORTED.
+ * Synchronous.  Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_adjoint_nu(lbm_ctx *ctx, int64_t steps, int ckpt_every, int from_rest,
+                   double *J, double *dDa, double *dn, double *dRa,
+                   double *peak_bytes);
+
+/* ------------------------------------------------------------- sweeps
+ * The paper's results are a sweep of independent cavities over n, Da and Ra
+ * (section "Results and discussions", Tables 1-2).  A batch runs such a sweep
+ * as one workload: each time step is one kernel launch over the row tiles of
+ * every active case (grids may differ), every resid_interval steps each
+ * case's residual is checked on the device and converged cases stop being
+ * stepped.  All cases share the storage precision and the options of
+ * lbm_batch_create (the two-buffer layout; resid_interval must be even). */
+typedef struct {
+    int nx, ny;
+    double n, Da, Ra, Pr, porosity;
+} lbm_case;
+
+typedef struct lbm_batch lbm_batch;
+
+/* Create one context per case (validated as by lbm_init) on one stream.
+ * Errors as lbm_init; LBM_ERR_ARG also for an odd resid_interval. */
+int lbm_batch_create(lbm_batch **out, const lbm_case *cases, int ncases,
+                     const lbm_opts *opts);
+void lbm_batch_destroy(lbm_batch *batch);
+
+/* Borrow case i's context for state I/O, fields or Nu (do not destroy it). */
+int lbm_batch_get_case(lbm_batch *batch, int i, lbm_ctx **ctx);
+
+/* Advance every case k steps (one launch per step). Asynchronous. */
+int lbm_batch_step(lbm_batch *batch, int64_t k);
+
+/* Run every case until its residual (as lbm_run_to_steady) falls below tol,
+ * stagnates below the storage's noise floor, or reaches max_steps.
+ * graph_mode 0: the host relaunches a CUDA graph of one resid_interval chunk
+ * (all cases' steps, residuals and the convergence update) while any case is
+ * active; 1: a single CUDA graph launch runs the whole sweep, looping on the
+ * device (a conditional while node), bounded by max_steps.  steps, resid,
+ * reason (per case, caller-owned, ncases entries; NULL skips) receive the
+ * steps run, the last residual, and 0 tol / 1 stagnated / 2 max_steps /
+ * 3 non-finite.  Synchronous.  Returns LBM_ERR_NONFINITE if any case blew up. */
+int lbm_batch_run_to_steady(lbm_batch *batch, double tol, int64_t max_steps,
+                            int graph_mode, int64_t *steps, double *resid,
+                            int *reason);
+
+/* Hot- and cold-wall average Nu of every case (host arrays of ncases). */
+int lbm_batch_nusselt(lbm_batch *batch, double *nu_hot, double *nu_cold);
+
+/* Autotune the batched kernel's block size (tile width) by timing `steps`
+ * batched steps for each candidate on copies of the current states (the
+ * states are restored); *threads_out receives the block size chosen. */
+int lbm_batch_tune(lbm_batch *batch, int steps, int *threads_out);
 
 /* Allocation-free form of lbm_residual, for callers that cannot call
  * cudaMalloc at the point where they check convergence: host code that must

@@ -97,6 +97,8 @@ def lib():
             L.orc_set_state.argtypes = [ctypes.c_void_p, _D, _D, _D]
             L.orc_fields.argtypes = [ctypes.c_void_p] + [_D] * 6
             L.orc_nusselt.argtypes = [ctypes.c_void_p, _D, _D, _D]
+            L.orc_set_darcy_field.argtypes = [ctypes.c_void_p, _D]
+            L.orc_set_darcy_field.restype = None
             L.orc_matrices.argtypes = [_D] * 4
             L.orc_meq.argtypes = [ctypes.c_double] * 4 + [_D]
             L.orc_feq.argtypes = [ctypes.c_double] * 4 + [_D]
@@ -204,6 +206,16 @@ class Cavity:
         out = {k: np.zeros((self.ny, self.nx)) for k in ("rho", "ux", "uy", "T", "nu", "gamma")}
         lib().orc_fields(self._h, *[_ptr(out[k]) for k in ("rho", "ux", "uy", "T", "nu", "gamma")])
         return out
+
+    def set_darcy_field(self, Da):
+        """Per-node Darcy numbers [ny][nx] (None: uniform K again)."""
+        if Da is None:
+            lib().orc_set_darcy_field(self._h, None)
+            return
+        Da = np.ascontiguousarray(Da, dtype=np.float64)
+        assert Da.shape == (self.ny, self.nx)
+        self._Da = Da
+        lib().orc_set_darcy_field(self._h, _ptr(Da))
 
     def nusselt(self):
         """(hot-wall average Nu, cold-wall average Nu, hot-wall local Nu[ny])."""

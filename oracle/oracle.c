@@ -220,7 +220,7 @@ typedef struct {
     double rho, ux, uy, T, nu, gamma;
 } node_diag;
 
-static void node_update(const orc_lattice *p, const double f[9],
+static void node_update(const orc_lattice *p, double K, const double f[9],
                         const double g[5], double tau_prev, double fo[9],
                         double go[5], double *tau_new, node_diag *d)
 {
@@ -241,17 +241,17 @@ static void node_update(const orc_lattice *p, const double f[9],
     double vy = jy / rho + 0.5 * p->eps * Gy;
     /* 4 */
     double nu_prev = (tau_prev - 0.5) / 3.0;
-    double c0 = 0.5 * (1.0 + p->eps * nu_prev / (2.0 * p->K));
-    double c1 = p->eps * p->Feps / (2.0 * sqrt(p->K));
+    double c0 = 0.5 * (1.0 + p->eps * nu_prev / (2.0 * K));
+    double c1 = p->eps * p->Feps / (2.0 * sqrt(K));
     double vmag = sqrt(vx * vx + vy * vy);
     double den = c0 + sqrt(c0 * c0 + c1 * vmag);
     double ux = vx / den, uy = vy / den;
     /* 5 */
     double umag = sqrt(ux * ux + uy * uy);
-    double Fx = -p->eps * nu_prev * ux / p->K
-                - p->eps * p->Feps * umag * ux / sqrt(p->K) + p->eps * Gx;
-    double Fy = -p->eps * nu_prev * uy / p->K
-                - p->eps * p->Feps * umag * uy / sqrt(p->K) + p->eps * Gy;
+    double Fx = -p->eps * nu_prev * ux / K
+                - p->eps * p->Feps * umag * ux / sqrt(K) + p->eps * Gx;
+    double Fy = -p->eps * nu_prev * uy / K
+                - p->eps * p->Feps * umag * uy / sqrt(K) + p->eps * Gy;
     /* 6 */
     double feq[9], fneq[9], S[9], A[81], tmp[81], h[9];
     orc_feq(rho, ux, uy, p->eps, feq);
@@ -326,7 +326,7 @@ void orc_collide_node(const orc_lattice *lat, const double f[9],
                       double go[5], double *tau_new, double *gamma)
 {
     node_diag d;
-    node_update(lat, f, g, tau_prev, fo, go, tau_new, &d);
+    node_update(lat, lat->K, f, g, tau_prev, fo, go, tau_new, &d);
     if (gamma) *gamma = d.gamma;
 }
 
@@ -400,7 +400,21 @@ struct orc_ctx {
     size_t nn;
     double *f, *g, *tau;  /* post-collision state          */
     double *fs, *gs;      /* streamed (pre-collision) work */
+    double *Kf;           /* per-node permeability or NULL */
 };
+
+static double K_at(const orc_ctx *c, size_t q) { return c->Kf ? c->Kf[q] : c->p.K; }
+
+void orc_set_darcy_field(orc_ctx *c, const double *Da)
+{
+    if (!Da) {
+        free(c->Kf);
+        c->Kf = NULL;
+        return;
+    }
+    if (!c->Kf) c->Kf = (double *)malloc(sizeof(double) * c->nn);
+    for (size_t q = 0; q < c->nn; q++) c->Kf[q] = Da[q] * c->p.L * c->p.L;
+}
 
 int orc_create(orc_ctx **out, const orc_lattice *lat)
 {
@@ -437,6 +451,7 @@ void orc_destroy(orc_ctx *c)
     free(c->tau);
     free(c->fs);
     free(c->gs);
+    free(c->Kf);
     free(c);
 }
 
@@ -498,7 +513,7 @@ int orc_step(orc_ctx *c, int64_t k)
             double f[9], g[5], fo[9], go[5], tnew;
             gather(c->fs, 9, nn, (size_t)q, f);
             gather(c->gs, 5, nn, (size_t)q, g);
-            node_update(&c->p, f, g, c->tau[q], fo, go, &tnew, NULL);
+            node_update(&c->p, K_at(c, (size_t)q), f, g, c->tau[q], fo, go, &tnew, NULL);
             for (int i = 0; i < 9; i++) c->f[i * nn + q] = fo[i];
             for (int i = 0; i < 5; i++) c->g[i * nn + q] = go[i];
             c->tau[q] = tnew;
@@ -538,7 +553,7 @@ void orc_fields(const orc_ctx *c, double *rho, double *ux, double *uy,
         node_diag d;
         gather(fs, 9, nn, q, f);
         gather(gs, 5, nn, q, g);
-        node_update(&c->p, f, g, c->tau[q], fo, go, &tnew, &d);
+        node_update(&c->p, K_at(c, q), f, g, c->tau[q], fo, go, &tnew, &d);
         if (rho) rho[q] = d.rho;
         if (ux) ux[q] = d.ux;
         if (uy) uy[q] = d.uy;

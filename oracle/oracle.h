@@ -79,6 +79,10 @@ void orc_fields(const orc_ctx *c, double *rho, double *ux, double *uy,
  * nu_local (NULL or ny values) gets the hot-wall local Nu. */
 void orc_nusselt(const orc_ctx *c, double *hot, double *cold, double *nu_local);
 
+/* Per-node Darcy numbers (nx*ny values, [ny][nx]); K(x) = Da(x) L^2 replaces
+ * the uniform K.  NULL restores the uniform permeability. */
+void orc_set_darcy_field(orc_ctx *c, const double *Da);
+
 /* Pieces exposed for the unit pins. */
 void orc_matrices(double M[81], double Minv[81], double N[25], double Ninv[25]);
 void orc_meq(double rho, double ux, double uy, double eps, double out[9]);

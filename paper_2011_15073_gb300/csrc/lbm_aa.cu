@@ -66,7 +66,7 @@ aa_even_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::Ta
 #pragma unroll
     for (int i = 0; i < 5; i++) g[i] = St::ld(A + 9 * P, i * P + k, R(rest_g(i)));
     Macro<R> m;
-    const R t = collide<R>(p, f, g, R(tau[k]), m);
+    const R t = collide<R>(p, f, g, R(tau[k]), m, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) St::st(A, opp(i) * P + k, f[i], R(rest_f(opp(i))));
 #pragma unroll
@@ -83,7 +83,7 @@ __device__ __forceinline__ void odd_node(typename Store<PREC>::S *__restrict__ A
     R f[9], g[5];
     pull<PREC, R, true>(A, p, x, y, f, g);
     Macro<R> m;
-    const R t = collide<R>(p, f, g, R(tau[k]), m);
+    const R t = collide<R>(p, f, g, R(tau[k]), m, k);
     push<PREC, R>(A, p, x, y, f, g);
     tau[k] = typename Store<PREC>::TauS(t);
 }
@@ -112,7 +112,7 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
         for (int i = 0; i < 9; i++) f[i] = St::ld(A, i * P + k, float(rest_f(i)));
         for (int i = 0; i < 5; i++) g[i] = St::ld(A + 9 * P, i * P + k, float(rest_g(i)));
         Macro<float> m;
-        const float t = collide<float>(p, f, g, tau[k], m);
+        const float t = collide<float>(p, f, g, tau[k], m, k);
         for (int i = 0; i < 9; i++) St::st(A, opp(i) * P + k, f[i], float(rest_f(opp(i))));
         for (int i = 0; i < 5; i++) St::st(A + 9 * P, opp(i) * P + k, g[i], float(rest_g(opp(i))));
         tau[k] = t;
@@ -124,7 +124,7 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
 #pragma unroll
     for (int i = 0; i < 5; i++) g[i] = St::ld2(A + (9 + i) * P, k, float(rest_g(i)));
     Macro<F2> m;
-    const F2 t = collide<F2>(p2, f, g, F2(*reinterpret_cast<const float2 *>(tau + k)), m);
+    const F2 t = collide<F2>(p2, f, g, F2(*reinterpret_cast<const float2 *>(tau + k)), m, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) St::st2(A + opp(i) * P, k, f[i], float(rest_f(opp(i))));
 #pragma unroll
@@ -196,7 +196,7 @@ aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau,
     g[3] = from_right(St::ld2(gs + P, k, float(rest_g(1))), l31 ? St::ld(gs + P, k + 2, float(rest_g(1))) : 0.f, lane);
     g[4] = St::ld2(gs + 2 * P, k + W, float(rest_g(2)));
     Macro<F2> m;
-    const F2 t = collide<F2>(p2, f, g, F2(*reinterpret_cast<const float2 *>(tau + k)), m);
+    const F2 t = collide<F2>(p2, f, g, F2(*reinterpret_cast<const float2 *>(tau + k)), m, k);
     // push f*_i(x) into slot i of node x + e_i
     St::st2(fs, k, f[0], float(rest_f(0)));
     push_right<PREC>(fs + P, k, f[1], float(rest_f(1)), lane);
@@ -229,7 +229,7 @@ aa_normalize_kernel(typename Store<PREC>::S *__restrict__ A, Phys<typename Store
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= p.nx) return;
     const int64_t P = p.plane, W = p.pitch, k = (int64_t)y * W + x;
-    const bool xl = x > 0, xr = x < p.nx - 1, yb = y > 0, yt = y < p.ny - 1;
+    const bool xl = x > 0, xr = x < p.nx - 1, yt = y < p.ny - 1;
     auto swap = [&](typename Store<PREC>::S *base, int i, int64_t kt, bool flow) {
         const R ri = R(flow ? rest_f(i) : rest_g(i)), ro = R(flow ? rest_f(opp(i)) : rest_g(opp(i)));
         const R a = St::ld(base, i * P + kt, ri);

@@ -1,0 +1,306 @@
+// lbm_adjoint.cu -- discrete adjoint of the hot-wall average Nusselt number
+// through a run of the fused step (two-buffer layout), with checkpoints.
+//
+// J = Nu_hot(s_T) after T steps from s_0.  With s_{t+1} = C(P(s_t)) (P the
+// pull with the wall rules, C the per-node collision), the adjoint state
+// lambda_t = dJ/ds_t obeys lambda_t = P^T C'^T lambda_{t+1}.  P maps every
+// post-collision slot to exactly one pulled value (a neighbour, or the node
+// itself across a wall, negated by the anti-bounce-back), so P^T is a scatter
+// in which every slot is written once: no atomics.  Parameter gradients
+// (per-node Darcy number, n, Ra) are summed per node in FP64 planes that
+// each node owns, and reduced once at the end.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "lbm_adjoint.cuh"
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+#include "lbm_step.cuh"
+
+namespace {
+
+using namespace lbm;
+
+// Parameters of the chain from (n, Ra, Da) to the lattice coefficients.
+struct Chain {
+    double n, Ra, tauT;  // power-law index, Rayleigh number, thermal tau
+};
+
+// Seed: lambda_T = dJ/ds_T.  Nu_hot = mean_j -L (9 theta_0 - theta_1 - 8)/3
+// with theta = (T - T_c)/(T_h - T_c) and T the sum of the pulled g at
+// columns 0 and 1; every pulled value there reads exactly one slot.
+template <class V>
+__global__ void adj_seed_kernel(V *__restrict__ lam, Phys<V> p, double coef0, double coef1)
+{
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= p.ny) return;
+    const int64_t P = p.plane, W = p.pitch;
+    V *G = lam + 9 * P;
+    for (int col = 0; col < 2 && col < p.nx; col++) {
+        const V a = V(col == 0 ? coef0 : coef1);
+        const int x = col;
+        const int64_t k = (int64_t)y * W + x;
+        const bool xl = x > 0, xr = x < p.nx - 1, yb = y > 0, yt = y < p.ny - 1;
+        // pulled g_i(x) reads: g0 own; g1 from x-1 or -(own g3) at the hot wall;
+        // g2 from y-1 or own g4; g3 from x+1 or -(own g1); g4 from y+1 or own g2
+        G[0 * P + k] += a;
+        if (xl) G[1 * P + k - 1] += a; else G[3 * P + k] += -a;
+        if (yb) G[2 * P + k - W] += a; else G[4 * P + k] += a;
+        if (xr) G[3 * P + k + 1] += a; else G[1 * P + k] += -a;
+        if (yt) G[4 * P + k + W] += a; else G[2 * P + k] += a;
+    }
+}
+
+// One reverse step: lam_out (adjoint of s_{t+1}) -> lam_in (adjoint of s_t),
+// recomputing the collision of every node from s_t.
+template <int PREC, class V>
+__global__ void __launch_bounds__(128)
+adj_step_kernel(const typename Store<PREC>::S *__restrict__ st, const typename Store<PREC>::TauS *__restrict__ tst,
+                const V *__restrict__ lam_out, V *__restrict__ lam_in, double *__restrict__ gDa,
+                double *__restrict__ gn, double *__restrict__ gRa, Phys<V> p, Chain ch)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= p.nx) return;
+    const int64_t P = p.plane, W = p.pitch;
+    const int64_t k = (int64_t)y * W + x;
+    V f[9], g[5];
+    pull<PREC, V>(st, p, x, y, f, g);
+    const V tau_prev = V(tst[k]);
+    V fo[9], go[5];
+#pragma unroll
+    for (int i = 0; i < 9; i++) fo[i] = lam_out[i * P + k];
+#pragma unroll
+    for (int i = 0; i < 5; i++) go[i] = lam_out[(9 + i) * P + k];
+    const V tb_new = lam_out[14 * P + k];
+    V fb[9], gb[5], tb_prev;
+    ParamAdj<V> pa;
+    collide_adj<V>(p, f, g, tau_prev, k, fo, go, tb_new, fb, gb, tb_prev, pa);
+    // P^T: the pulled f_i(x) came from slot i of x - e_i, or slot opp(i) of x
+    const bool xl = x > 0, xr = x < p.nx - 1, yb = y > 0, yt = y < p.ny - 1;
+    lam_in[0 * P + k] = fb[0];
+    if (xl) lam_in[1 * P + k - 1] = fb[1]; else lam_in[3 * P + k] = fb[1];
+    if (yb) lam_in[2 * P + k - W] = fb[2]; else lam_in[4 * P + k] = fb[2];
+    if (xr) lam_in[3 * P + k + 1] = fb[3]; else lam_in[1 * P + k] = fb[3];
+    if (yt) lam_in[4 * P + k + W] = fb[4]; else lam_in[2 * P + k] = fb[4];
+    if (xl && yb) lam_in[5 * P + k - W - 1] = fb[5]; else lam_in[7 * P + k] = fb[5];
+    if (xr && yb) lam_in[6 * P + k - W + 1] = fb[6]; else lam_in[8 * P + k] = fb[6];
+    if (xr && yt) lam_in[7 * P + k + W + 1] = fb[7]; else lam_in[5 * P + k] = fb[7];
+    if (xl && yt) lam_in[8 * P + k + W - 1] = fb[8]; else lam_in[6 * P + k] = fb[8];
+    V *G = lam_in + 9 * P;
+    G[0 * P + k] = gb[0];
+    if (xl) G[1 * P + k - 1] = gb[1]; else G[3 * P + k] = -gb[1];
+    if (yb) G[2 * P + k - W] = gb[2]; else G[4 * P + k] = gb[2];
+    if (xr) G[3 * P + k + 1] = gb[3]; else G[1 * P + k] = -gb[3];
+    if (yt) G[4 * P + k + W] = gb[4]; else G[2 * P + k] = gb[4];
+    lam_in[14 * P + k] = tb_prev;
+    // parameters: porous coefficients of this node -> Da(x)
+    const Porous<V> q = porous_at(p, k);
+    const double Da = p.da ? double(load_da(p, k)) : double(p.eps / (p.eps_invK * p.L2));
+    const double dDa = -(double(q.heK) * double(pa.heK) + double(q.eK) * double(pa.eK)) / Da -
+                       (double(q.c1) * double(pa.c1) + double(q.eFsK) * double(pa.eFsK)) / (2.0 * Da);
+    // nu_ref = Pr Ra^(-(2-n)/2) U_c L, n - 1, and 1/tauT with tauT - 1/2 ~ Ra^(-1/2)
+    const double nu_ref = double(p.nu_ref), wT = double(p.omegaT);
+    const double dn = double(pa.nu_ref) * nu_ref * 0.5 * log(ch.Ra) + double(pa.nm1);
+    const double dRa = double(pa.nu_ref) * (-nu_ref * (2.0 - ch.n) / (2.0 * ch.Ra)) +
+                       double(pa.omegaT) * wT * wT * (ch.tauT - 0.5) / (2.0 * ch.Ra);
+    const int64_t q0 = (int64_t)y * p.nx + x;
+    gDa[q0] += dDa;
+    gn[q0] += dn;
+    gRa[q0] += dRa;
+}
+
+// Single-block FP64 sum of n values (fixed order).
+__global__ void __launch_bounds__(256) sum_kernel(const double *__restrict__ a, int64_t n, double *out)
+{
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += a[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// dJ/dtau_0 summed over the nodes (the rest state's tau_0 depends on n, Ra).
+template <class V>
+__global__ void __launch_bounds__(256) tau0_sum_kernel(const V *__restrict__ lam, Phys<V> p, double *out)
+{
+    __shared__ double sh[256];
+    double s = 0.0;
+    const int64_t n = (int64_t)p.nx * p.ny;
+    for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
+        const int y = (int)(q / p.nx), x = (int)(q - (int64_t)y * p.nx);
+        s += double(lam[14 * p.plane + (int64_t)y * p.pitch + x]);
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+template <int PREC>
+struct Adj {
+    using St = Store<PREC>;
+    using S = typename St::S;
+    using TauS = typename St::TauS;
+    using V = typename St::R;
+};
+
+template <int PREC>
+int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, double *dDa, double *dn,
+                double *dRa, double *peak_bytes)
+{
+    using A = Adj<PREC>;
+    using S = typename A::S;
+    using TauS = typename A::TauS;
+    using V = typename A::V;
+    const size_t es = sizeof(S), ts = sizeof(TauS);
+    const size_t dist_bytes = es * 14 * (size_t)c->plane, tau_bytes = ts * (size_t)c->plane;
+    const size_t lam_bytes = sizeof(V) * 15 * (size_t)c->plane;
+    const int64_t nseg = (steps + ckpt - 1) / ckpt;
+    const size_t nn = (size_t)c->nx * c->ny;
+    std::vector<void *> allocs;
+    auto alloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        allocs.push_back(p);
+        return p;
+    };
+    auto cleanup = [&]() {
+        cudaStreamSynchronize(c->stream);
+        for (void *p : allocs) cudaFree(p);
+    };
+    int rc = LBM_OK;
+    // checkpoints s_{j ckpt}, the states of one segment, two adjoint buffers, gradients
+    char *ck = (char *)alloc((dist_bytes + tau_bytes) * (size_t)(nseg > 0 ? nseg : 1));
+    const int seg_len = (int)(steps < ckpt ? steps : ckpt);
+    char *seg = (char *)alloc((dist_bytes + tau_bytes) * (size_t)(seg_len > 0 ? seg_len : 1));
+    V *lam[2] = {(V *)alloc(lam_bytes), (V *)alloc(lam_bytes)};
+    double *g3 = (double *)alloc(sizeof(double) * 3 * nn);
+    double *red = (double *)alloc(sizeof(double) * 4);
+    if (!ck || !seg || !lam[0] || !lam[1] || !g3 || !red) {
+        cleanup();
+        return LBM_ERR_OOM;
+    }
+    // device memory of this run: the context's two state buffers plus the
+    // checkpoints, one segment of states, two adjoint buffers and the gradients
+    const double total = (double)(dist_bytes + tau_bytes) * (double)(nseg + seg_len + 2) + 2.0 * lam_bytes +
+                         sizeof(double) * 3.0 * nn;
+    if (peak_bytes) *peak_bytes = total;
+    if (from_rest) {
+        c->cur = 0;
+        if (lbm::launch_init(c) != cudaSuccess) rc = LBM_ERR_CUDA;
+    }
+    const Phys<V> pv = make_params<V>(c);
+    auto ckd = [&](int64_t j) { return (S *)(ck + (size_t)j * (dist_bytes + tau_bytes)); };
+    auto ckt = [&](int64_t j) { return (TauS *)(ck + (size_t)j * (dist_bytes + tau_bytes) + dist_bytes); };
+    auto sgd = [&](int j) { return (S *)(seg + (size_t)j * (dist_bytes + tau_bytes)); };
+    auto sgt = [&](int j) { return (TauS *)(seg + (size_t)j * (dist_bytes + tau_bytes) + dist_bytes); };
+    // forward with checkpoints (the context's own buffers advance to s_T)
+    for (int64_t j = 0; j < nseg && rc == LBM_OK; j++) {
+        if (cudaMemcpyAsync(ckd(j), c->buf.dist[c->cur], dist_bytes, cudaMemcpyDeviceToDevice, c->stream) ||
+            cudaMemcpyAsync(ckt(j), c->buf.tau[c->cur], tau_bytes, cudaMemcpyDeviceToDevice, c->stream)) {
+            rc = LBM_ERR_CUDA;
+            break;
+        }
+        const int64_t len = (j + 1) * ckpt <= steps ? ckpt : steps - j * ckpt;
+        for (int64_t s = 0; s < len && rc == LBM_OK; s++)
+            if (lbm::launch_step(c) != cudaSuccess) rc = LBM_ERR_CUDA;
+    }
+    // J and the seed
+    if (rc == LBM_OK && lbm::launch_nusselt(c) != cudaSuccess) rc = LBM_ERR_CUDA;
+    double hj = 0.0;
+    if (rc == LBM_OK && (cudaMemcpyAsync(&hj, c->d_small, sizeof(double), cudaMemcpyDeviceToHost, c->stream) ||
+                         cudaStreamSynchronize(c->stream)))
+        rc = LBM_ERR_CUDA;
+    if (J) *J = hj;
+    const double L = c->lat.L, dT = c->lat.T_hot - c->lat.T_cold;
+    int cur = 0;
+    if (rc == LBM_OK) {
+        cudaMemsetAsync(lam[0], 0, lam_bytes, c->stream);
+        cudaMemsetAsync(lam[1], 0, lam_bytes, c->stream);
+        cudaMemsetAsync(g3, 0, sizeof(double) * 3 * nn, c->stream);
+        adj_seed_kernel<V><<<(c->ny + 127) / 128, 128, 0, c->stream>>>(lam[0], pv, -3.0 * L / (c->ny * dT),
+                                                                       L / (3.0 * c->ny * dT));
+        if (cudaGetLastError() != cudaSuccess) rc = LBM_ERR_CUDA;
+    }
+    // reverse sweep, one segment at a time
+    Chain chain{c->lat.n, 0.0, c->lat.tauT};
+    {
+        // Ra from the mapping: tauT - 1/2 = 3 U_c L / sqrt(Ra)
+        const double Uc = c->opts.Ma / sqrt(3.0);
+        const double r = 3.0 * Uc * L / (c->lat.tauT - 0.5);
+        chain.Ra = r * r;
+    }
+    const dim3 grid((c->nx + 127) / 128, c->ny);
+    for (int64_t j = nseg - 1; j >= 0 && rc == LBM_OK; j--) {
+        const int64_t len = (j + 1) * ckpt <= steps ? ckpt : steps - j * ckpt;
+        // states s_{j ckpt + i}, i = 0..len-1, recomputed from the checkpoint
+        cudaMemcpyAsync(sgd(0), ckd(j), dist_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(sgt(0), ckt(j), tau_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        for (int i = 1; i < len && rc == LBM_OK; i++)
+            if (lbm::launch_step_buffers(c, sgd(i - 1), sgd(i), sgt(i - 1), sgt(i)) != cudaSuccess) rc = LBM_ERR_CUDA;
+        for (int i = (int)len - 1; i >= 0 && rc == LBM_OK; i--) {
+            adj_step_kernel<PREC, V><<<grid, 128, 0, c->stream>>>(sgd(i), sgt(i), lam[cur], lam[cur ^ 1], g3,
+                                                                 g3 + nn, g3 + 2 * nn, pv, chain);
+            if (cudaGetLastError() != cudaSuccess) rc = LBM_ERR_CUDA;
+            cur ^= 1;
+        }
+    }
+    // reductions: sum of the n and Ra partials, and lambda_0 on tau for tau_0(n, Ra)
+    double h[3] = {0, 0, 0};
+    if (rc == LBM_OK) {
+        sum_kernel<<<1, 256, 0, c->stream>>>(g3 + nn, (int64_t)nn, red);
+        sum_kernel<<<1, 256, 0, c->stream>>>(g3 + 2 * nn, (int64_t)nn, red + 1);
+        tau0_sum_kernel<V><<<1, 256, 0, c->stream>>>(lam[cur], pv, red + 2);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(h, red, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream) ||
+            (dDa && cudaMemcpyAsync(dDa, g3, sizeof(double) * nn, cudaMemcpyDeviceToHost, c->stream)) ||
+            cudaStreamSynchronize(c->stream))
+            rc = LBM_ERR_CUDA;
+    }
+    if (rc == LBM_OK) {
+        double gn = h[0], gR = h[1];
+        if (from_rest) {
+            // tau_0 = 3 nu_ref D(0) + 1/2, nu_ref ~ Ra^(-(2-n)/2), D(0) = 1 (literal) or gamma1^(n-1)
+            const double nu_ref = c->lat.nu_ref, n = c->lat.n;
+            const double D0 = c->lat.clamp_mode == 0 ? 1.0 : pow(c->lat.gamma1, n - 1.0);
+            double dtau_dn = 3.0 * D0 * nu_ref * 0.5 * log(chain.Ra);
+            if (c->lat.clamp_mode == 1) dtau_dn += 3.0 * nu_ref * D0 * log(c->lat.gamma1);
+            const double dtau_dRa = 3.0 * D0 * (-nu_ref * (2.0 - n) / (2.0 * chain.Ra));
+            gn += h[2] * dtau_dn;
+            gR += h[2] * dtau_dRa;
+        }
+        if (dn) *dn = gn;
+        if (dRa) *dRa = gR;
+        c->steps += steps;
+        c->have_snap = false;
+    }
+    cleanup();
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int lbm_adjoint_nu(lbm_ctx *c, int64_t steps, int ckpt_every, int from_rest, double *J, double *dDa,
+                              double *dn, double *dRa, double *peak_bytes)
+{
+    if (!c || steps < 1 || ckpt_every < 1) return LBM_ERR_ARG;
+    if (c->opts.layout != 0) return LBM_ERR_UNSUPPORTED;
+    if (cudaSetDevice(c->device) != cudaSuccess) return LBM_ERR_CUDA;
+    switch (c->opts.prec) {
+    case LBM_F64: return run_adjoint<LBM_F64>(c, steps, ckpt_every, from_rest, J, dDa, dn, dRa, peak_bytes);
+    case LBM_F32: return run_adjoint<LBM_F32>(c, steps, ckpt_every, from_rest, J, dDa, dn, dRa, peak_bytes);
+    default: return LBM_ERR_UNSUPPORTED;
+    }
+}

@@ -95,6 +95,7 @@ void free_ctx(lbm_ctx *c)
     cudaFree(c->d_snap);
     cudaFree(c->d_part);
     cudaFree(c->d_nuloc);
+    cudaFree(c->d_da);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -247,6 +248,42 @@ void lbm_destroy(lbm_ctx *c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_ctx(c);
+}
+
+int lbm_set_darcy_field(lbm_ctx *c, const double *Da)
+{
+    if (!c) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    if (!Da) {
+        CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->d_da);
+        c->d_da = nullptr;
+        return LBM_OK;
+    }
+    const size_t n = (size_t)c->nx * c->ny;
+    for (size_t q = 0; q < n; q++)
+        if (!(Da[q] > 0) || !isfinite(Da[q])) return LBM_ERR_ARG;
+    const size_t es = c->opts.prec == LBM_F64 ? 8 : 4;
+    if (!c->d_da) {
+        CK(cudaMalloc(&c->d_da, es * (size_t)c->plane));
+        CK(cudaMemsetAsync(c->d_da, 0, es * (size_t)c->plane, c->stream));
+    }
+    if (es == 8) {
+        CK(cudaMemcpy2DAsync(c->d_da, c->pitch * es, Da, c->nx * es, c->nx * es, c->ny, cudaMemcpyHostToDevice,
+                             c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        float *tmp = new (std::nothrow) float[n];
+        if (!tmp) return LBM_ERR_OOM;
+        for (size_t q = 0; q < n; q++) tmp[q] = (float)Da[q];
+        const cudaError_t e1 = cudaMemcpy2DAsync(c->d_da, c->pitch * es, tmp, c->nx * es, c->nx * es, c->ny,
+                                                 cudaMemcpyHostToDevice, c->stream);
+        const cudaError_t e2 = cudaStreamSynchronize(c->stream);
+        delete[] tmp;
+        CK(e1);
+        CK(e2);
+    }
+    return LBM_OK;
 }
 
 int lbm_get_lattice(const lbm_ctx *c, lbm_lattice *out)

@@ -92,6 +92,11 @@ struct Phys {
     V gbeta, Tm;
     V omegaT, s_e, s_p;
     V abb_hot, abb_cold;   // 2 w T_wall for the anti-bounce-back (w = 1/6)
+    // Per-node Darcy numbers (lbm_set_darcy_field), or null for the uniform
+    // permeability above: a plane of the compute type (float for the F2
+    // paths), indexed like the state planes; K = Da L2.
+    const void *da;
+    V L2, eFe;                 // L^2 and eps F_eps
 };
 
 // ------------------------------------------------------------ parameters
@@ -125,6 +130,9 @@ inline Phys<V> make_params(const lbm_ctx *c)
     p.s_p = V(L.s_p);
     p.abb_hot = V(2.0 / 6.0 * L.T_hot);
     p.abb_cold = V(2.0 / 6.0 * L.T_cold);
+    p.da = c->d_da;
+    p.L2 = V(L.L * L.L);
+    p.eFe = V(L.eps * L.Feps);
     return p;
 }
 
@@ -280,6 +288,38 @@ struct Macro {
     V nu;  // apparent viscosity chosen by the collision (set by collide)
 };
 
+// Porous coefficients of node k when a per-node Darcy field is set:
+// K = Da L^2, eps/(4K), eps/K, eps F_eps/(2 sqrt K), eps F_eps/sqrt K.
+__device__ __forceinline__ double load_da(const Phys<double> &p, int64_t k) { return ((const double *)p.da)[k]; }
+__device__ __forceinline__ float load_da(const Phys<float> &p, int64_t k) { return ((const float *)p.da)[k]; }
+__device__ __forceinline__ F2 load_da(const Phys<F2> &p, int64_t k)
+{
+    return F2(*reinterpret_cast<const float2 *>((const float *)p.da + k));
+}
+template <class V>
+struct Porous {
+    V heK, eK, c1, eFsK;
+};
+template <class V>
+__device__ __forceinline__ Porous<V> porous_at(const Phys<V> &p, int64_t k)
+{
+    Porous<V> q;
+    if (!p.da) {
+        q.heK = p.half_eps_invK;
+        q.eK = p.eps_invK;
+        q.c1 = p.c1;
+        q.eFsK = p.eFe_isqK;
+        return q;
+    }
+    const V iK = vrcp(load_da(p, k) * p.L2);
+    const V isK = vsqrt(iK);
+    q.heK = V(0.25) * p.eps * iK;
+    q.eK = p.eps * iK;
+    q.c1 = V(0.5) * p.eFe * isK;
+    q.eFsK = p.eFe * isK;
+    return q;
+}
+
 // Density and temperature (Eqs. macro_fluid_density and the D2Q5 zeroth
 // moment), the half-force velocity of Eq. (velo) with buoyancy
 // G = g beta (T - T_m) along +y, and the porous velocity solve
@@ -287,9 +327,10 @@ struct Macro {
 // apparent viscosity of the lagged relaxation time; then the total force
 // F = -eps nu u / K - eps F_eps |u| u / sqrt K + eps G.
 template <class V>
-__device__ __forceinline__ Macro<V> macro(const Phys<V> &p, const V f[9], const V g[5], V tau_prev)
+__device__ __forceinline__ Macro<V> macro(const Phys<V> &p, const V f[9], const V g[5], V tau_prev, int64_t k)
 {
     Macro<V> m;
+    const Porous<V> q = porous_at(p, k);
     const V sax = (f[1] + f[2]) + (f[3] + f[4]);
     const V sdg = (f[5] + f[6]) + (f[7] + f[8]);
     m.rho = f[0] + sax + sdg;
@@ -301,13 +342,13 @@ __device__ __forceinline__ Macro<V> macro(const Phys<V> &p, const V f[9], const 
     const V vx = jx * m.irho;
     const V vy = vfma(p.half_eps, Gy, jy * m.irho);
     m.nu_prev = (tau_prev - V(0.5)) * V(1.0 / 3.0);
-    const V c0 = vfma(p.half_eps_invK, m.nu_prev, V(0.5));
+    const V c0 = vfma(q.heK, m.nu_prev, V(0.5));
     const V vmag = vsqrt(vfma(vx, vx, vy * vy));
-    const V iden = vrcp(c0 + vsqrt(vfma(c0, c0, p.c1 * vmag)));
+    const V iden = vrcp(c0 + vsqrt(vfma(c0, c0, q.c1 * vmag)));
     m.ux = vx * iden;
     m.uy = vy * iden;
     const V umag = vmag * iden;  // |u| = |v| / den
-    const V drag = -vfma(p.eps_invK, m.nu_prev, p.eFe_isqK * umag);
+    const V drag = -vfma(q.eK, m.nu_prev, q.eFsK * umag);
     m.Fx = drag * m.ux;
     m.Fy = vfma(drag, m.uy, p.eps * Gy);
     return m;
@@ -335,11 +376,12 @@ __device__ __forceinline__ F2 apparent(const Phys<F2> &p, F2 gs)
 
 // Full node update in place: f, g become the post-collision populations.
 // Returns the new relaxation time; m receives the macroscopic moments and the
-// apparent lattice viscosity of this collision.
+// apparent lattice viscosity of this collision.  k is the node's offset in a
+// plane (used only to read a per-node Darcy field).
 template <class V>
-__device__ __forceinline__ V collide(const Phys<V> &p, V f[9], V g[5], V tau_prev, Macro<V> &m)
+__device__ __forceinline__ V collide(const Phys<V> &p, V f[9], V g[5], V tau_prev, Macro<V> &m, int64_t k)
 {
-    m = macro<V>(p, f, g, tau_prev);
+    m = macro<V>(p, f, g, tau_prev, k);
     const V rho = m.rho, ux = m.ux, uy = m.uy;
     // raw moments
     const V sax = (f[1] + f[2]) + (f[3] + f[4]);

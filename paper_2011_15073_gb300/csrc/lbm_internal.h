@@ -44,6 +44,7 @@ struct lbm_ctx {
     double *d_part = nullptr;    // per-block partial sums of the residual
     int n_part = 0;
     double *d_nuloc = nullptr;   // local hot-wall Nu [ny]
+    void *d_da = nullptr;        // per-node Darcy numbers (compute type), or null
     bool have_snap = false;
     bool aa_form_o = false;      // in-place layout: state in the odd-step form
     int64_t steps = 0;
@@ -55,6 +56,9 @@ namespace lbm {
 // cudaError_t from cudaGetLastError().
 cudaError_t launch_init(lbm_ctx *c);
 cudaError_t launch_step(lbm_ctx *c);
+// One step of the two-buffer layout between explicit state buffers (same
+// plane geometry as the context's own).
+cudaError_t launch_step_buffers(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst);
 cudaError_t launch_fields(lbm_ctx *c, double *d_out5);
 cudaError_t launch_nusselt(lbm_ctx *c);  // -> d_small[0..1], d_nuloc
 cudaError_t launch_residual(lbm_ctx *c, bool first);  // -> d_small[2..5]

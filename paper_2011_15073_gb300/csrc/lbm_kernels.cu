@@ -65,7 +65,7 @@ __global__ void fields_kernel(const typename Store<PREC>::S *__restrict__ src,
     R f[9], g[5];
     pull<PREC, R, REV>(src, p, x, y, f, g);
     Macro<R> m;
-    collide<R>(p, f, g, R(tsrc[k]), m);
+    collide<R>(p, f, g, R(tsrc[k]), m, k);
     out[q] = double(m.rho);
     out[n + q] = double(m.ux);
     out[2 * n + q] = double(m.uy);
@@ -151,7 +151,7 @@ residual_kernel(const typename Store<PREC>::S *__restrict__ src,
         const int y = (int)(q / p.nx), x = (int)(q - (int64_t)y * p.nx);
         R f[9], g[5];
         pull<PREC, R, REV>(src, p, x, y, f, g);
-        const Macro<R> m = macro<R>(p, f, g, R(tsrc[(int64_t)y * p.pitch + x]));
+        const Macro<R> m = macro<R>(p, f, g, R(tsrc[(int64_t)y * p.pitch + x]), (int64_t)y * p.pitch + x);
         const double v[3] = {double(m.ux), double(m.uy), double(m.T)};
         for (int c = 0; c < 3; c++) {
             const double old = first ? v[c] : snap[c * n + q];
@@ -278,6 +278,22 @@ static cudaError_t step_t(lbm_ctx *c)
 }
 
 template <int PREC>
+static cudaError_t step_buffers_t(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
+{
+    using St = Store<PREC>;
+    if constexpr (PREC == LBM_F64) {
+        step_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
+            (const typename St::S *)src, (typename St::S *)dst, (const typename St::TauS *)tsrc,
+            (typename St::TauS *)tdst, make_params<typename St::R>(c));
+    } else {
+        step2_kernel<PREC><<<node_grid(c, 256), 128, 0, c->stream>>>(
+            (const typename St::S *)src, (typename St::S *)dst, (const float *)tsrc, (float *)tdst,
+            make_params<float>(c), make_params<F2>(c));
+    }
+    return cudaGetLastError();
+}
+
+template <int PREC>
 static cudaError_t fields_t(lbm_ctx *c, double *out)
 {
     using St = Store<PREC>;
@@ -345,6 +361,10 @@ static cudaError_t export_t(lbm_ctx *c, double *out)
 
 cudaError_t launch_init(lbm_ctx *c) { LBM_DISPATCH(init_t, c) }
 cudaError_t launch_step(lbm_ctx *c) { LBM_DISPATCH(step_t, c) }
+cudaError_t launch_step_buffers(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
+{
+    LBM_DISPATCH(step_buffers_t, c, src, dst, tsrc, tdst)
+}
 cudaError_t launch_fields(lbm_ctx *c, double *out) { LBM_DISPATCH(fields_t, c, out) }
 cudaError_t launch_nusselt(lbm_ctx *c) { LBM_DISPATCH(nusselt_t, c) }
 cudaError_t launch_residual(lbm_ctx *c, bool first) { LBM_DISPATCH(residual_t, c, first) }

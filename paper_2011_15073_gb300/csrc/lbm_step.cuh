@@ -20,7 +20,7 @@ __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restr
     R f[9], g[5];
     pull<PREC, R>(src, p, x, y, f, g);
     Macro<R> m;
-    const R tau = collide<R>(p, f, g, R(tsrc[k]), m);
+    const R tau = collide<R>(p, f, g, R(tsrc[k]), m, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) St::st(dst, i * p.plane + k, f[i], R(rest_f(i)));
 #pragma unroll
@@ -78,7 +78,7 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
     g[4] = St::ld2(gs + 4 * P, k + W, float(rest_g(4)));
     const F2 tau_prev(*reinterpret_cast<const float2 *>(tsrc + k));
     Macro<F2> m;
-    const F2 tau = collide<F2>(p2, f, g, tau_prev, m);
+    const F2 tau = collide<F2>(p2, f, g, tau_prev, m, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) St::st2(dst + i * P, k, f[i], float(rest_f(i)));
 #pragma unroll

@@ -66,6 +66,7 @@ SIGNATURES = [
                                 ctypes.POINTER(Opts)]),
     ("lbm_destroy", None, [_VP]),
     ("lbm_get_lattice", ctypes.c_int, [_VP, ctypes.POINTER(Lattice)]),
+    ("lbm_set_darcy_field", ctypes.c_int, [_VP, _D]),
     ("lbm_step", ctypes.c_int, [_VP, ctypes.c_int64]),
     ("lbm_synchronize", ctypes.c_int, [_VP]),
     ("lbm_fields", ctypes.c_int, [_VP, _D, _D, _D, _D, _D]),
@@ -79,6 +80,16 @@ SIGNATURES = [
     ("lbm_set_state", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     ("lbm_get_state_f64", ctypes.c_int, [_VP, _D, _D, _D]),
     ("lbm_set_state_f64", ctypes.c_int, [_VP, _D, _D, _D]),
+    ("lbm_batch_create", ctypes.c_int, [ctypes.POINTER(_VP), _VP, ctypes.c_int, ctypes.POINTER(Opts)]),
+    ("lbm_batch_destroy", None, [_VP]),
+    ("lbm_batch_get_case", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("lbm_batch_step", ctypes.c_int, [_VP, ctypes.c_int64]),
+    ("lbm_batch_run_to_steady", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int64, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int64), _D,
+                                               ctypes.POINTER(ctypes.c_int)]),
+    ("lbm_batch_nusselt", ctypes.c_int, [_VP, _D, _D]),
+    ("lbm_batch_tune", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    ("lbm_adjoint_nu", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]),
     ("lbm_residual_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("lbm_last_cuda_error", ctypes.c_char_p, []),
@@ -152,6 +163,15 @@ def get_lattice(ctx) -> Lattice:
     return L
 
 
+def set_darcy_field(ctx, Da):
+    """Per-node Darcy numbers [ny][nx] (None: back to the uniform Da)."""
+    if Da is None:
+        _check(lib().lbm_set_darcy_field(ctx, None), "lbm_set_darcy_field")
+        return
+    Da = np.ascontiguousarray(Da, dtype=np.float64)
+    _check(lib().lbm_set_darcy_field(ctx, _ptr(Da)), "lbm_set_darcy_field")
+
+
 def step(ctx, k: int):
     _check(lib().lbm_step(ctx, int(k)), "lbm_step")
 
@@ -184,6 +204,16 @@ def residual(ctx) -> float:
 def residual_noalloc(ctx, d_snapshot: int, first: bool, d_result: int):
     """Allocation-free residual: device pointers in, results left on the device."""
     _check(lib().lbm_residual_noalloc(ctx, d_snapshot, 1 if first else 0, d_result), "lbm_residual_noalloc")
+
+
+def adjoint_nu(ctx, nx, ny, steps: int, ckpt_every: int = 500, from_rest: bool = True):
+    """(J, dJ/dDa[ny][nx], dJ/dn, dJ/dRa, peak device bytes) by the discrete adjoint."""
+    J = ctypes.c_double(); dn = ctypes.c_double(); dRa = ctypes.c_double(); pk = ctypes.c_double()
+    dDa = np.empty((ny, nx))
+    _check(lib().lbm_adjoint_nu(ctx, int(steps), int(ckpt_every), 1 if from_rest else 0, ctypes.byref(J),
+                                _ptr(dDa), ctypes.byref(dn), ctypes.byref(dRa), ctypes.byref(pk)),
+           "lbm_adjoint_nu")
+    return J.value, dDa, dn.value, dRa.value, pk.value
 
 
 def run_to_steady(ctx, tol: float, max_steps: int):
@@ -226,6 +256,69 @@ def strerror(code: int) -> str:
     return lib().lbm_strerror(code).decode()
 
 
+class Case(ctypes.Structure):
+    """Mirror of ``lbm_case``."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("n", ctypes.c_double),
+                ("Da", ctypes.c_double), ("Ra", ctypes.c_double), ("Pr", ctypes.c_double),
+                ("porosity", ctypes.c_double)]
+
+
+class Batch:
+    """Owning wrapper of an ``lbm_batch`` (a sweep of independent cavities)."""
+
+    def __init__(self, cases, **opts):
+        arr = (Case * len(cases))(*[Case(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"],
+                                         c.get("porosity", 0.6)) for c in cases])
+        self.cases = list(cases)
+        self.n = len(cases)
+        o = default_opts(**opts)
+        h = _VP()
+        _check(lib().lbm_batch_create(ctypes.byref(h), ctypes.cast(arr, _VP), self.n, ctypes.byref(o)),
+               "lbm_batch_create")
+        self.h = h.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def case_ctx(self, i):
+        c = _VP()
+        _check(lib().lbm_batch_get_case(self.h, i, ctypes.byref(c)), "lbm_batch_get_case")
+        return c.value
+
+    def step(self, k):
+        _check(lib().lbm_batch_step(self.h, int(k)), "lbm_batch_step")
+
+    def run_to_steady(self, tol, max_steps, graph_mode=1):
+        steps = (ctypes.c_int64 * self.n)(); res = np.empty(self.n); why = (ctypes.c_int * self.n)()
+        _check(lib().lbm_batch_run_to_steady(self.h, tol, int(max_steps), graph_mode, steps, _ptr(res), why),
+               "lbm_batch_run_to_steady")
+        return list(steps), res, list(why)
+
+    def nusselt(self):
+        hot = np.empty(self.n); cold = np.empty(self.n)
+        _check(lib().lbm_batch_nusselt(self.h, _ptr(hot), _ptr(cold)), "lbm_batch_nusselt")
+        return hot, cold
+
+    def tune(self, steps=200):
+        t = ctypes.c_int()
+        _check(lib().lbm_batch_tune(self.h, int(steps), ctypes.byref(t)), "lbm_batch_tune")
+        return t.value
+
+
 class Cavity:
     """Owning wrapper of one context with the calls above as methods."""
 
@@ -253,6 +346,12 @@ class Cavity:
 
     def lattice(self):
         return get_lattice(self.ctx)
+
+    def set_darcy_field(self, Da):
+        set_darcy_field(self.ctx, Da)
+
+    def adjoint_nu(self, steps, ckpt_every=500, from_rest=True):
+        return adjoint_nu(self.ctx, self.nx, self.ny, steps, ckpt_every, from_rest)
 
     def step(self, k):
         step(self.ctx, k)

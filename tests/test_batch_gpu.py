@@ -1,0 +1,121 @@
+"""The batched sweep (lbm_batch_*) against single contexts and the oracle.
+
+A batch steps many cavities of different sizes in one launch per step, one
+row tile per block; each case must evolve exactly as it would alone:
+* FP32: bit-for-bit equal to the same case stepped as a single context
+  (the batched kernel runs the same tile code on the same numbers);
+* FP64: within the parity bounds of test_parity_gpu against the oracle;
+* run-to-steady (host-looped graph and single device-looped graph): the same
+  per-case stopping step and Nusselt numbers as lbm_run_to_steady alone.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    dict(nx=17, ny=13, n=0.6, Da=1e-2, Ra=1e5, Pr=6.2, porosity=0.6),
+    dict(nx=130, ny=67, n=1.0, Da=1e-1, Ra=1e3, Pr=10.0, porosity=0.6),
+    dict(nx=64, ny=64, n=0.8, Da=1e-3, Ra=1e4, Pr=6.2, porosity=0.6),
+    dict(nx=258, ny=9, n=1.4, Da=1e-3, Ra=1e5, Pr=6.2, porosity=0.6),
+]
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import oracle
+    from paper_2011_15073_gb300 import inputs, lbm
+    oracle.build()
+    lbm.lib()
+    return oracle, inputs, lbm
+
+
+def start_states(oracle, inputs, cases):
+    out = []
+    for i, c in enumerate(cases):
+        ref = oracle.Cavity.from_params(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"],
+                                        porosity=c["porosity"], clamp_mode=1)
+        out.append((ref, inputs.perturbed_state(ref.get_state(), seed=100 + i)))
+    return out
+
+
+@pytest.mark.parametrize("tuned", [False, True])
+def test_batch_fp32_equals_single_contexts(mods, tuned):
+    oracle, inputs, lbm = mods
+    st = start_states(oracle, inputs, CASES)
+    with lbm.Batch(CASES, prec="f32", clamp_mode=1) as b:
+        for i, (_, s) in enumerate(st):
+            lbm.set_state_f64(b.case_ctx(i), *s)
+        if tuned:
+            b.tune(20)   # whatever block size it picks, the results may not change
+        b.step(37)
+        got = [lbm.get_state_f64(b.case_ctx(i), c["nx"], c["ny"]) for i, c in enumerate(CASES)]
+    for i, c in enumerate(CASES):
+        with lbm.Cavity(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec="f32",
+                        clamp_mode=1) as cav:
+            cav.set_state_f64(*st[i][1])
+            cav.step(37)
+            want = cav.get_state_f64()
+        for a, w in zip(got[i], want):
+            assert np.array_equal(a, w), i
+
+
+def test_batch_fp64_parity_with_oracle(mods):
+    oracle, inputs, lbm = mods
+    st = start_states(oracle, inputs, CASES)
+    with lbm.Batch(CASES, prec="f64", clamp_mode=1) as b:
+        for i, (_, s) in enumerate(st):
+            lbm.set_state_f64(b.case_ctx(i), *s)
+        b.step(60)
+        got = [lbm.get_state_f64(b.case_ctx(i), c["nx"], c["ny"]) for i, c in enumerate(CASES)]
+    for i, (ref, s) in enumerate(st):
+        ref.set_state(*s)
+        ref.step(60)
+        f_r, g_r, t_r = ref.get_state()
+        f, g, tau = got[i]
+        assert np.max(np.abs(f - f_r) / np.abs(f_r)) < 1e-12
+        assert np.max(np.abs(g - g_r) / np.abs(g_r)) < 1e-12
+        assert np.max(np.abs(tau - t_r) / t_r) < 1e-10
+
+
+@pytest.mark.parametrize("graph_mode", [0, 1])
+def test_batch_run_to_steady_matches_single_runs(mods, graph_mode):
+    _, _, lbm = mods
+    cases = [dict(nx=24, ny=24, n=0.8, Da=1e-2, Ra=1e3, Pr=6.2, porosity=0.6),
+             dict(nx=32, ny=20, n=1.0, Da=1e-1, Ra=1e4, Pr=6.2, porosity=0.6),
+             dict(nx=20, ny=28, n=0.6, Da=1e-3, Ra=1e4, Pr=6.2, porosity=1.0)]
+    with lbm.Batch(cases, prec="f64", clamp_mode=1, resid_interval=200) as b:
+        steps, res, why = b.run_to_steady(1e-8, 400_000, graph_mode=graph_mode)
+        hot, cold = b.nusselt()
+    assert all(w == 0 for w in why), (steps, res, why)
+    for i, c in enumerate(cases):
+        with lbm.Cavity(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec="f64",
+                        clamp_mode=1, resid_interval=200) as cav:
+            s1, r1, w1 = cav.run_to_steady(1e-8, 400_000)
+            h1, c1, _ = cav.nusselt()
+        assert (steps[i], why[i]) == (s1, w1)
+        assert res[i] == pytest.approx(r1, rel=1e-12)
+        assert hot[i] == h1 and cold[i] == c1
+
+
+def test_batch_run_stops_at_max_steps(mods):
+    _, _, lbm = mods
+    cases = [dict(nx=16, ny=16, n=0.6, Da=1e-2, Ra=1e5, Pr=6.2, porosity=0.6)] * 2
+    with lbm.Batch(cases, prec="f32", resid_interval=100) as b:
+        steps, res, why = b.run_to_steady(0.0, 1000, graph_mode=1)
+    assert steps == [1000, 1000] and why == [2, 2]
+
+
+def test_batch_tune_keeps_states(mods):
+    oracle, inputs, lbm = mods
+    st = start_states(oracle, inputs, CASES)
+    with lbm.Batch(CASES, prec="f32", clamp_mode=1) as b:
+        for i, (_, s) in enumerate(st):
+            lbm.set_state_f64(b.case_ctx(i), *s)
+        before = [lbm.get_state_f64(b.case_ctx(i), c["nx"], c["ny"]) for i, c in enumerate(CASES)]
+        t = b.tune(20)
+        after = [lbm.get_state_f64(b.case_ctx(i), c["nx"], c["ny"]) for i, c in enumerate(CASES)]
+    assert t in (64, 128, 256)
+    for x, y in zip(before, after):
+        for a, w in zip(x, y):
+            assert np.array_equal(a, w)

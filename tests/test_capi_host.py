@@ -84,6 +84,13 @@ def test_init_rejects_bad_options(L, field, value, code):
     assert L.lbm_init(ctypes.byref(h), 8, 8, 0.6, 1e-2, 1e5, 6.2, 0.6, ctypes.byref(o)) == code
 
 
+def test_darcy_field_rejects_bad_values(L):
+    import numpy as np
+    from paper_2011_15073_gb300 import lbm
+    bad = np.full(4, -1.0)
+    assert L.lbm_set_darcy_field(None, bad.ctypes.data_as(lbm._D)) == -1
+
+
 def test_null_context_is_rejected(L):
     assert L.lbm_step(None, 1) == -1
     assert L.lbm_nusselt(None, None, None, None) == -1

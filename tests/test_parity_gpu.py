@@ -269,3 +269,161 @@ def test_one_step_parity_literal_clamp(mods, prec, tol_f, tol_g, case, size):
         assert ef[amb].max() < 1e-3 and eg[amb].max() < tol_g
     assert amb.mean() < 0.5   # most nodes are unambiguous, so the strict bound is exercised
     check_tau(tau, t_r, gam_r, ref.lat, prec, df)
+
+
+@LAYOUTS
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_darcy_field_parity(mods, prec, layout):
+    """A per-node Darcy field, log-uniform in [1e-3, 1e-1], against the oracle
+    with the same field (FP32 with the continuous law, as above)."""
+    oracle, inputs, lbm = mods
+    nx, ny = 130, 67
+    c = dict(CASES["thinning"], clamp_mode=1 if prec == "f32" else 0)
+    Da = inputs.darcy_field(2011, nx, ny)
+    ref = oracle_for(oracle, nx, ny, c)
+    ref.set_darcy_field(Da)
+    state = inputs.perturbed_state(ref.get_state(), seed=77)
+    if prec == "f32":
+        state = [a.astype(np.float32).astype(np.float64) for a in state]
+    ref.set_state(*state)
+    ref.step(59)
+    f59_r, g59_r, _ = ref.get_state()
+    gam_r = ref.fields()["gamma"]
+    ref.step(1)
+    f_r, g_r, t_r = ref.get_state()
+    with gpu_for(lbm, nx, ny, c, prec, layout) as cav:
+        cav.set_darcy_field(Da)
+        cav.set_state_f64(*state)
+        cav.step(59)
+        f59, g59, _ = cav.get_state_f64()
+        cav.step(1)
+        f, g, tau = cav.get_state_f64()
+    tol = 1e-12 if prec == "f64" else 5e-5
+    assert rel_err(f, f_r, W9) < tol and rel_err(g, g_r, W5) < tol
+    df = max(np.abs(f59 - f59_r).max(), np.abs(g59 - g59_r).max())
+    check_tau(tau, t_r, gam_r, ref.lat, prec, df)
+
+
+def test_zero_steps_and_repeat_calls(mods):
+    oracle, inputs, lbm = mods
+    c = CASES["thinning"]
+    ref = oracle_for(oracle, 17, 13, c)
+    state = inputs.perturbed_state(ref.get_state(), seed=5)
+    with gpu_for(lbm, 17, 13, c, "f64") as cav:
+        cav.set_state_f64(*state)
+        cav.step(0)
+        f, g, tau = cav.get_state_f64()
+        assert np.array_equal(f, state[0]) and np.array_equal(g, state[1])
+        cav.step(3)
+        cav.step(4)
+        a = cav.get_state_f64()
+    ref.set_state(*state)
+    ref.step(7)
+    b = ref.get_state()
+    for x, y in zip(a[:2], b[:2]):
+        assert np.max(np.abs(x - y) / np.abs(y)) < 1e-13
+    assert np.max(np.abs(a[2] - b[2]) / b[2]) < 1e-10   # tau: see check_tau
+
+
+@LAYOUTS
+def test_native_state_roundtrip(mods, layout):
+    _, inputs, lbm = mods
+    c = CASES["thinning"]
+    for prec in ("f64", "f32", "bf16d", "f16d"):
+        with gpu_for(lbm, 33, 21, c, prec, layout) as cav:
+            cav.step(5)
+            buf = np.empty(cav.state_bytes(), dtype=np.uint8)
+            cav.get_state(buf)
+            cav.step(5)
+            after = np.empty_like(buf)
+            cav.get_state(after)
+            cav.set_state(buf)
+            cav.step(5)
+            again = np.empty_like(buf)
+            cav.get_state(again)
+            assert np.array_equal(after, again), prec
+
+
+def test_residual_matches_definition(mods):
+    oracle, inputs, lbm = mods
+    c = CASES["thinning"]
+    nx, ny = 40, 30
+    ref = oracle_for(oracle, nx, ny, c)
+    state = inputs.perturbed_state(ref.get_state(), seed=9)
+    ref.set_state(*state)
+    with gpu_for(lbm, nx, ny, c, "f64") as cav:
+        cav.set_state_f64(*state)
+        assert math.isinf(cav.residual())
+        cav.step(50)
+        r = cav.residual()
+    a = ref.fields()
+    ref.step(50)
+    b = ref.fields()
+    expect = max(np.linalg.norm(b[k] - a[k]) / np.linalg.norm(b[k]) for k in ("ux", "uy", "T"))
+    assert r == pytest.approx(expect, rel=1e-9)
+
+
+def test_nonfinite_state_is_reported(mods):
+    oracle, inputs, lbm = mods
+    c = CASES["thinning"]
+    ref = oracle_for(oracle, 16, 16, c)
+    f, g, tau = ref.get_state()
+    f = f.copy()
+    f[3, 7, 9] = np.nan
+    with gpu_for(lbm, 16, 16, c, "f32") as cav:
+        cav.set_state_f64(f, g, tau)
+        with pytest.raises(lbm.LBMError) as e:
+            cav.residual()
+        assert e.value.code == -3
+
+
+@pytest.mark.parametrize("prec,layout", [("f32", 0), ("f64", 0), ("f32", 1)])
+def test_full_size_sampled_parity(mods, prec, layout):
+    """4096 x 4096, the benchmark's launch configuration: the state after k
+    steps at a node depends only on the (2k+1)^2 nodes around it, so the
+    oracle recomputes sampled nodes one window at a time.  A window that
+    touches a real wall keeps it; its artificial edges stay more than k nodes
+    away from the sampled node."""
+    oracle, inputs, lbm = mods
+    N, k, h = 4096, 3, 5
+    c = CASES["thinning"]
+    dt = np.float64 if prec == "f64" else np.float32
+    lat_full = oracle.map_params(N, N, c["n"], c["Da"], c["Ra"], c["Pr"], porosity=c["porosity"])
+    rest = oracle.Cavity(oracle.map_params(4, 4, 1.0, 1e-2, 1e5, 6.2))
+    f0, g0, t0 = rest.get_state()
+    rng = np.random.default_rng(4096)
+    f = (f0[:, :1, :1] * (1 + rng.uniform(-1e-3, 1e-3, (9, N, N)))).astype(dt)
+    g = (g0[:, :1, :1] * (1 + rng.uniform(-1e-3, 1e-3, (5, N, N)))).astype(dt)
+    tau = np.full((N, N), lat_full.tau0, dtype=dt)
+    with gpu_for(lbm, N, N, c, prec, layout) as cav:
+        host = np.concatenate([f.reshape(-1), g.reshape(-1), tau.reshape(-1)])
+        cav.set_state(host.view(np.uint8))
+        cav.step(k)
+        out = np.empty_like(host)
+        cav.get_state(out.view(np.uint8))
+    nn = N * N
+    fo = out[:9 * nn].reshape(9, N, N)
+    go = out[9 * nn:14 * nn].reshape(5, N, N)
+    to = out[14 * nn:].reshape(N, N)
+    samples = [(0, 0), (N - 1, 0), (0, N - 1), (N - 1, N - 1), (N // 2, 0), (0, N // 2),
+               (N - 1, N // 2), (N // 2, N - 1)] + [tuple(rng.integers(0, N, 2)) for _ in range(24)]
+    tol = 1e-12 if prec == "f64" else 2e-6
+    for (x, y) in samples:
+        x0 = 0 if x < h + k else (N - (2 * h + 1) if x > N - 1 - h - k else x - h)
+        y0 = 0 if y < h + k else (N - (2 * h + 1) if y > N - 1 - h - k else y - h)
+        w = 2 * h + 1
+        lat = lat_full.copy()
+        lat.nx = lat.ny = w
+        win = oracle.Cavity(lat)
+        win.set_state(f[:, y0:y0 + w, x0:x0 + w].astype(np.float64),
+                      g[:, y0:y0 + w, x0:x0 + w].astype(np.float64),
+                      tau[y0:y0 + w, x0:x0 + w].astype(np.float64))
+        win.step(k - 1)
+        gam_w = win.fields()["gamma"]
+        win.step(1)
+        fw, gw, tw = win.get_state()
+        lx, ly = x - x0, y - y0
+        assert np.max(np.abs(fo[:, y, x] - fw[:, ly, lx]) / W9[:, 0, 0]) < tol, (x, y)
+        assert np.max(np.abs(go[:, y, x] - gw[:, ly, lx]) / W5[:, 0, 0]) < tol, (x, y)
+        df = max(np.max(np.abs(fo[:, y, x] - fw[:, ly, lx])), np.max(np.abs(go[:, y, x] - gw[:, ly, lx])))
+        check_tau(np.array([to[y, x]], float), tw[ly, lx:lx + 1], gam_w[ly, lx:lx + 1], lat, prec, df)
