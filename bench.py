@@ -31,7 +31,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_NODE = {"f64": 240, "f32": 120, "bf16d": 64, "f16d": 64}
+BYTES_PER_NODE = {"f64": 240, "f32": 120, "f32d": 120, "bf16d": 64, "f16d": 64}
 CASE = dict(n=0.6, Da=1e-3, Ra=1e5, Pr=6.2, porosity=0.6)
 FALLBACK_HBM_GBS = 6800.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
@@ -87,7 +87,7 @@ def parse():
                     help="fused time steps per bench step (the convergence-check interval)")
     ap.add_argument("--variant-delta", type=int, default=200)
     ap.add_argument("--prec", default="f32")
-    ap.add_argument("--variants", default="f64,bf16d,f16d",
+    ap.add_argument("--variants", default="f64,f32d,bf16d,f16d",
                     help="other storage precisions measured beside the headline ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -112,6 +112,197 @@ PAPER_TABLES = [
     ("case3", dict(n=0.6, Da=1e-2, Ra=1e3, Pr=6.2), 1.068697),
     ("case3", dict(n=0.6, Da=1e-2, Ra=1e4, Pr=6.2), 4.411946),
 ]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if k in d:
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler for the SM clock and throttle reasons (read-only)."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def clk_summary_max(clk):
+    try:
+        return clk.summary()["sm_max_mhz"]
+    except Exception:
+        return None
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def time_ours(lbm, torch, N, prec, steps, warmup, delta, stream):
+    """Device-resident run: returns (seconds for `steps` bench steps, avg fused
+    kernel seconds, kernels launched in the timed region, Nu)."""
+    cav = lbm.Cavity(N, N, prec=prec, cuda_stream=stream, **CASE)
+    try:
+        cav.residual()   # first call stores the snapshot
+        for _ in range(warmup):
+            cav.step(delta)
+            cav.nusselt()
+            cav.residual()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        nu = None
+        for s in range(steps):
+            ev[s][0].record(stream)
+            cav.step(delta)
+            ev[s][1].record(stream)
+            nu = cav.nusselt()[0]
+            cav.residual()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        total = t0.elapsed_time(t1) / 1e3
+        kern = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / (steps * delta)
+        launches = steps * (delta + 1 + 2)
+        return total, kern, launches, nu
+    finally:
+        cav.close()
+
+
+def time_e2e(lbm, torch, N, prec, steps, warmup, delta, stream):
+    """End to end through the C ABI with host buffers: each bench step uploads
+    the state from pinned host memory, runs `delta` fused steps and reads the
+    hot-wall Nusselt number back."""
+    cav = lbm.Cavity(N, N, prec=prec, cuda_stream=stream, **CASE)
+    try:
+        nbytes = cav.state_bytes()
+        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        cav.get_state(host)
+        for _ in range(warmup):
+            cav.set_state(host)
+            cav.step(delta)
+            cav.nusselt()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(steps):
+            cav.set_state(host)
+            cav.step(delta)
+            cav.nusselt()
+        dt = time.perf_counter() - t
+        return dt, nbytes, 8
+    finally:
+        cav.close()
+
+
+def cpu_baseline(N_sample=1024, steps=150):
+    """The FP64 oracle as it stands, on all host cores (OpenMP), on a bounded
+    sample of the workload: an N_sample^2 cavity with the same parameters."""
+    import oracle
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    oracle.build()
+    c = oracle.Cavity.from_params(N_sample, N_sample, CASE["n"], CASE["Da"], CASE["Ra"], CASE["Pr"],
+                                  porosity=CASE["porosity"])
+    c.step(1)
+    t = time.perf_counter()
+    c.step(steps)
+    dt = time.perf_counter() - t
+    mlups = N_sample * N_sample * steps / dt / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
+            "sample": f"FP64 oracle, {N_sample}x{N_sample} cavity, {steps} steps, same (n, Da, Ra, Pr, porosity)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    steps_each = 10
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    Ns = 1024
+    c = oracle.Cavity.from_params(Ns, Ns, CASE["n"], CASE["Da"], CASE["Ra"], CASE["Pr"], porosity=CASE["porosity"])
+    for _ in range(args.warmup):
+        c.step(steps_each)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        c.step(steps_each)
+    dt = time.perf_counter() - t
+    mlups = Ns * Ns * steps_each * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": "fused MRT step MLUPS", "value": mlups, "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"cavity {args.N}x{args.N} (timed on a {Ns}x{Ns} sample), "
+                                   f"n={CASE['n']}, Da={CASE['Da']}, Ra={CASE['Ra']}, Pr={CASE['Pr']}, "
+                                   f"porosity={CASE['porosity']}",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle",
+                             "sample": f"{Ns}x{Ns} cavity, {steps_each} steps per bench step"},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
 
 
 def run_until_nu_settles(cav, max_steps, chunk=20000, window=6, rel=1e-6):
@@ -169,7 +360,7 @@ def study_precision(args):
         case = dict(n=n, Da=1e-2, Ra=1e5, Pr=6.2, porosity=0.6)
         res = {}
         S = None
-        for prec in ("f64", "f32", "f16d", "bf16d"):
+        for prec in ("f64", "f32", "f32d", "f16d", "bf16d"):
             t = time.perf_counter()
             with lbm.Cavity(N, N, prec=prec, resid_interval=1000, clamp_mode=1, **case) as cav:
                 if prec == "f64":

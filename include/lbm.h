@@ -50,9 +50,10 @@ enum {
 
 /* Storage precision of the distributions.  Arithmetic is FP64 for LBM_F64
  * and FP32 otherwise.  The *D forms store the deviation of each population
- * from its rest-state value (w_i for the flow, w_i T_m for the heat) in 16
- * bits; the per-node relaxation time is then stored as FP32. */
-typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_BF16D = 2, LBM_F16D = 3 } lbm_prec;
+ * from its rest-state value (w_i for the flow, w_i T_m for the heat): in 16
+ * bits for BF16D and F16D, in 32 bits for F32D; the per-node relaxation time
+ * is then stored as FP32. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_BF16D = 2, LBM_F16D = 3, LBM_F32D = 4 } lbm_prec;
 
 /* Options; lbm_default_opts() fills the defaults listed per field. */
 typedef struct {
@@ -76,7 +77,8 @@ typedef struct {
     double stag_floor; /* lbm_run_to_steady stops on stagnation only
                           below this residual (the storage's noise
                           floor); < 0: 0 for F64 (never), 1e-6 for
-                          F32, 1e-2 for F16D, 1e-1 for BF16D         [-1]   */
+                          F32 and F32D, 1e-2 for F16D, 1e-1 for
+                          BF16D                                      [-1]   */
 } lbm_opts;
 
 /* Lattice-unit parameters the library derived from the problem groups

@@ -301,6 +301,7 @@ extern "C" int lbm_adjoint_nu(lbm_ctx *c, int64_t steps, int ckpt_every, int fro
     switch (c->opts.prec) {
     case LBM_F64: return run_adjoint<LBM_F64>(c, steps, ckpt_every, from_rest, J, dDa, dn, dRa, peak_bytes);
     case LBM_F32: return run_adjoint<LBM_F32>(c, steps, ckpt_every, from_rest, J, dDa, dn, dRa, peak_bytes);
+    case LBM_F32D: return run_adjoint<LBM_F32D>(c, steps, ckpt_every, from_rest, J, dDa, dn, dRa, peak_bytes);
     default: return LBM_ERR_UNSUPPORTED;
     }
 }

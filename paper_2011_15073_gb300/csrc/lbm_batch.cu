@@ -182,7 +182,8 @@ cudaError_t launch_batch_step(lbm_batch *b, int parity)
     case LBM_F64: batch_step_kernel<LBM_F64><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
     case LBM_F32: batch_step_kernel<LBM_F32><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
     case LBM_BF16D: batch_step_kernel<LBM_BF16D><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
-    default: batch_step_kernel<LBM_F16D><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
+    case LBM_F16D: batch_step_kernel<LBM_F16D><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
+    default: batch_step_kernel<LBM_F32D><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
     }
     return cudaGetLastError();
 }
@@ -190,7 +191,7 @@ cudaError_t launch_batch_step(lbm_batch *b, int parity)
 double default_floor(const lbm_opts &o)
 {
     if (o.stag_floor >= 0) return o.stag_floor;
-    return o.prec == LBM_F64 ? 0.0 : (o.prec == LBM_F32 ? 1e-6 : (o.prec == LBM_F16D ? 1e-2 : 1e-1));
+    return o.prec == LBM_F64 ? 0.0 : ((o.prec == LBM_F32 || o.prec == LBM_F32D) ? 1e-6 : (o.prec == LBM_F16D ? 1e-2 : 1e-1));
 }
 
 // Enqueue one chunk: `delta` steps of every active case, their residuals and

@@ -23,7 +23,7 @@ static thread_local char g_last_cuda[256] = "";
 
 namespace {
 
-size_t store_elem(int prec) { return prec == LBM_F64 ? 8 : (prec == LBM_F32 ? 4 : 2); }
+size_t store_elem(int prec) { return prec == LBM_F64 ? 8 : ((prec == LBM_F32 || prec == LBM_F32D) ? 4 : 2); }
 size_t tau_elem(int prec) { return prec == LBM_F64 ? 8 : 4; }
 
 // Mapping of the non-dimensional problem to lattice units.  The paper defers
@@ -45,7 +45,7 @@ int map_lattice(int nx, int ny, double n, double Da, double Ra, double Pr, doubl
     if (nx < 2 || ny < 2 || ny > 65535 || nx > (1 << 30) || !(n > 0) || !(Da > 0) || !(Ra > 0) || !(Pr > 0) || !(porosity > 0) ||
         porosity > 1 || !isfinite(n) || !isfinite(Da) || !isfinite(Ra) || !isfinite(Pr))
         return LBM_ERR_ARG;
-    if (o.prec < LBM_F64 || o.prec > LBM_F16D || !(o.Ma > 0) || o.Ma > 1 ||
+    if (o.prec < LBM_F64 || o.prec > LBM_F32D || !(o.Ma > 0) || o.Ma > 1 ||
         (o.clamp_mode != 0 && o.clamp_mode != 1) || (o.porous_model != 0 && o.porous_model != 1) ||
         !(o.s_e > 0) || !(o.s_e < 2) || !(o.s_p > 0) || !(o.s_p < 2) || o.resid_interval < 1 ||
         o.device < -1)
@@ -114,7 +114,8 @@ double stag_floor(const lbm_ctx *c)
     if (c->opts.stag_floor >= 0) return c->opts.stag_floor;
     switch (c->opts.prec) {
     case LBM_F64: return 0.0;
-    case LBM_F32: return 1e-6;
+    case LBM_F32:
+    case LBM_F32D: return 1e-6;
     case LBM_F16D: return 1e-2;
     default: return 1e-1;
     }

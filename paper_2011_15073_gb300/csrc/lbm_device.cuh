@@ -176,6 +176,22 @@ struct Store<LBM_F32> {
     }
 };
 template <>
+struct Store<LBM_F32D> {
+    using S = float;
+    using R = float;
+    using TauS = float;
+    static __device__ __forceinline__ R ld(const S *p, int64_t k, R rest) { return rest + p[k]; }
+    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest) { p[k] = v - rest; }
+    static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float rest)
+    {
+        return F2(*reinterpret_cast<const float2 *>(p + k)) + F2(rest);
+    }
+    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest)
+    {
+        *reinterpret_cast<float2 *>(p + k) = (v - F2(rest)).v;
+    }
+};
+template <>
 struct Store<LBM_BF16D> {
     using S = __nv_bfloat16;
     using R = float;

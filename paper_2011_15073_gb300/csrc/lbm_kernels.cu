@@ -356,6 +356,7 @@ static cudaError_t export_t(lbm_ctx *c, double *out)
     case LBM_F32: return fn<LBM_F32>(__VA_ARGS__);                 \
     case LBM_BF16D: return fn<LBM_BF16D>(__VA_ARGS__);             \
     case LBM_F16D: return fn<LBM_F16D>(__VA_ARGS__);               \
+    case LBM_F32D: return fn<LBM_F32D>(__VA_ARGS__);               \
     default: return cudaErrorInvalidValue;                         \
     }
 

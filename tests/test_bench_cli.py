@@ -1,0 +1,29 @@
+"""bench.py keeps its command-line contract (CPU part): the reference arm
+runs and prints one JSON line with the keys the benchmark contract names."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0
+
+
+def test_bench_defines_every_leg():
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    for fn in ("def time_ours", "def time_e2e", "def cpu_baseline", "def run_reference", "def hbm_peak",
+               "def dist_env", "class Clocks", "def study_tables", "def study_precision", "def study_batch",
+               "def study_adjoint", "def main"):
+        assert fn in src, fn

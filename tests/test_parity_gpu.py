@@ -101,7 +101,7 @@ def test_lattice_mapping_matches_oracle(mods):
         assert L.clamp_mode == ref.clamp_mode
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "bf16d", "f16d"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "f32d", "bf16d", "f16d"])
 def test_initial_state_is_rest_state(mods, prec):
     oracle, _, lbm = mods
     c = CASES["thinning"]
@@ -172,9 +172,10 @@ def test_fp64_parity_covers_both_clamp_branches(mods):
 
 
 @LAYOUTS
+@pytest.mark.parametrize("prec", ["f32", "f32d"])
 @pytest.mark.parametrize("case", ["thinning", "darcy", "thickening"])
 @pytest.mark.parametrize("size", [(17, 13), (130, 67)], ids=lambda s: f"{s[0]}x{s[1]}")
-def test_fp32_step_parity(mods, case, size, layout):
+def test_fp32_step_parity(mods, case, size, layout, prec):
     oracle, inputs, lbm = mods
     nx, ny = size
     c = dict(CASES[case], clamp_mode=1)
@@ -187,7 +188,7 @@ def test_fp32_step_parity(mods, case, size, layout):
     gam_r = ref.fields()["gamma"]
     ref.step(1)
     f_r, g_r, t_r = ref.get_state()
-    with gpu_for(lbm, nx, ny, c, "f32", layout) as cav:
+    with gpu_for(lbm, nx, ny, c, prec, layout) as cav:
         cav.set_state_f64(*state)
         cav.step(99)
         f99, g99, _ = cav.get_state_f64()
@@ -197,7 +198,7 @@ def test_fp32_step_parity(mods, case, size, layout):
     assert rel_err(f, f_r, W9) < 5e-5
     assert rel_err(g, g_r, W5) < 5e-5
     df = max(np.abs(f99 - f99_r).max(), np.abs(g99 - g99_r).max())
-    check_tau(tau, t_r, gam_r, ref.lat, "f32", df)
+    check_tau(tau, t_r, gam_r, ref.lat, prec, df)
     h_r = ref.nusselt()[0]
     assert abs(hot - h_r) <= 1e-4 * abs(h_r)
 
@@ -329,7 +330,7 @@ def test_zero_steps_and_repeat_calls(mods):
 def test_native_state_roundtrip(mods, layout):
     _, inputs, lbm = mods
     c = CASES["thinning"]
-    for prec in ("f64", "f32", "bf16d", "f16d"):
+    for prec in ("f64", "f32", "f32d", "bf16d", "f16d"):
         with gpu_for(lbm, 33, 21, c, prec, layout) as cav:
             cav.step(5)
             buf = np.empty(cav.state_bytes(), dtype=np.uint8)
