@@ -87,7 +87,7 @@ def parse():
                     help="fused time steps per bench step (the convergence-check interval)")
     ap.add_argument("--variant-delta", type=int, default=200)
     ap.add_argument("--prec", default="f32")
-    ap.add_argument("--variants", default="f64,f32d,bf16d,f16d",
+    ap.add_argument("--variants", default="f64,f32d,f32@aa,bf16d,f16d",
                     help="other storage precisions measured beside the headline ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -196,10 +196,10 @@ def dist_env():
     return rank, world, local
 
 
-def time_ours(lbm, torch, N, prec, steps, warmup, delta, stream):
+def time_ours(lbm, torch, N, prec, steps, warmup, delta, stream, layout=0):
     """Device-resident run: returns (seconds for `steps` bench steps, avg fused
     kernel seconds, kernels launched in the timed region, Nu)."""
-    cav = lbm.Cavity(N, N, prec=prec, cuda_stream=stream, **CASE)
+    cav = lbm.Cavity(N, N, prec=prec, cuda_stream=stream, layout=layout, **CASE)
     try:
         cav.residual()   # first call stores the snapshot
         for _ in range(warmup):
@@ -395,7 +395,9 @@ def study_batch(args):
     max_steps = args.study_max_steps if args.study_max_steps != 3_000_000 else 1_000_000
     cl = [dict(nx=c["N"], ny=c["N"], n=c["n"], Da=c["Da"], Ra=c["Ra"], Pr=6.2, porosity=0.6)
           for c in inputs.sweep_cases(2011)]
-    opts = dict(prec="f32", clamp_mode=1, resid_interval=1000)
+    # FP32 storage cannot bring the residual to 1e-8 (its rounding keeps it
+    # near 1e-5): stagnation below 1e-4 ends a case
+    opts = dict(prec="f32", clamp_mode=1, resid_interval=1000, stag_floor=1e-4)
     with lbm.Batch(cl, **opts) as b:
         t = time.perf_counter()
         threads = b.tune(200)
@@ -434,7 +436,9 @@ def study_adjoint(args):
     Darcy field log-uniform in [1e-3, 1e-1] (seed 2011), by the discrete
     adjoint with checkpoints every 500 steps; checked against FP64 central
     differences (h = 1e-4 in log Da) on 16 random nodes and one random
-    direction, and against the FP64 adjoint."""
+    direction, and against the FP64 adjoint.  The continuous clamp of the
+    power law is used: the literal law jumps at gamma_1, so J is not
+    differentiable and a difference quotient across a jump is meaningless."""
     import numpy as np
     from paper_2011_15073_gb300 import inputs, lbm
     N = args.study_N or 256
@@ -443,7 +447,7 @@ def study_adjoint(args):
     Da = inputs.darcy_field(2011, N, N)
 
     def cav(prec):
-        c = lbm.Cavity(N, N, case["n"], 1e-2, case["Ra"], case["Pr"], case["porosity"], prec=prec)
+        c = lbm.Cavity(N, N, case["n"], 1e-2, case["Ra"], case["Pr"], case["porosity"], prec=prec, clamp_mode=1)
         c.set_darcy_field(Da)
         return c
 
@@ -463,7 +467,8 @@ def study_adjoint(args):
         res[prec] = dict(J=J, dDa=dDa, dn=dn, dRa=dRa, peak=peak, t_fwd=t_fwd, t_adj=t_adj)
 
     def J_of(D):
-        with lbm.Cavity(N, N, case["n"], 1e-2, case["Ra"], case["Pr"], case["porosity"], prec="f64") as c:
+        with lbm.Cavity(N, N, case["n"], 1e-2, case["Ra"], case["Pr"], case["porosity"], prec="f64",
+                        clamp_mode=1) as c:
             c.set_darcy_field(D)
             c.step(steps)
             return c.nusselt()[0]
@@ -550,11 +555,13 @@ def main():
     variants = {}
     for v in [p for p in args.variants.split(",") if p and p != prec]:
         vs, vd = 2, args.variant_delta
-        tv, kv, _, nuv = time_ours(lbm, torch, N, v, vs, 1, vd, stream)
-        av = BYTES_PER_NODE[v] * N * N / kv / 1e9
+        vp, vl = (v.split("@")[0], 1) if v.endswith("@aa") else (v, 0)
+        tv, kv, _, nuv = time_ours(lbm, torch, N, vp, vs, 1, vd, stream, layout=vl)
+        av = BYTES_PER_NODE[vp] * N * N / kv / 1e9
         variants[v] = {"MLUPS": N * N * vd * vs / tv / 1e6, "kernel_MLUPS": N * N / kv / 1e6,
                        "fused_steps_per_bench_step": vd,
-                       "bytes_per_node": BYTES_PER_NODE[v], "achieved_GBs": av, "frac_of_hbm": av / peak,
+                       "bytes_per_node": BYTES_PER_NODE[vp], "achieved_GBs": av, "frac_of_hbm": av / peak,
+                       "layout": "aa (in place)" if vl else "ab (two buffers)",
                        "nu_hot": nuv}
         if v == "f64":
             ipn = recorded("f64_fp64_inst_per_node")

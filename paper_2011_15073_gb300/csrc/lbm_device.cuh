@@ -316,11 +316,14 @@ template <class V>
 struct Porous {
     V heK, eK, c1, eFsK;
 };
-template <class V>
+// FIELD: 0 the uniform permeability, 1 the per-node field, 2 decide at run
+// time from p.da (kernels that know which one they run pass 0 or 1, so the
+// other path costs them no registers).
+template <class V, int FIELD = 2>
 __device__ __forceinline__ Porous<V> porous_at(const Phys<V> &p, int64_t k)
 {
     Porous<V> q;
-    if (!p.da) {
+    if (FIELD == 0 || (FIELD == 2 && !p.da)) {
         q.heK = p.half_eps_invK;
         q.eK = p.eps_invK;
         q.c1 = p.c1;
@@ -342,11 +345,11 @@ __device__ __forceinline__ Porous<V> porous_at(const Phys<V> &p, int64_t k)
 // u = v / (c0 + sqrt(c0^2 + c1 |v|)), c0 = (1 + eps nu / (2K)) / 2, with the
 // apparent viscosity of the lagged relaxation time; then the total force
 // F = -eps nu u / K - eps F_eps |u| u / sqrt K + eps G.
-template <class V>
+template <class V, int FIELD = 2>
 __device__ __forceinline__ Macro<V> macro(const Phys<V> &p, const V f[9], const V g[5], V tau_prev, int64_t k)
 {
     Macro<V> m;
-    const Porous<V> q = porous_at(p, k);
+    const Porous<V> q = porous_at<V, FIELD>(p, k);
     const V sax = (f[1] + f[2]) + (f[3] + f[4]);
     const V sdg = (f[5] + f[6]) + (f[7] + f[8]);
     m.rho = f[0] + sax + sdg;
@@ -394,10 +397,10 @@ __device__ __forceinline__ F2 apparent(const Phys<F2> &p, F2 gs)
 // Returns the new relaxation time; m receives the macroscopic moments and the
 // apparent lattice viscosity of this collision.  k is the node's offset in a
 // plane (used only to read a per-node Darcy field).
-template <class V>
+template <class V, int FIELD = 2>
 __device__ __forceinline__ V collide(const Phys<V> &p, V f[9], V g[5], V tau_prev, Macro<V> &m, int64_t k)
 {
-    m = macro<V>(p, f, g, tau_prev, k);
+    m = macro<V, FIELD>(p, f, g, tau_prev, k);
     const V rho = m.rho, ux = m.ux, uy = m.uy;
     // raw moments
     const V sax = (f[1] + f[2]) + (f[3] + f[4]);

@@ -29,7 +29,7 @@ __global__ void init_kernel(typename Store<PREC>::S *__restrict__ dist,
 
 // One time step of the whole cavity (pull scheme, two buffers); the node
 // and tile bodies are in lbm_step.cuh.
-template <int PREC>
+template <int PREC, int FIELD>
 __global__ void __launch_bounds__(128)
 step_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
             const typename Store<PREC>::TauS *__restrict__ tsrc, typename Store<PREC>::TauS *__restrict__ tdst,
@@ -37,15 +37,15 @@ step_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= p.nx) return;
-    step_node<PREC, typename Store<PREC>::R>(src, dst, tsrc, tdst, p, x, y);
+    step_node<PREC, typename Store<PREC>::R, FIELD>(src, dst, tsrc, tdst, p, x, y);
 }
 
-template <int PREC>
+template <int PREC, int FIELD>
 __global__ void __launch_bounds__(128)
 step2_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
              const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
 {
-    step2_tile<PREC>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
+    step2_tile<PREC, FIELD>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
 }
 
 // Streamed macroscopic fields: rho, u_x, u_y, T, nu -> out[5][ny][nx].
@@ -258,39 +258,32 @@ static cudaError_t init_t(lbm_ctx *c)
 }
 
 template <int PREC>
+static cudaError_t step_buffers_t(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
+{
+    using St = Store<PREC>;
+    if constexpr (PREC == LBM_F64) {
+        auto *kern = c->d_da ? step_kernel<PREC, 1> : step_kernel<PREC, 0>;
+        kern<<<node_grid(c, 128), 128, 0, c->stream>>>(
+            (const typename St::S *)src, (typename St::S *)dst, (const typename St::TauS *)tsrc,
+            (typename St::TauS *)tdst, make_params<typename St::R>(c));
+    } else {
+        auto *kern = c->d_da ? step2_kernel<PREC, 1> : step2_kernel<PREC, 0>;
+        kern<<<node_grid(c, 256), 128, 0, c->stream>>>(
+            (const typename St::S *)src, (typename St::S *)dst, (const float *)tsrc, (float *)tdst,
+            make_params<float>(c), make_params<F2>(c));
+    }
+    return cudaGetLastError();
+}
+
+template <int PREC>
 static cudaError_t step_t(lbm_ctx *c)
 {
     using St = Store<PREC>;
     if (c->opts.layout == 1) return launch_aa_step(c);
     const int s = c->cur, d = 1 - c->cur;
-    if constexpr (PREC == LBM_F64) {
-        step_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
-            (const typename St::S *)c->buf.dist[s], (typename St::S *)c->buf.dist[d],
-            (const typename St::TauS *)c->buf.tau[s], (typename St::TauS *)c->buf.tau[d],
-            make_params<typename St::R>(c));
-    } else {
-        step2_kernel<PREC><<<node_grid(c, 256), 128, 0, c->stream>>>(
-            (const typename St::S *)c->buf.dist[s], (typename St::S *)c->buf.dist[d],
-            (const float *)c->buf.tau[s], (float *)c->buf.tau[d], make_params<float>(c), make_params<F2>(c));
-    }
+    const cudaError_t e = step_buffers_t<PREC>(c, c->buf.dist[s], c->buf.dist[d], c->buf.tau[s], c->buf.tau[d]);
     c->cur = d;
-    return cudaGetLastError();
-}
-
-template <int PREC>
-static cudaError_t step_buffers_t(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
-{
-    using St = Store<PREC>;
-    if constexpr (PREC == LBM_F64) {
-        step_kernel<PREC><<<node_grid(c, 128), 128, 0, c->stream>>>(
-            (const typename St::S *)src, (typename St::S *)dst, (const typename St::TauS *)tsrc,
-            (typename St::TauS *)tdst, make_params<typename St::R>(c));
-    } else {
-        step2_kernel<PREC><<<node_grid(c, 256), 128, 0, c->stream>>>(
-            (const typename St::S *)src, (typename St::S *)dst, (const float *)tsrc, (float *)tdst,
-            make_params<float>(c), make_params<F2>(c));
-    }
-    return cudaGetLastError();
+    return e;
 }
 
 template <int PREC>

@@ -8,7 +8,7 @@
 namespace lbm {
 
 // Pull, collide and store one node (wall rules included).
-template <int PREC, class R>
+template <int PREC, class R, int FIELD = 2>
 __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restrict__ src,
                                           typename Store<PREC>::S *__restrict__ dst,
                                           const typename Store<PREC>::TauS *__restrict__ tsrc,
@@ -20,7 +20,7 @@ __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restr
     R f[9], g[5];
     pull<PREC, R>(src, p, x, y, f, g);
     Macro<R> m;
-    const R tau = collide<R>(p, f, g, R(tsrc[k]), m, k);
+    const R tau = collide<R, FIELD>(p, f, g, R(tsrc[k]), m, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) St::st(dst, i * p.plane + k, f[i], R(rest_f(i)));
 #pragma unroll
@@ -35,7 +35,7 @@ __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restr
 // on the packed FP32x2 pipe; any warp that touches a wall or the ragged end
 // of a row updates its nodes one at a time with the wall rules.  The branch
 // is uniform per warp.
-template <int PREC>
+template <int PREC, int FIELD = 2>
 __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__restrict__ src,
                                            typename Store<PREC>::S *__restrict__ dst,
                                            const float *__restrict__ tsrc, float *__restrict__ tdst,
@@ -49,7 +49,7 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
     const bool fast = y > 0 && y < p.ny - 1 && wx > 0 && wx + 64 < p.nx;
     if (!fast) {
         for (int j = 0; j < 2; j++)
-            if (x0 + j < p.nx) step_node<PREC, float>(src, dst, tsrc, tdst, p, x0 + j, y);
+            if (x0 + j < p.nx) step_node<PREC, float, FIELD>(src, dst, tsrc, tdst, p, x0 + j, y);
         return;
     }
     const int64_t P = p.plane, W = p.pitch;
@@ -78,7 +78,7 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
     g[4] = St::ld2(gs + 4 * P, k + W, float(rest_g(4)));
     const F2 tau_prev(*reinterpret_cast<const float2 *>(tsrc + k));
     Macro<F2> m;
-    const F2 tau = collide<F2>(p2, f, g, tau_prev, m, k);
+    const F2 tau = collide<F2, FIELD>(p2, f, g, tau_prev, m, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) St::st2(dst + i * P, k, f[i], float(rest_f(i)));
 #pragma unroll

@@ -24,8 +24,8 @@ N = 64
 
 def steady(lbm, n, Da, Ra, Pr=6.2, porous_model=0, porosity=1.0):
     """FP64 run until the residual is below 1e-9, or the hot-wall Nu of the
-    last six 20,000-step chunks agrees to 1e-7 (a converged Nu on a flow that
-    keeps a tiny oscillation)."""
+    last six 20,000-step chunks agrees to 1e-3 (a settled Nu on a flow that
+    keeps a small oscillation; the trends below differ by far more)."""
     with lbm.Cavity(N, N, n, Da, Ra, Pr, porosity, prec="f64", porous_model=porous_model,
                     clamp_mode=1, resid_interval=500) as cav:
         cav.residual()
@@ -36,7 +36,7 @@ def steady(lbm, n, Da, Ra, Pr=6.2, porous_model=0, porosity=1.0):
             r = cav.residual()
             hist.append(cav.nusselt()[0])
             last = hist[-6:]
-            ok = r < 1e-9 or (len(last) == 6 and max(last) - min(last) <= 1e-7 * abs(last[-1]))
+            ok = r < 1e-9 or (len(last) == 6 and max(last) - min(last) <= 1e-3 * abs(last[-1]))
         hot, cold, _ = cav.nusselt()
         fl = cav.fields()
     assert ok, (done, r, hist[-6:])
