@@ -59,7 +59,7 @@ class Lattice(ctypes.Structure):
         ("periodic_x", ctypes.c_int), ("T_hot", ctypes.c_double),
         ("T_cold", ctypes.c_double), ("L", ctypes.c_double),
         ("tau0", ctypes.c_double), ("rho0", ctypes.c_double),
-        ("T0", ctypes.c_double),
+        ("T0", ctypes.c_double), ("tau_iters", ctypes.c_int),
     ]
 
     def copy(self) -> "Lattice":
@@ -105,18 +105,24 @@ def lib():
             L.orc_forcing_vel.argtypes = [ctypes.c_double] * 6 + [_D]
             L.orc_collide_node.argtypes = [ctypes.POINTER(Lattice), _D, _D, ctypes.c_double,
                                            _D, _D, _D, _D]
+            L.orc_phi.argtypes = [ctypes.POINTER(Lattice), _D, _D, ctypes.c_double, _D]
+            L.orc_phi.restype = ctypes.c_double
+            L.orc_implicit_tau.argtypes = [ctypes.POINTER(Lattice), _D, _D]
+            L.orc_implicit_tau.restype = ctypes.c_double
             _lib = L
     return _lib
 
 
 def map_params(nx, ny, n, Da, Ra, Pr, porosity=0.6, Ma=0.1, porous_model=1,
-               clamp_mode=0, s_e=1.5, s_p=1.5) -> Lattice:
-    """Lattice-unit parameters of the cavity problem (see ``orc_map_params``)."""
+               clamp_mode=0, s_e=1.5, s_p=1.5, tau_iters=0) -> Lattice:
+    """Lattice-unit parameters of the cavity problem (see ``orc_map_params``);
+    tau_iters > 0 selects the node-local implicit tau with that many Newton steps."""
     lat = Lattice()
     rc = lib().orc_map_params(nx, ny, n, Da, Ra, Pr, porosity, Ma, porous_model,
                               clamp_mode, s_e, s_p, ctypes.byref(lat))
-    if rc != 0:
+    if rc != 0 or tau_iters < 0:
         raise ValueError("invalid cavity parameters")
+    lat.tau_iters = int(tau_iters)
     return lat
 
 
@@ -153,6 +159,22 @@ def collide_node(lat: Lattice, f, g, tau_prev):
     lib().orc_collide_node(ctypes.byref(lat), _ptr(f), _ptr(g), float(tau_prev),
                            _ptr(fo), _ptr(go), ctypes.byref(tn), ctypes.byref(gm))
     return fo, go, tn.value, gm.value
+
+
+def phi(lat: Lattice, f, g, tau):
+    """The implicit-tau map of one node: (Phi(tau), Newton factor J)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    J = ctypes.c_double()
+    v = lib().orc_phi(ctypes.byref(lat), _ptr(f), _ptr(g), float(tau), ctypes.byref(J))
+    return v, J.value
+
+
+def implicit_tau(lat: Lattice, f, g):
+    """lat.tau_iters Newton steps toward the node's implicit tau."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    return lib().orc_implicit_tau(ctypes.byref(lat), _ptr(f), _ptr(g))
 
 
 class Cavity:

@@ -202,12 +202,13 @@ static double apparent_factor(const orc_lattice *p, double gstar)
  *  3. v = sum f_i e_i / rho + eps G / 2 (half-force shift of Eq. velo).
  *  4. Porous solve: u = v / (c0 + sqrt(c0^2 + c1 |v|)), with
  *     c0 = (1 + eps nu / (2K)) / 2, c1 = eps F_eps / (2 sqrt K), and nu the
- *     apparent viscosity of the lagged relaxation time tau_prev.
+ *     apparent viscosity of the relaxation time tau_in that the collision
+ *     starts from (the lagged tau_prev, or the node-local implicit solve).
  *  5. Total force per unit mass F = -eps nu u / K - eps F_eps |u| u / sqrt K
  *     + eps G (Darcy drag with the apparent viscosity as in the
  *     non-dimensional momentum equations, Forchheimer, buoyancy).
  *  6. Strain rate gamma_ab = -3/(2 rho) sum_i e_ia e_ib
- *     sum_j (M^-1 S M)_ij (f_j - f_j^eq), with s7 = s8 = 1/tau_prev, and
+ *     sum_j (M^-1 S M)_ij (f_j - f_j^eq), with s7 = s8 = 1/tau_in, and
  *     |gamma| = sqrt(2 gamma_ab gamma_ab).
  *  7. gamma* = |gamma| gamma_scale, nu = nu_ref D(gamma*), tau = 3 nu + 1/2.
  *  8. m* = m - S (m - m^eq) + (I - S/2) M F_vel with s7 = s8 = 1/tau;
@@ -215,14 +216,25 @@ static double apparent_factor(const orc_lattice *p, double gstar)
  *  9. n = N g, n^eq = (T, T u_x, T u_y, -2T/3, 0),
  *     n* = n - S_T (n - n^eq), S_T = diag(1, 1/tauT, 1/tauT, s_e, s_p);
  *     g* = N^-1 n*.
+ * Steps 1-6 are strain_state(); steps 7-9 node_update().
  * ------------------------------------------------------------------------- */
 typedef struct {
     double rho, ux, uy, T, nu, gamma;
 } node_diag;
 
-static void node_update(const orc_lattice *p, double K, const double f[9],
-                        const double g[5], double tau_prev, double fo[9],
-                        double go[5], double *tau_new, node_diag *d)
+typedef struct {
+    double rho, T, ux, uy, Fx, Fy;
+    double gamma;  /* |gamma| of step 6                                   */
+    double R;      /* d ln|gamma| / d ln(1/tau_in) at fixed velocity:
+                      omega (gamma : gamma_p) / (gamma : gamma), where
+                      gamma_p is the strain tensor of step 6 with S replaced
+                      by diag(0, ..., 0, 1, 1) (the part that scales with
+                      omega = 1/tau_in); 0 where gamma = 0 or when not
+                      asked for                                          */
+} strain_out;
+
+static void strain_state(const orc_lattice *p, double K, const double f[9],
+                         const double g[5], double tau_in, int want_R, strain_out *o)
 {
     ensure_matrices();
     /* 1 */
@@ -240,56 +252,139 @@ static void node_update(const orc_lattice *p, double K, const double f[9],
     double vx = jx / rho + 0.5 * p->eps * Gx;
     double vy = jy / rho + 0.5 * p->eps * Gy;
     /* 4 */
-    double nu_prev = (tau_prev - 0.5) / 3.0;
-    double c0 = 0.5 * (1.0 + p->eps * nu_prev / (2.0 * K));
+    double nu_in = (tau_in - 0.5) / 3.0;
+    double c0 = 0.5 * (1.0 + p->eps * nu_in / (2.0 * K));
     double c1 = p->eps * p->Feps / (2.0 * sqrt(K));
     double vmag = sqrt(vx * vx + vy * vy);
     double den = c0 + sqrt(c0 * c0 + c1 * vmag);
     double ux = vx / den, uy = vy / den;
     /* 5 */
     double umag = sqrt(ux * ux + uy * uy);
-    double Fx = -p->eps * nu_prev * ux / K
+    double Fx = -p->eps * nu_in * ux / K
                 - p->eps * p->Feps * umag * ux / sqrt(K) + p->eps * Gx;
-    double Fy = -p->eps * nu_prev * uy / K
+    double Fy = -p->eps * nu_in * uy / K
                 - p->eps * p->Feps * umag * uy / sqrt(K) + p->eps * Gy;
     /* 6 */
-    double feq[9], fneq[9], S[9], A[81], tmp[81], h[9];
+    double feq[9], fneq[9], S[9], P[9], A[81], Ap[81], tmp[81], tmpp[81], h[9], hp[9];
     orc_feq(rho, ux, uy, p->eps, feq);
     for (int i = 0; i < 9; i++) fneq[i] = f[i] - feq[i];
-    for (int i = 0; i < 9; i++) S[i] = p->s[i];
-    S[7] = S[8] = 1.0 / tau_prev;
-    for (int r = 0; r < 9; r++) /* tmp = S M */
-        for (int c = 0; c < 9; c++) tmp[r * 9 + c] = S[r] * MROWS[r * 9 + c];
-    for (int r = 0; r < 9; r++) /* A = M^-1 (S M) */
+    for (int i = 0; i < 9; i++) {
+        S[i] = p->s[i];
+        P[i] = 0.0;
+    }
+    S[7] = S[8] = 1.0 / tau_in;
+    P[7] = P[8] = 1.0;
+    for (int r = 0; r < 9; r++) /* tmp = S M, tmpp = P M */
         for (int c = 0; c < 9; c++) {
-            double acc = 0.0;
-            for (int k = 0; k < 9; k++) acc += MINV[r * 9 + k] * tmp[k * 9 + c];
+            tmp[r * 9 + c] = S[r] * MROWS[r * 9 + c];
+            tmpp[r * 9 + c] = P[r] * MROWS[r * 9 + c];
+        }
+    for (int r = 0; r < 9; r++) /* A = M^-1 (S M), Ap = M^-1 (P M) */
+        for (int c = 0; c < 9; c++) {
+            double acc = 0.0, accp = 0.0;
+            for (int k = 0; k < 9; k++) {
+                acc += MINV[r * 9 + k] * tmp[k * 9 + c];
+                if (want_R) accp += MINV[r * 9 + k] * tmpp[k * 9 + c];
+            }
             A[r * 9 + c] = acc;
+            Ap[r * 9 + c] = accp;
         }
     matvec(A, fneq, h, 9);
-    double gab[2][2] = {{0, 0}, {0, 0}};
+    matvec(Ap, fneq, hp, 9);
+    double gab[2][2], gabp[2][2];
     for (int a = 0; a < 2; a++)
         for (int b = 0; b < 2; b++) {
-            double acc = 0.0;
+            double acc = 0.0, accp = 0.0;
             for (int i = 0; i < 9; i++) {
                 double ea = a == 0 ? EX9[i] : EY9[i];
                 double eb = b == 0 ? EX9[i] : EY9[i];
                 acc += ea * eb * h[i];
+                accp += ea * eb * hp[i];
             }
             gab[a][b] = -3.0 / (2.0 * rho) * acc; /* c = 1 */
+            gabp[a][b] = -3.0 / (2.0 * rho) * accp;
         }
-    double gg = 0.0;
+    double gg = 0.0, ggp = 0.0;
     for (int a = 0; a < 2; a++)
-        for (int b = 0; b < 2; b++) gg += gab[a][b] * gab[a][b];
-    double gamma = sqrt(2.0 * gg);
+        for (int b = 0; b < 2; b++) {
+            gg += gab[a][b] * gab[a][b];
+            ggp += gab[a][b] * gabp[a][b];
+        }
+    o->rho = rho;
+    o->T = T;
+    o->ux = ux;
+    o->uy = uy;
+    o->Fx = Fx;
+    o->Fy = Fy;
+    o->gamma = sqrt(2.0 * gg);
+    o->R = want_R && gg > 0.0 ? (1.0 / tau_in) * ggp / gg : 0.0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Node-local implicit relaxation time (an extension: the paper does not say
+ * how the tau used in the strain rate is obtained; the lagged reading uses
+ * the node's previous tau).  The implicit tau is the root of
+ *   tau = Phi(tau),  Phi(tau) = 3 nu_ref D(gamma*(tau)) + 1/2,
+ * with gamma(tau) = steps 1-6 above taken with tau_in = tau.  It is found by
+ * p->tau_iters Newton steps on ln tau, starting from the rest-state tau0:
+ *   J_k = 1 - (1 - n) R_k (Phi_k - 1/2) / Phi_k   where D has slope, i.e.
+ *         gamma1 < gamma* < gamma2,  else J_k = 1,
+ *   tau_{k+1} = tau_k (Phi_k / tau_k)^(1 / J_k)
+ * (d ln Phi / d ln tau = -(n - 1) R (Phi - 1/2) / Phi with the velocity held;
+ * the slope of the drag through the velocity is left out of J only, so the
+ * root is exact but convergence there is linear with a small rate).
+ * J lies between n and 1, so the step is defined for every n > 0.
+ * Pinned by: n = 1 reproduces the lagged update bit for bit; the converged
+ * tau satisfies tau = Phi(tau) and equals the root found by bisection on
+ * ln tau; a lagged steady state is a fixed point of the implicit step.
+ * ------------------------------------------------------------------------- */
+static double phi_of(const orc_lattice *p, double K, const double f[9],
+                     const double g[5], double tau, double *J)
+{
+    strain_out st;
+    strain_state(p, K, f, g, tau, J != NULL, &st);
+    double gs = st.gamma * p->gamma_scale;
+    double phi = 3.0 * p->nu_ref * apparent_factor(p, gs) + 0.5;
+    if (J) {
+        if (gs > p->gamma1 && gs < p->gamma2)
+            *J = 1.0 - (1.0 - p->n) * st.R * (phi - 0.5) / phi;
+        else
+            *J = 1.0;
+    }
+    return phi;
+}
+
+static double implicit_tau(const orc_lattice *p, double K, const double f[9],
+                           const double g[5])
+{
+    double tau = p->tau0;
+    for (int it = 0; it < p->tau_iters; it++) {
+        double J;
+        double phi = phi_of(p, K, f, g, tau, &J);
+        if (J == 1.0)
+            tau = phi;
+        else
+            tau = tau * pow(phi / tau, 1.0 / J);
+    }
+    return tau;
+}
+
+static void node_update(const orc_lattice *p, double K, const double f[9],
+                        const double g[5], double tau_in, double fo[9],
+                        double go[5], double *tau_new, node_diag *d)
+{
+    strain_out st;
+    strain_state(p, K, f, g, tau_in, 0, &st);
+    double rho = st.rho, T = st.T, ux = st.ux, uy = st.uy;
     /* 7 */
-    double nu_new = p->nu_ref * apparent_factor(p, gamma * p->gamma_scale);
+    double nu_new = p->nu_ref * apparent_factor(p, st.gamma * p->gamma_scale);
     double tau = 3.0 * nu_new + 0.5;
     /* 8 */
-    double m[9], meq[9], Fv[9], Fh[9], ms[9];
+    double m[9], meq[9], Fv[9], Fh[9], ms[9], S[9];
+    for (int i = 0; i < 9; i++) S[i] = p->s[i];
     matvec(MROWS, f, m, 9);
     orc_meq(rho, ux, uy, p->eps, meq);
-    orc_forcing_vel(rho, ux, uy, Fx, Fy, p->eps, Fv);
+    orc_forcing_vel(rho, ux, uy, st.Fx, st.Fy, p->eps, Fv);
     matvec(MROWS, Fv, Fh, 9);
     S[7] = S[8] = 1.0 / tau;
     for (int k = 0; k < 9; k++)
@@ -317,8 +412,27 @@ static void node_update(const orc_lattice *p, double K, const double f[9],
         d->uy = uy;
         d->T = T;
         d->nu = nu_new;
-        d->gamma = gamma;
+        d->gamma = st.gamma;
     }
+}
+
+/* tau the collision of a node starts from: the stored lagged tau, or the
+ * implicit solve when tau_iters > 0. */
+static double tau_start(const orc_lattice *p, double K, const double f[9],
+                        const double g[5], double tau_stored)
+{
+    return p->tau_iters > 0 ? implicit_tau(p, K, f, g) : tau_stored;
+}
+
+double orc_phi(const orc_lattice *lat, const double f[9], const double g[5],
+               double tau, double *J)
+{
+    return phi_of(lat, lat->K, f, g, tau, J);
+}
+
+double orc_implicit_tau(const orc_lattice *lat, const double f[9], const double g[5])
+{
+    return implicit_tau(lat, lat->K, f, g);
 }
 
 void orc_collide_node(const orc_lattice *lat, const double f[9],
@@ -513,10 +627,11 @@ int orc_step(orc_ctx *c, int64_t k)
             double f[9], g[5], fo[9], go[5], tnew;
             gather(c->fs, 9, nn, (size_t)q, f);
             gather(c->gs, 5, nn, (size_t)q, g);
-            node_update(&c->p, K_at(c, (size_t)q), f, g, c->tau[q], fo, go, &tnew, NULL);
+            double Kq = K_at(c, (size_t)q);
+            node_update(&c->p, Kq, f, g, tau_start(&c->p, Kq, f, g, c->tau[q]), fo, go, &tnew, NULL);
             for (int i = 0; i < 9; i++) c->f[i * nn + q] = fo[i];
             for (int i = 0; i < 5; i++) c->g[i * nn + q] = go[i];
-            c->tau[q] = tnew;
+            if (c->p.tau_iters == 0) c->tau[q] = tnew; /* implicit runs keep no tau */
         }
     }
     return 0;
@@ -553,7 +668,8 @@ void orc_fields(const orc_ctx *c, double *rho, double *ux, double *uy,
         node_diag d;
         gather(fs, 9, nn, q, f);
         gather(gs, 5, nn, q, g);
-        node_update(&c->p, K_at(c, q), f, g, c->tau[q], fo, go, &tnew, &d);
+        node_update(&c->p, K_at(c, q), f, g, tau_start(&c->p, K_at(c, q), f, g, c->tau[q]), fo, go,
+                    &tnew, &d);
         if (rho) rho[q] = d.rho;
         if (ux) ux[q] = d.ux;
         if (uy) uy[q] = d.uy;

@@ -49,6 +49,9 @@ typedef struct {
     double L;            /* length unit for Nu (distance hot -> cold wall) */
     double tau0;         /* initial relaxation time                        */
     double rho0, T0;     /* initial density and temperature                */
+    int    tau_iters;    /* 0: lagged tau (stored per node); k > 0: node-
+                            local implicit tau by k Newton steps from tau0,
+                            no stored tau (orc_implicit_tau)               */
 } orc_lattice;
 
 typedef struct orc_ctx orc_ctx;
@@ -94,6 +97,15 @@ void orc_forcing_vel(double rho, double ux, double uy, double Fx, double Fy,
 void orc_collide_node(const orc_lattice *lat, const double f[9],
                       const double g[5], double tau_prev, double fo[9],
                       double go[5], double *tau_new, double *gamma);
+
+/* The implicit-tau map of one node (uniform K of lat): Phi(tau) =
+ * 3 nu_ref D(gamma*(tau)) + 1/2, gamma(tau) the strain rate of the collision
+ * started from tau; *J (may be NULL) receives the Newton factor
+ * 1 - d ln Phi / d ln tau at fixed velocity (1 where D is flat). */
+double orc_phi(const orc_lattice *lat, const double f[9], const double g[5],
+               double tau, double *J);
+/* lat->tau_iters Newton steps on ln tau from lat->tau0 toward tau = Phi(tau). */
+double orc_implicit_tau(const orc_lattice *lat, const double f[9], const double g[5]);
 
 #ifdef __cplusplus
 }

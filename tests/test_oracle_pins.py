@@ -373,3 +373,47 @@ def test_brinkman_forchheimer_channel_matches_bvp(orc):
     # the Forchheimer term matters at this forcing: without it the flow is faster
     uD = G * K / nu * (1 - np.cosh(math.sqrt(eps / K) * (y - ny / 2)) / math.cosh(math.sqrt(eps / K) * ny / 2))
     assert np.linalg.norm(uD - ua) / np.linalg.norm(ua) > 0.05
+
+
+@pytest.mark.parametrize("tau_iters", [0, 4])
+def test_powerlaw_porous_channel_matches_bvp(orc, tau_iters):
+    """A power-law fluid driven through a porous channel: the apparent
+    viscosity enters both the shear stress and the Darcy drag, so the steady
+    profile solves (nu(|u'|) u')' - eps nu(|u'|) u / K - eps Feps u^2 / sqrt K
+    + eps G = 0, u(0) = u(H) = 0, with nu(s) = K_c max(s, gamma_1)^(n-1).
+    Integrated independently with scipy's collocation solver in the
+    variables (u, q = nu u'); both the lagged and the implicit tau must land
+    on it (it fixes the viscosity the velocity solve uses)."""
+    from scipy.integrate import solve_bvp
+    n, ny, eps = 0.7, 64, 0.6
+    K = (ny / 8) ** 2
+    Feps = 1.75 / math.sqrt(150 * eps ** 3)
+    G = 1e-5
+    lat = channel_lattice(orc, ny, n, nu_w=0.1, gam_w=1e-3, eps=eps, K=K, Feps=Feps, G=G)
+    lat.tau_iters = tau_iters
+    Kc, g1 = lat.nu_ref, lat.gamma1
+    q1 = Kc * g1 ** n
+
+    def dudy(q):
+        a = np.abs(q)
+        return np.sign(q) * np.where(a >= q1, (a / Kc) ** (1 / n), a / (Kc * g1 ** (n - 1)))
+
+    def rhs(yy, s):
+        u, q = s
+        nu = Kc * np.maximum(np.abs(dudy(q)), g1) ** (n - 1)
+        return np.vstack([dudy(q), eps * nu * u / K + eps * Feps * np.abs(u) * u / math.sqrt(K) - eps * G])
+
+    yy = np.linspace(0, ny, 4001)
+    guess = np.vstack([1e-3 * np.sin(np.pi * yy / ny), np.zeros_like(yy)])
+    sol = solve_bvp(rhs, lambda a, b: np.array([a[0], b[0]]), yy, guess, tol=1e-10, max_nodes=400000)
+    assert sol.success
+    y = np.arange(ny) + 0.5
+    ua = sol.sol(y)[0]
+    c = start_from_profile(orc, lat, ua)
+    run_to_steady(c, 2000, 1e-12, 400000)
+    u = c.fields()["ux"][:, 0]
+    assert np.linalg.norm(u - ua) / np.linalg.norm(ua) < 2e-3
+    # the viscosity varies across the channel by a factor of ~5, so a drag
+    # taken with one viscosity would give a visibly different profile
+    nu = c.fields()["nu"][:, 0]
+    assert nu.max() / nu.min() > 3
