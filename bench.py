@@ -32,6 +32,27 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_NODE = {"f64": 240, "f32": 120, "f32d": 120, "bf16d": 64, "f16d": 64}
+# bytes of the stored lagged tau in those figures (read + write); the
+# node-local implicit tau (tau_iters > 0) moves none
+TAU_BYTES = {"f64": 16, "f32": 8, "f32d": 8, "bf16d": 8, "f16d": 8}
+
+
+def parse_variant(v):
+    """'prec[@aa][@tauK]' -> (prec, layout, tau_iters)."""
+    parts = v.split("@")
+    layout, tau_iters = 0, 0
+    for m in parts[1:]:
+        if m == "aa":
+            layout = 1
+        elif m.startswith("tau") and m[3:].isdigit():
+            tau_iters = int(m[3:])
+        else:
+            raise ValueError(f"unknown variant modifier {m!r} in {v!r}")
+    return parts[0], layout, tau_iters
+
+
+def bytes_per_node(prec, tau_iters=0):
+    return BYTES_PER_NODE[prec] - (TAU_BYTES[prec] if tau_iters else 0)
 CASE = dict(n=0.6, Da=1e-3, Ra=1e5, Pr=6.2, porosity=0.6)
 FALLBACK_HBM_GBS = 6800.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
@@ -87,7 +108,9 @@ def parse():
                     help="fused time steps per bench step (the convergence-check interval)")
     ap.add_argument("--variant-delta", type=int, default=200)
     ap.add_argument("--prec", default="f32")
-    ap.add_argument("--variants", default="f64,f32d,f32@aa,bf16d,f16d",
+    ap.add_argument("--tau-iters", type=int, default=0,
+                    help="0: lagged tau (stored per node); K > 0: node-local implicit tau, K Newton steps")
+    ap.add_argument("--variants", default="f64,f32d,f32@aa,f32@tau2,f32@aa@tau2,bf16d,f16d",
                     help="other storage precisions measured beside the headline ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -196,10 +219,10 @@ def dist_env():
     return rank, world, local
 
 
-def time_ours(lbm, torch, N, prec, steps, warmup, delta, stream, layout=0):
+def time_ours(lbm, torch, N, prec, steps, warmup, delta, stream, layout=0, tau_iters=0):
     """Device-resident run: returns (seconds for `steps` bench steps, avg fused
     kernel seconds, kernels launched in the timed region, Nu)."""
-    cav = lbm.Cavity(N, N, prec=prec, cuda_stream=stream, layout=layout, **CASE)
+    cav = lbm.Cavity(N, N, prec=prec, cuda_stream=stream, layout=layout, tau_iters=tau_iters, **CASE)
     try:
         cav.residual()   # first call stores the snapshot
         for _ in range(warmup):
@@ -542,7 +565,8 @@ def main():
 
     barrier()
     with Clocks(local) as clk:
-        total, kern, launches, nu = time_ours(lbm, torch, N, prec, args.steps, max(3, args.warmup), delta, stream)
+        total, kern, launches, nu = time_ours(lbm, torch, N, prec, args.steps, max(3, args.warmup), delta, stream,
+                                              tau_iters=args.tau_iters)
     barrier()
     if world > 1:
         t = torch.tensor([total], device="cuda")
@@ -551,17 +575,21 @@ def main():
     units = world * N * N * delta * args.steps
     mlups = units / total / 1e6
     peak, peak_src = hbm_peak()
-    achieved = BYTES_PER_NODE[prec] * N * N / kern / 1e9
+    bpn_main = bytes_per_node(prec, args.tau_iters)
+    achieved = bpn_main * N * N / kern / 1e9
+    key_main = prec + (f"@tau{args.tau_iters}" if args.tau_iters else "")
     variants = {}
-    for v in [p for p in args.variants.split(",") if p and p != prec]:
+    for v in [p for p in args.variants.split(",") if p and p != key_main]:
         vs, vd = 2, args.variant_delta
-        vp, vl = (v.split("@")[0], 1) if v.endswith("@aa") else (v, 0)
-        tv, kv, _, nuv = time_ours(lbm, torch, N, vp, vs, 1, vd, stream, layout=vl)
-        av = BYTES_PER_NODE[vp] * N * N / kv / 1e9
+        vp, vl, vt = parse_variant(v)
+        tv, kv, _, nuv = time_ours(lbm, torch, N, vp, vs, 1, vd, stream, layout=vl, tau_iters=vt)
+        bpn = bytes_per_node(vp, vt)
+        av = bpn * N * N / kv / 1e9
         variants[v] = {"MLUPS": N * N * vd * vs / tv / 1e6, "kernel_MLUPS": N * N / kv / 1e6,
                        "fused_steps_per_bench_step": vd,
-                       "bytes_per_node": BYTES_PER_NODE[vp], "achieved_GBs": av, "frac_of_hbm": av / peak,
+                       "bytes_per_node": bpn, "achieved_GBs": av, "frac_of_hbm": av / peak,
                        "layout": "aa (in place)" if vl else "ab (two buffers)",
+                       "tau": f"implicit, {vt} Newton steps" if vt else "lagged (stored)",
                        "nu_hot": nuv}
         if v == "f64":
             ipn = recorded("f64_fp64_inst_per_node")
@@ -588,14 +616,17 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
         "data": "synthetic",
         "config": {"workload": f"cavity {N}x{N}, n={CASE['n']}, Da={CASE['Da']}, Ra={CASE['Ra']}, "
-                               f"Pr={CASE['Pr']}, porosity={CASE['porosity']}, {prec} storage; "
-                               f"bench step = {delta} fused steps + Nu + residual",
+                               f"Pr={CASE['Pr']}, porosity={CASE['porosity']}, {prec} storage, "
+                               + (f"implicit tau ({args.tau_iters} Newton steps)" if args.tau_iters
+                                  else "lagged tau") +
+                               f"; bench step = {delta} fused steps + Nu + residual",
                    "grid": [N, N], "fused_steps_per_bench_step": delta,
                    "l2": "state larger than L2 (no flush needed)", "parallelism": f"independent cavity per GPU x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(prec, N),
-                     "peak_source": peak_src, "kernel": f"step_kernel<{prec}>",
-                     "bytes_per_node": BYTES_PER_NODE[prec], "avg_launch_us": kern * 1e6},
+                     "frac": achieved / peak, "traffic": recorded_traffic(key_main, N),
+                     "peak_source": peak_src,
+                     "kernel": f"{'step_kernel' if prec == 'f64' else 'step2_kernel'}<{key_main}>",
+                     "bytes_per_node": bpn_main, "avg_launch_us": kern * 1e6},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -47,6 +47,7 @@ enum {
 
 /* Rows (ny) that lbm_residual_noalloc's fixed scratch area can serve. */
 #define LBM_NOALLOC_MAX_ROWS 16384
+#define LBM_TAU_ITERS_MAX 16   /* largest lbm_opts.tau_iters */
 
 /* Storage precision of the distributions.  Arithmetic is FP64 for LBM_F64
  * and FP32 otherwise.  The *D forms store the deviation of each population
@@ -79,6 +80,21 @@ typedef struct {
                           floor); < 0: 0 for F64 (never), 1e-6 for
                           F32 and F32D, 1e-2 for F16D, 1e-1 for
                           BF16D                                      [-1]   */
+    int tau_iters;     /* how the relaxation time of the strain rate and
+                          the velocity solve is obtained (the paper
+                          does not say: section "Power-law fluid"):
+                          0: lagged -- each node stores the tau of its
+                          last collision (one value per node read and
+                          written every step);
+                          1..LBM_TAU_ITERS_MAX: node-local implicit --
+                          the root of tau = 3 nu_ref D(gamma*(tau)) +
+                          1/2 (Eq. MPL, gamma from the collision started
+                          at tau), by that many Newton steps on ln tau
+                          from tau0; no tau is stored, so a step moves
+                          8 bytes per node less in FP32 storage.  2
+                          reach FP32 rounding, 4 FP64 rounding on
+                          developed flows.  Not built with the batch
+                          API or the adjoint                         [0]    */
 } lbm_opts;
 
 /* Lattice-unit parameters the library derived from the problem groups
@@ -188,7 +204,9 @@ int lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
 /* The post-collision state as FP64 host arrays: f[9][ny][nx], g[5][ny][nx]
  * and tau[ny][nx] (full population values, deviations resolved).  The
  * import rounds to the storage precision.  Any pointer may be NULL (skipped
- * on export, left unchanged on import).  Synchronous. */
+ * on export, left unchanged on import).  With tau_iters > 0 tau is not part
+ * of the state: the export gives the implicit tau each node's next
+ * collision starts from, and the import ignores it.  Synchronous. */
 int lbm_get_state_f64(lbm_ctx *ctx, double *f, double *g, double *tau);
 int lbm_set_state_f64(lbm_ctx *ctx, const double *f, const double *g,
                       const double *tau);

@@ -50,7 +50,7 @@ __device__ __forceinline__ void push(typename Store<PREC>::S *__restrict__ A, co
 }
 
 // ------------------------------------------------------- one node / thread
-template <int PREC>
+template <int PREC, int TAU>
 __global__ void __launch_bounds__(128)
 aa_even_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::TauS *__restrict__ tau,
                Phys<typename Store<PREC>::R> p)
@@ -66,15 +66,15 @@ aa_even_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::Ta
 #pragma unroll
     for (int i = 0; i < 5; i++) g[i] = St::ld(A + 9 * P, i * P + k, R(rest_g(i)));
     Macro<R> m;
-    const R t = collide<R>(p, f, g, R(tau[k]), m, k);
+    const R t = collide<R>(p, f, g, tau_start<TAU, R, 2>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) St::st(A, opp(i) * P + k, f[i], R(rest_f(opp(i))));
 #pragma unroll
     for (int i = 0; i < 5; i++) St::st(A + 9 * P, opp(i) * P + k, g[i], R(rest_g(opp(i))));
-    tau[k] = typename St::TauS(t);
+    if constexpr (TAU == 0) tau[k] = typename St::TauS(t);
 }
 
-template <int PREC, class R>
+template <int PREC, class R, int TAU>
 __device__ __forceinline__ void odd_node(typename Store<PREC>::S *__restrict__ A,
                                          typename Store<PREC>::TauS *__restrict__ tau, const Phys<R> &p, int x,
                                          int y)
@@ -83,23 +83,23 @@ __device__ __forceinline__ void odd_node(typename Store<PREC>::S *__restrict__ A
     R f[9], g[5];
     pull<PREC, R, true>(A, p, x, y, f, g);
     Macro<R> m;
-    const R t = collide<R>(p, f, g, R(tau[k]), m, k);
+    const R t = collide<R>(p, f, g, tau_start<TAU, R, 2>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
     push<PREC, R>(A, p, x, y, f, g);
-    tau[k] = typename Store<PREC>::TauS(t);
+    if constexpr (TAU == 0) tau[k] = typename Store<PREC>::TauS(t);
 }
 
-template <int PREC>
+template <int PREC, int TAU>
 __global__ void __launch_bounds__(128)
 aa_odd_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::TauS *__restrict__ tau,
               Phys<typename Store<PREC>::R> p)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= p.nx) return;
-    odd_node<PREC, typename Store<PREC>::R>(A, tau, p, x, y);
+    odd_node<PREC, typename Store<PREC>::R, TAU>(A, tau, p, x, y);
 }
 
 // ------------------------------------------------------ two nodes / thread
-template <int PREC>
+template <int PREC, int TAU>
 __global__ void __launch_bounds__(128)
 aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
 {
@@ -112,10 +112,10 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
         for (int i = 0; i < 9; i++) f[i] = St::ld(A, i * P + k, float(rest_f(i)));
         for (int i = 0; i < 5; i++) g[i] = St::ld(A + 9 * P, i * P + k, float(rest_g(i)));
         Macro<float> m;
-        const float t = collide<float>(p, f, g, tau[k], m, k);
+        const float t = collide<float>(p, f, g, tau_start<TAU, float, 2>(p, f, g, k, [&] { return tau[k]; }), m, k);
         for (int i = 0; i < 9; i++) St::st(A, opp(i) * P + k, f[i], float(rest_f(opp(i))));
         for (int i = 0; i < 5; i++) St::st(A + 9 * P, opp(i) * P + k, g[i], float(rest_g(opp(i))));
-        tau[k] = t;
+        if constexpr (TAU == 0) tau[k] = t;
         return;
     }
     F2 f[9], g[5];
@@ -124,12 +124,13 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
 #pragma unroll
     for (int i = 0; i < 5; i++) g[i] = St::ld2(A + (9 + i) * P, k, float(rest_g(i)));
     Macro<F2> m;
-    const F2 t = collide<F2>(p2, f, g, F2(*reinterpret_cast<const float2 *>(tau + k)), m, k);
+    const F2 t0 = tau_start<TAU, F2, 2>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
+    const F2 t = collide<F2>(p2, f, g, t0, m, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) St::st2(A + opp(i) * P, k, f[i], float(rest_f(opp(i))));
 #pragma unroll
     for (int i = 0; i < 5; i++) St::st2(A + (9 + opp(i)) * P, k, g[i], float(rest_g(opp(i))));
-    *reinterpret_cast<float2 *>(tau + k) = t.v;
+    if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tau + k) = t.v;
 }
 
 // Odd-step pushes of a pair (nodes x0, x0 + 1) one node to the right / left
@@ -155,7 +156,7 @@ __device__ __forceinline__ void push_left(typename Store<PREC>::S *base, int64_t
     if (lane == 0) St::st(base, kr - 1, v.v.x, rest);
 }
 
-template <int PREC>
+template <int PREC, int TAU>
 __global__ void __launch_bounds__(128)
 aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
 {
@@ -167,7 +168,7 @@ aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau,
     const bool fast = y > 0 && y < p.ny - 1 && wx > 0 && wx + 64 < p.nx;
     if (!fast) {
         for (int j = 0; j < 2; j++)
-            if (x0 + j < p.nx) odd_node<PREC, float>(A, tau, p, x0 + j, y);
+            if (x0 + j < p.nx) odd_node<PREC, float, TAU>(A, tau, p, x0 + j, y);
         return;
     }
     const int64_t P = p.plane, W = p.pitch;
@@ -196,7 +197,8 @@ aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau,
     g[3] = from_right(St::ld2(gs + P, k, float(rest_g(1))), l31 ? St::ld(gs + P, k + 2, float(rest_g(1))) : 0.f, lane);
     g[4] = St::ld2(gs + 2 * P, k + W, float(rest_g(2)));
     Macro<F2> m;
-    const F2 t = collide<F2>(p2, f, g, F2(*reinterpret_cast<const float2 *>(tau + k)), m, k);
+    const F2 t0 = tau_start<TAU, F2, 2>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
+    const F2 t = collide<F2>(p2, f, g, t0, m, k);
     // push f*_i(x) into slot i of node x + e_i
     St::st2(fs, k, f[0], float(rest_f(0)));
     push_right<PREC>(fs + P, k, f[1], float(rest_f(1)), lane);
@@ -212,7 +214,7 @@ aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau,
     St::st2(gs + 2 * P, k + W, g[2], float(rest_g(2)));
     push_left<PREC>(gs + 3 * P, k, g[3], float(rest_g(3)), lane);
     St::st2(gs + 4 * P, k - W, g[4], float(rest_g(4)));
-    *reinterpret_cast<float2 *>(tau + k) = t.v;
+    if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tau + k) = t.v;
 }
 
 // Form O -> form E in place, without a collision: each interior link
@@ -249,26 +251,37 @@ aa_normalize_kernel(typename Store<PREC>::S *__restrict__ A, Phys<typename Store
 }
 
 // ------------------------------------------------------------- launchers
-template <int PREC>
-static cudaError_t aa_step_t(lbm_ctx *c)
+template <int PREC, int TAU>
+static void aa_launch(lbm_ctx *c)
 {
     using St = Store<PREC>;
     auto *A = (typename St::S *)c->buf.dist[0];
     if constexpr (PREC == LBM_F64) {
         const dim3 grid((c->nx + 127) / 128, c->ny);
         if (c->aa_form_o)
-            aa_even_kernel<PREC><<<grid, 128, 0, c->stream>>>(A, (double *)c->buf.tau[0], make_params<double>(c));
+            aa_even_kernel<PREC, TAU><<<grid, 128, 0, c->stream>>>(A, (double *)c->buf.tau[0],
+                                                                 make_params<double>(c));
         else
-            aa_odd_kernel<PREC><<<grid, 128, 0, c->stream>>>(A, (double *)c->buf.tau[0], make_params<double>(c));
+            aa_odd_kernel<PREC, TAU><<<grid, 128, 0, c->stream>>>(A, (double *)c->buf.tau[0],
+                                                                make_params<double>(c));
     } else {
         const dim3 grid((c->nx + 255) / 256, c->ny);
         if (c->aa_form_o)
-            aa_even2_kernel<PREC><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0], make_params<float>(c),
-                                                             make_params<F2>(c));
+            aa_even2_kernel<PREC, TAU><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0],
+                                                                  make_params<float>(c), make_params<F2>(c));
         else
-            aa_odd2_kernel<PREC><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0], make_params<float>(c),
-                                                            make_params<F2>(c));
+            aa_odd2_kernel<PREC, TAU><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0],
+                                                                 make_params<float>(c), make_params<F2>(c));
     }
+}
+
+template <int PREC>
+static cudaError_t aa_step_t(lbm_ctx *c)
+{
+    if (c->opts.tau_iters > 0)
+        aa_launch<PREC, 1>(c);
+    else
+        aa_launch<PREC, 0>(c);
     c->aa_form_o = !c->aa_form_o;
     return cudaGetLastError();
 }

@@ -296,7 +296,7 @@ extern "C" int lbm_adjoint_nu(lbm_ctx *c, int64_t steps, int ckpt_every, int fro
                               double *dn, double *dRa, double *peak_bytes)
 {
     if (!c || steps < 1 || ckpt_every < 1) return LBM_ERR_ARG;
-    if (c->opts.layout != 0) return LBM_ERR_UNSUPPORTED;
+    if (c->opts.layout != 0 || c->opts.tau_iters != 0) return LBM_ERR_UNSUPPORTED;
     if (cudaSetDevice(c->device) != cudaSuccess) return LBM_ERR_CUDA;
     switch (c->opts.prec) {
     case LBM_F64: return run_adjoint<LBM_F64>(c, steps, ckpt_every, from_rest, J, dDa, dn, dRa, peak_bytes);

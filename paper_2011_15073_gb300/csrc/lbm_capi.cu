@@ -48,7 +48,7 @@ int map_lattice(int nx, int ny, double n, double Da, double Ra, double Pr, doubl
     if (o.prec < LBM_F64 || o.prec > LBM_F32D || !(o.Ma > 0) || o.Ma > 1 ||
         (o.clamp_mode != 0 && o.clamp_mode != 1) || (o.porous_model != 0 && o.porous_model != 1) ||
         !(o.s_e > 0) || !(o.s_e < 2) || !(o.s_p > 0) || !(o.s_p < 2) || o.resid_interval < 1 ||
-        o.device < -1)
+        o.device < -1 || o.tau_iters < 0 || o.tau_iters > LBM_TAU_ITERS_MAX)
         return LBM_ERR_ARG;
     if (o.layout != 0 && o.layout != 1) return LBM_ERR_UNSUPPORTED;
     memset(L, 0, sizeof(*L));
@@ -214,6 +214,7 @@ void lbm_default_opts(lbm_opts *o)
     o->cuda_stream = nullptr;
     o->device = -1;
     o->stag_floor = -1.0;
+    o->tau_iters = 0;
 }
 
 int lbm_init(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra, double Pr,

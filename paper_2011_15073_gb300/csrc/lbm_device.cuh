@@ -97,6 +97,10 @@ struct Phys {
     // paths), indexed like the state planes; K = Da L2.
     const void *da;
     V L2, eFe;                 // L^2 and eps F_eps
+    // Node-local implicit relaxation time (tau_iters > 0): Newton steps per
+    // collision, their start tau0 and 3 nu_ref.
+    int tau_iters;
+    V tau0, nu3;
 };
 
 // ------------------------------------------------------------ parameters
@@ -133,6 +137,9 @@ inline Phys<V> make_params(const lbm_ctx *c)
     p.da = c->d_da;
     p.L2 = V(L.L * L.L);
     p.eFe = V(L.eps * L.Feps);
+    p.tau_iters = c->opts.tau_iters;
+    p.tau0 = V(L.tau0);
+    p.nu3 = V(3.0 * L.nu_ref);
     return p;
 }
 
@@ -391,6 +398,89 @@ __device__ __forceinline__ F2 apparent(const Phys<F2> &p, F2 gs)
 {
     return F2(apparent_s(p.clamp_mode, gs.v.x, p.gamma1.v.x, p.gamma2.v.x, p.nm1.v.x, p.D_hi.v.x),
               apparent_s(p.clamp_mode, gs.v.y, p.gamma1.v.x, p.gamma2.v.x, p.nm1.v.x, p.D_hi.v.x));
+}
+
+// ------------------------------------------- node-local implicit tau
+// The relaxation time a collision starts from, solved at the node from its
+// own streamed populations instead of read from a stored (lagged) value: the
+// root of tau = Phi(tau) = 3 nu_ref D(gamma*(tau)) + 1/2 (Eq. MPL), where
+// gamma(tau) is the strain rate macro() and collide() compute when started
+// from tau (viscosity of the velocity solve, s7 = s8 = 1/tau).  p.tau_iters
+// Newton steps on ln tau from the rest-state tau0:
+//   tau <- tau (Phi / tau)^(1/J),  J = 1 + (n - 1) R (Phi - 1/2) / Phi
+// where gamma1 < gamma* < gamma2 (D has slope) and J = 1 elsewhere, with
+// R = (B^2 + C^2) / (A^2 + B^2 + C^2) = d ln|gamma| / d ln(1/tau) at fixed
+// velocity.  J lies between n and 1, so every step is defined.
+template <class R>
+__device__ __forceinline__ R tau_newton_s(R tau, R gs, R bc, R ss, R g1, R g2, R nm1, R Dhi, int mode, R nu3)
+{
+    const R phi = vfma(nu3, apparent_s(mode, gs, g1, g2, nm1, Dhi), R(0.5));
+    if (!(gs > g1 && gs < g2)) return phi;
+    const R J = vfma(nm1 * (bc * vrcp(ss)), (phi - R(0.5)) * vrcp(phi), R(1));
+    return tau * vpow(phi * vrcp(tau), vrcp(J));
+}
+template <class V>
+__device__ __forceinline__ V tau_newton(const Phys<V> &p, V tau, V gs, V bc, V ss)
+{
+    return tau_newton_s(tau, gs, bc, ss, p.gamma1, p.gamma2, p.nm1, p.D_hi, p.clamp_mode, p.nu3);
+}
+template <>
+__device__ __forceinline__ F2 tau_newton(const Phys<F2> &p, F2 tau, F2 gs, F2 bc, F2 ss)
+{
+    const float g1 = p.gamma1.v.x, g2 = p.gamma2.v.x, nm1 = p.nm1.v.x, Dhi = p.D_hi.v.x, nu3 = p.nu3.v.x;
+    return F2(tau_newton_s(tau.v.x, gs.v.x, bc.v.x, ss.v.x, g1, g2, nm1, Dhi, p.clamp_mode, nu3),
+              tau_newton_s(tau.v.y, gs.v.y, bc.v.y, ss.v.y, g1, g2, nm1, Dhi, p.clamp_mode, nu3));
+}
+
+template <class V, int FIELD = 2>
+__device__ __forceinline__ V implicit_tau(const Phys<V> &p, const V f[9], const V g[5], int64_t k)
+{
+    const Porous<V> q = porous_at<V, FIELD>(p, k);
+    // moments that do not depend on tau (as in macro() and collide())
+    const V sax = (f[1] + f[2]) + (f[3] + f[4]);
+    const V sdg = (f[5] + f[6]) + (f[7] + f[8]);
+    const V rho = f[0] + sax + sdg;
+    const V jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    const V jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    const V T = g[0] + (g[1] + g[2]) + (g[3] + g[4]);
+    const V irho = vrcp(rho);
+    const V vx = jx * irho;
+    const V vy = vfma(p.half_eps, p.gbeta * (T - p.Tm), jy * irho);
+    const V c1v = q.c1 * vsqrt(vfma(vx, vx, vy * vy));
+    const V e = vfma(V(2), sdg, vfma(V(-4), f[0], -sax));
+    const V pxx = (f[1] + f[3]) - (f[2] + f[4]);
+    const V pxy = (f[5] + f[7]) - (f[6] + f[8]);
+    const V rie = rho * p.inv_eps;
+    const V gsc = V(3) * irho * p.gamma_scale;
+    V tau = p.tau0;
+#pragma unroll 1
+    for (int it = 0; it < p.tau_iters; ++it) {
+        const V nu = (tau - V(0.5)) * V(1.0 / 3.0);
+        const V c0 = vfma(q.heK, nu, V(0.5));
+        const V iden = vrcp(c0 + vsqrt(vfma(c0, c0, c1v)));
+        const V ux = vx * iden, uy = vy * iden;
+        const V u2e3 = V(3) * vfma(ux, ux, uy * uy) * p.inv_eps;
+        const V e_eq = vfma(rho, u2e3, V(-2) * rho);
+        const V w = vrcp(tau);
+        const V A = V(1.4 / 6.0) * (e - e_eq);
+        const V B = V(0.5) * w * (pxx - rie * vfma(ux, ux, -(uy * uy)));
+        const V C = w * (pxy - rie * (ux * uy));
+        const V bc = vfma(B, B, C * C);
+        const V ss = vfma(A, A, bc);
+        tau = tau_newton(p, tau, gsc * vsqrt(ss), bc, ss);
+    }
+    return tau;
+}
+
+// tau the collision of a node starts from: TAU 0 the stored lagged value
+// (loaded only then), TAU 1 the implicit solve.
+template <int TAU, class V, int FIELD, class Load>
+__device__ __forceinline__ V tau_start(const Phys<V> &p, const V f[9], const V g[5], int64_t k, Load load)
+{
+    if constexpr (TAU == 1)
+        return implicit_tau<V, FIELD>(p, f, g, k);
+    else
+        return load();
 }
 
 // Full node update in place: f, g become the post-collision populations.

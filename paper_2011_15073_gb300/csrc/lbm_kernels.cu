@@ -28,8 +28,9 @@ __global__ void init_kernel(typename Store<PREC>::S *__restrict__ dist,
 }
 
 // One time step of the whole cavity (pull scheme, two buffers); the node
-// and tile bodies are in lbm_step.cuh.
-template <int PREC, int FIELD>
+// and tile bodies are in lbm_step.cuh.  TAU 1: node-local implicit tau (the
+// tau planes are neither read nor written).
+template <int PREC, int FIELD, int TAU>
 __global__ void __launch_bounds__(128)
 step_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
             const typename Store<PREC>::TauS *__restrict__ tsrc, typename Store<PREC>::TauS *__restrict__ tdst,
@@ -37,15 +38,29 @@ step_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= p.nx) return;
-    step_node<PREC, typename Store<PREC>::R, FIELD>(src, dst, tsrc, tdst, p, x, y);
+    step_node<PREC, typename Store<PREC>::R, FIELD, TAU>(src, dst, tsrc, tdst, p, x, y);
 }
 
-template <int PREC, int FIELD>
+template <int PREC, int FIELD, int TAU>
 __global__ void __launch_bounds__(128)
 step2_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
              const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
 {
-    step2_tile<PREC, FIELD>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
+    step2_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
+}
+
+// tau the next collision of every node starts from, in implicit mode (the
+// solve of implicit_tau on the streamed populations) -> out[ny][nx].
+template <int PREC, bool REV>
+__global__ void tau_next_kernel(const typename Store<PREC>::S *__restrict__ src,
+                                Phys<typename Store<PREC>::R> p, double *__restrict__ out)
+{
+    using R = typename Store<PREC>::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= p.nx) return;
+    R f[9], g[5];
+    pull<PREC, R, REV>(src, p, x, y, f, g);
+    out[(int64_t)y * p.nx + x] = double(implicit_tau<R>(p, f, g, (int64_t)y * p.pitch + x));
 }
 
 // Streamed macroscopic fields: rho, u_x, u_y, T, nu -> out[5][ny][nx].
@@ -65,7 +80,7 @@ __global__ void fields_kernel(const typename Store<PREC>::S *__restrict__ src,
     R f[9], g[5];
     pull<PREC, R, REV>(src, p, x, y, f, g);
     Macro<R> m;
-    collide<R>(p, f, g, R(tsrc[k]), m, k);
+    collide<R>(p, f, g, p.tau_iters ? implicit_tau<R>(p, f, g, k) : R(tsrc[k]), m, k);
     out[q] = double(m.rho);
     out[n + q] = double(m.ux);
     out[2 * n + q] = double(m.uy);
@@ -151,7 +166,8 @@ residual_kernel(const typename Store<PREC>::S *__restrict__ src,
         const int y = (int)(q / p.nx), x = (int)(q - (int64_t)y * p.nx);
         R f[9], g[5];
         pull<PREC, R, REV>(src, p, x, y, f, g);
-        const Macro<R> m = macro<R>(p, f, g, R(tsrc[(int64_t)y * p.pitch + x]), (int64_t)y * p.pitch + x);
+        const int64_t k = (int64_t)y * p.pitch + x;
+        const Macro<R> m = macro<R>(p, f, g, p.tau_iters ? implicit_tau<R>(p, f, g, k) : R(tsrc[k]), k);
         const double v[3] = {double(m.ux), double(m.uy), double(m.T)};
         for (int c = 0; c < 3; c++) {
             const double old = first ? v[c] : snap[c * n + q];
@@ -257,22 +273,29 @@ static cudaError_t init_t(lbm_ctx *c)
     return cudaGetLastError();
 }
 
-template <int PREC>
-static cudaError_t step_buffers_t(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
+template <int PREC, int TAU>
+static cudaError_t step_buffers_tau(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
 {
     using St = Store<PREC>;
     if constexpr (PREC == LBM_F64) {
-        auto *kern = c->d_da ? step_kernel<PREC, 1> : step_kernel<PREC, 0>;
+        auto *kern = c->d_da ? step_kernel<PREC, 1, TAU> : step_kernel<PREC, 0, TAU>;
         kern<<<node_grid(c, 128), 128, 0, c->stream>>>(
             (const typename St::S *)src, (typename St::S *)dst, (const typename St::TauS *)tsrc,
             (typename St::TauS *)tdst, make_params<typename St::R>(c));
     } else {
-        auto *kern = c->d_da ? step2_kernel<PREC, 1> : step2_kernel<PREC, 0>;
+        auto *kern = c->d_da ? step2_kernel<PREC, 1, TAU> : step2_kernel<PREC, 0, TAU>;
         kern<<<node_grid(c, 256), 128, 0, c->stream>>>(
             (const typename St::S *)src, (typename St::S *)dst, (const float *)tsrc, (float *)tdst,
             make_params<float>(c), make_params<F2>(c));
     }
     return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t step_buffers_t(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
+{
+    return c->opts.tau_iters > 0 ? step_buffers_tau<PREC, 1>(c, src, dst, tsrc, tdst)
+                                 : step_buffers_tau<PREC, 0>(c, src, dst, tsrc, tdst);
 }
 
 template <int PREC>
@@ -340,6 +363,12 @@ static cudaError_t export_t(lbm_ctx *c, double *out)
     kern<<<node_grid(c, 128), 128, 0, c->stream>>>(
         out, (const typename St::S *)c->buf.dist[c->cur], (const typename St::TauS *)c->buf.tau[c->cur],
         c->nx, c->ny, c->pitch, c->plane);
+    if (c->opts.tau_iters > 0) {  // no stored tau: report the next collision's implicit tau
+        auto *tk = c->opts.layout == 1 ? tau_next_kernel<PREC, true> : tau_next_kernel<PREC, false>;
+        tk<<<node_grid(c, 128), 128, 0, c->stream>>>((const typename St::S *)c->buf.dist[c->cur],
+                                                     make_params<typename St::R>(c),
+                                                     out + (int64_t)14 * c->nx * c->ny);
+    }
     return cudaGetLastError();
 }
 

@@ -71,7 +71,9 @@ residual_rows_kernel(const typename lbm::Store<PREC>::S *__restrict__ src,
     for (int x = threadIdx.x; x < p.nx; x += blockDim.x) {
         R f[9], g[5];
         lbm::pull<PREC, R>(src, p, x, y, f, g);
-        const lbm::Macro<R> m = lbm::macro<R>(p, f, g, R(tsrc[(int64_t)y * p.pitch + x]), (int64_t)y * p.pitch + x);
+        const int64_t k = (int64_t)y * p.pitch + x;
+        const lbm::Macro<R> m =
+            lbm::macro<R>(p, f, g, p.tau_iters ? lbm::implicit_tau<R>(p, f, g, k) : R(tsrc[k]), k);
         const double v[3] = {double(m.ux), double(m.uy), double(m.T)};
         const int64_t q = (int64_t)y * p.nx + x;
         for (int c = 0; c < 3; c++) {

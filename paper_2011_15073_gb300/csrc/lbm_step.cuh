@@ -7,8 +7,10 @@
 
 namespace lbm {
 
-// Pull, collide and store one node (wall rules included).
-template <int PREC, class R, int FIELD = 2>
+// Pull, collide and store one node (wall rules included).  TAU 0: the
+// collision starts from the stored lagged tau and stores its new tau; TAU 1:
+// from the node-local implicit tau, and no tau is read or written.
+template <int PREC, class R, int FIELD = 2, int TAU = 0>
 __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restrict__ src,
                                           typename Store<PREC>::S *__restrict__ dst,
                                           const typename Store<PREC>::TauS *__restrict__ tsrc,
@@ -20,12 +22,13 @@ __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restr
     R f[9], g[5];
     pull<PREC, R>(src, p, x, y, f, g);
     Macro<R> m;
-    const R tau = collide<R, FIELD>(p, f, g, R(tsrc[k]), m, k);
+    const R t0 = tau_start<TAU, R, FIELD>(p, f, g, k, [&] { return R(tsrc[k]); });
+    const R tau = collide<R, FIELD>(p, f, g, t0, m, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) St::st(dst, i * p.plane + k, f[i], R(rest_f(i)));
 #pragma unroll
     for (int i = 0; i < 5; i++) St::st(dst + 9 * p.plane, i * p.plane + k, g[i], R(rest_g(i)));
-    tdst[k] = typename St::TauS(tau);
+    if constexpr (TAU == 0) tdst[k] = typename St::TauS(tau);
 }
 
 // One tile of a row: thread t of the block updates nodes xbase + 2t and
@@ -34,8 +37,8 @@ __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restr
 // x-shifted populations exchanged by warp shuffles, both nodes' arithmetic
 // on the packed FP32x2 pipe; any warp that touches a wall or the ragged end
 // of a row updates its nodes one at a time with the wall rules.  The branch
-// is uniform per warp.
-template <int PREC, int FIELD = 2>
+// is uniform per warp.  TAU as for step_node.
+template <int PREC, int FIELD = 2, int TAU = 0>
 __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__restrict__ src,
                                            typename Store<PREC>::S *__restrict__ dst,
                                            const float *__restrict__ tsrc, float *__restrict__ tdst,
@@ -49,7 +52,7 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
     const bool fast = y > 0 && y < p.ny - 1 && wx > 0 && wx + 64 < p.nx;
     if (!fast) {
         for (int j = 0; j < 2; j++)
-            if (x0 + j < p.nx) step_node<PREC, float, FIELD>(src, dst, tsrc, tdst, p, x0 + j, y);
+            if (x0 + j < p.nx) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, x0 + j, y);
         return;
     }
     const int64_t P = p.plane, W = p.pitch;
@@ -76,14 +79,14 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
     g[2] = St::ld2(gs + 2 * P, k - W, float(rest_g(2)));
     g[3] = from_right(St::ld2(gs + 3 * P, k, float(rest_g(3))), l31 ? St::ld(gs + 3 * P, k + 2, float(rest_g(3))) : 0.f, lane);
     g[4] = St::ld2(gs + 4 * P, k + W, float(rest_g(4)));
-    const F2 tau_prev(*reinterpret_cast<const float2 *>(tsrc + k));
+    const F2 t0 = tau_start<TAU, F2, FIELD>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tsrc + k)); });
     Macro<F2> m;
-    const F2 tau = collide<F2, FIELD>(p2, f, g, tau_prev, m, k);
+    const F2 tau = collide<F2, FIELD>(p2, f, g, t0, m, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) St::st2(dst + i * P, k, f[i], float(rest_f(i)));
 #pragma unroll
     for (int i = 0; i < 5; i++) St::st2(dst + (9 + i) * P, k, g[i], float(rest_g(i)));
-    *reinterpret_cast<float2 *>(tdst + k) = tau.v;
+    if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tdst + k) = tau.v;
 }
 
 }  // namespace lbm

@@ -39,7 +39,7 @@ class Opts(ctypes.Structure):
                 ("porous_model", ctypes.c_int), ("s_e", ctypes.c_double), ("s_p", ctypes.c_double),
                 ("resid_interval", ctypes.c_int), ("layout", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
-                ("stag_floor", ctypes.c_double)]
+                ("stag_floor", ctypes.c_double), ("tau_iters", ctypes.c_int)]
 
 
 class Lattice(ctypes.Structure):
@@ -136,7 +136,10 @@ def _stream_handle(stream):
 def default_opts(**kw) -> Opts:
     o = Opts()
     lib().lbm_default_opts(ctypes.byref(o))
+    names = {f[0] for f in Opts._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown lbm_opts field {k!r}")
         if k == "prec" and isinstance(v, str):
             v = PREC_NAMES[v]
         if k == "cuda_stream":

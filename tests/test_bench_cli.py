@@ -5,6 +5,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -27,3 +29,14 @@ def test_bench_defines_every_leg():
                "def dist_env", "class Clocks", "def study_tables", "def study_precision", "def study_batch",
                "def study_adjoint", "def main"):
         assert fn in src, fn
+
+
+def test_variant_names():
+    import bench
+    assert bench.parse_variant("f32") == ("f32", 0, 0)
+    assert bench.parse_variant("f32@aa") == ("f32", 1, 0)
+    assert bench.parse_variant("f32@tau2") == ("f32", 0, 2)
+    assert bench.parse_variant("f32d@aa@tau3") == ("f32d", 1, 3)
+    assert bench.bytes_per_node("f32", 2) == 112 and bench.bytes_per_node("f64", 1) == 224
+    with pytest.raises(ValueError):
+        bench.parse_variant("f32@bogus")

@@ -49,6 +49,7 @@ def test_default_opts(L):
     assert (o.prec, o.Ma, o.clamp_mode, o.porous_model, o.s_e, o.s_p, o.resid_interval, o.layout) == \
         (0, 0.1, 0, 1, 1.5, 1.5, 1000, 0)
     assert not o.cuda_stream and o.device == -1 and o.stag_floor == -1.0
+    assert o.tau_iters == 0
 
 
 @pytest.mark.parametrize("args,code", [
@@ -74,7 +75,7 @@ def test_init_rejects_bad_arguments(L, args, code):
 @pytest.mark.parametrize("field,value,code", [
     ("prec", 5, -1), ("Ma", 0.0, -1), ("clamp_mode", 2, -1), ("porous_model", 3, -1),
     ("s_e", 2.5, -1), ("s_p", 0.0, -1), ("resid_interval", 0, -1), ("layout", 2, -7),
-    ("device", -2, -1),
+    ("device", -2, -1), ("tau_iters", -1, -1), ("tau_iters", 17, -1),
 ])
 def test_init_rejects_bad_options(L, field, value, code):
     from paper_2011_15073_gb300 import lbm
@@ -102,3 +103,33 @@ def test_strerror_names_codes(L):
     from paper_2011_15073_gb300 import lbm
     for code, name in lbm.ERRORS.items():
         assert lbm.strerror(code).startswith(name)
+
+
+def test_binding_rejects_unknown_option():
+    from paper_2011_15073_gb300 import lbm
+    with pytest.raises(TypeError):
+        lbm.default_opts(tau_iter=2)
+
+
+def test_header_struct_matches_binding():
+    """lbm_opts in include/lbm.h and the ctypes mirror list the same fields
+    in the same order."""
+    import re
+    from paper_2011_15073_gb300 import lbm
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    body = src[src.index("typedef struct {\n    int prec;"):src.index("} lbm_opts;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"\b(?:int|double|void\s*\*)\s*\**\s*(\w+(?:\s*,\s*\w+)*)\s*;", body.split("{", 1)[1])
+    flat = [n.strip() for grp in names for n in grp.split(",")]
+    assert flat == [f[0] for f in lbm.Opts._fields_]
+
+
+def test_batch_refuses_implicit_tau(L):
+    """The batched sweep is built for the lagged tau only (checked before any
+    device work)."""
+    from paper_2011_15073_gb300 import lbm
+    o = lbm.default_opts(tau_iters=2, resid_interval=1000)
+    case = lbm.Case(16, 16, 0.6, 1e-2, 1e5, 6.2, 0.6)
+    h = ctypes.c_void_p()
+    assert L.lbm_batch_create(ctypes.byref(h), ctypes.byref(case), 1, ctypes.byref(o)) == -7
+    assert h.value is None

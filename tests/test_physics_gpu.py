@@ -75,3 +75,23 @@ def test_energy_balance_and_centro_symmetry(lbm, porous_model, porosity):
     assert np.max(np.abs(T + T[::-1, ::-1] - 1.0)) < 5e-3
     u = fl["ux"]
     assert np.max(np.abs(u + u[::-1, ::-1])) < 5e-2 * np.max(np.abs(u))
+
+
+def test_implicit_tau_reaches_the_lagged_steady_state(lbm):
+    """At a steady state the lagged tau equals the law at its own strain
+    rate, i.e. the implicit root: both ways of finding tau must converge to
+    the same cavity (FP64, residual below 1e-11)."""
+    out = []
+    for K in (0, 4):
+        with lbm.Cavity(48, 48, 0.7, 1e-2, 2e4, 6.2, 0.6, prec="f64", clamp_mode=1, tau_iters=K,
+                        resid_interval=1000) as cav:
+            steps, r, why = cav.run_to_steady(1e-11, 2_000_000)
+            assert why == 0, (K, steps, r)
+            fl = cav.fields()
+            out.append((cav.nusselt()[0], fl["nu"], fl["ux"]))
+    (nu0, v0, u0), (nu1, v1, u1) = out
+    # a residual of 1e-11 per 1000 steps leaves each run within ~1e-8 of its
+    # fixed point (slowest decay ~1e5 steps)
+    assert abs(nu1 - nu0) <= 1e-7 * nu0
+    assert np.max(np.abs(v1 - v0)) <= 1e-6 * np.max(v0)
+    assert np.max(np.abs(u1 - u0)) <= 1e-6 * np.max(np.abs(u0))
