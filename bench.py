@@ -219,6 +219,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value, world, device):
+    """The largest value over the ranks (the slowest rank's time): one
+    all-reduce of a scalar, nothing on the data path."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_units(world, N, delta, steps):
+    """Node updates of the whole job: every rank runs its own N x N cavity
+    for steps x delta time steps (weak scaling)."""
+    return world * N * N * delta * steps
+
+
 def time_ours(lbm, torch, N, prec, steps, warmup, delta, stream, layout=0, tau_iters=0):
     """Device-resident run: returns (seconds for `steps` bench steps, avg fused
     kernel seconds, kernels launched in the timed region, Nu)."""
@@ -568,11 +586,8 @@ def main():
         total, kern, launches, nu = time_ours(lbm, torch, N, prec, args.steps, max(3, args.warmup), delta, stream,
                                               tau_iters=args.tau_iters)
     barrier()
-    if world > 1:
-        t = torch.tensor([total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total = float(t.item())
-    units = world * N * N * delta * args.steps
+    total = max_over_ranks(total, world, "cuda")
+    units = whole_job_units(world, N, delta, args.steps)
     mlups = units / total / 1e6
     peak, peak_src = hbm_peak()
     bpn_main = bytes_per_node(prec, args.tau_iters)
