@@ -38,17 +38,19 @@ TAU_BYTES = {"f64": 16, "f32": 8, "f32d": 8, "bf16d": 8, "f16d": 8}
 
 
 def parse_variant(v):
-    """'prec[@aa][@tauK]' -> (prec, layout, tau_iters)."""
+    """'prec[@aa][@tauK][@tma|@reg]' -> (prec, layout, tau_iters, staging)."""
     parts = v.split("@")
-    layout, tau_iters = 0, 0
+    layout, tau_iters, staging = 0, 0, 0
     for m in parts[1:]:
         if m == "aa":
             layout = 1
         elif m.startswith("tau") and m[3:].isdigit():
             tau_iters = int(m[3:])
+        elif m in ("tma", "reg"):
+            staging = 2 if m == "tma" else 1
         else:
             raise ValueError(f"unknown variant modifier {m!r} in {v!r}")
-    return parts[0], layout, tau_iters
+    return parts[0], layout, tau_iters, staging
 
 
 def bytes_per_node(prec, tau_iters=0):
@@ -108,9 +110,12 @@ def parse():
                     help="fused time steps per bench step (the convergence-check interval)")
     ap.add_argument("--variant-delta", type=int, default=200)
     ap.add_argument("--prec", default="f32")
+    ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2],
+                    help="step-kernel inputs: 0 auto, 1 straight to registers, 2 bulk copies to shared memory")
     ap.add_argument("--tau-iters", type=int, default=0,
                     help="0: lagged tau (stored per node); K > 0: node-local implicit tau, K Newton steps")
-    ap.add_argument("--variants", default="f64,f32d,f32@aa,f32@tau2,f32@aa@tau2,bf16d,f16d",
+    ap.add_argument("--variants", default="f64,f32d,f32@aa,f32@tau2,f32@tma,f32@tau2@tma,bf16d,bf16d@tma,"
+                                          "f16d,f16d@tma",
                     help="other storage precisions measured beside the headline ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -237,10 +242,11 @@ def whole_job_units(world, N, delta, steps):
     return world * N * N * delta * steps
 
 
-def time_ours(lbm, torch, N, prec, steps, warmup, delta, stream, layout=0, tau_iters=0):
+def time_ours(lbm, torch, N, prec, steps, warmup, delta, stream, layout=0, tau_iters=0, staging=0):
     """Device-resident run: returns (seconds for `steps` bench steps, avg fused
     kernel seconds, kernels launched in the timed region, Nu)."""
-    cav = lbm.Cavity(N, N, prec=prec, cuda_stream=stream, layout=layout, tau_iters=tau_iters, **CASE)
+    cav = lbm.Cavity(N, N, prec=prec, cuda_stream=stream, layout=layout, tau_iters=tau_iters, staging=staging,
+                     **CASE)
     try:
         cav.residual()   # first call stores the snapshot
         for _ in range(warmup):
@@ -584,7 +590,7 @@ def main():
     barrier()
     with Clocks(local) as clk:
         total, kern, launches, nu = time_ours(lbm, torch, N, prec, args.steps, max(3, args.warmup), delta, stream,
-                                              tau_iters=args.tau_iters)
+                                              tau_iters=args.tau_iters, staging=args.staging)
     barrier()
     total = max_over_ranks(total, world, "cuda")
     units = whole_job_units(world, N, delta, args.steps)
@@ -592,12 +598,12 @@ def main():
     peak, peak_src = hbm_peak()
     bpn_main = bytes_per_node(prec, args.tau_iters)
     achieved = bpn_main * N * N / kern / 1e9
-    key_main = prec + (f"@tau{args.tau_iters}" if args.tau_iters else "")
+    key_main = prec + (f"@tau{args.tau_iters}" if args.tau_iters else "") + ("@tma" if args.staging == 2 else "")
     variants = {}
     for v in [p for p in args.variants.split(",") if p and p != key_main]:
         vs, vd = 2, args.variant_delta
-        vp, vl, vt = parse_variant(v)
-        tv, kv, _, nuv = time_ours(lbm, torch, N, vp, vs, 1, vd, stream, layout=vl, tau_iters=vt)
+        vp, vl, vt, vg = parse_variant(v)
+        tv, kv, _, nuv = time_ours(lbm, torch, N, vp, vs, 1, vd, stream, layout=vl, tau_iters=vt, staging=vg)
         bpn = bytes_per_node(vp, vt)
         av = bpn * N * N / kv / 1e9
         variants[v] = {"MLUPS": N * N * vd * vs / tv / 1e6, "kernel_MLUPS": N * N / kv / 1e6,
@@ -605,6 +611,7 @@ def main():
                        "bytes_per_node": bpn, "achieved_GBs": av, "frac_of_hbm": av / peak,
                        "layout": "aa (in place)" if vl else "ab (two buffers)",
                        "tau": f"implicit, {vt} Newton steps" if vt else "lagged (stored)",
+                       "staging": {0: "auto", 1: "registers", 2: "bulk copies to shared memory"}[vg],
                        "nu_hot": nuv}
         if v == "f64":
             ipn = recorded("f64_fp64_inst_per_node")
@@ -640,7 +647,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(key_main, N),
                      "peak_source": peak_src,
-                     "kernel": f"{'step_kernel' if prec == 'f64' else 'step2_kernel'}<{key_main}>",
+                     "kernel": ("step_kernel" if prec == "f64" else "step_tma_kernel" if args.staging == 2
+                                else "step2_kernel") + f"<{key_main}>",
                      "bytes_per_node": bpn_main, "avg_launch_us": kern * 1e6},
         "cpu_baseline": cpu,
         "e2e": e2e,

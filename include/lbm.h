@@ -40,7 +40,8 @@ enum {
     LBM_ERR_NONFINITE = -3, /* NaN or Inf found in the fields              */
     LBM_ERR_CUDA = -4,      /* a CUDA runtime call failed                  */
     LBM_ERR_OOM = -5,       /* device memory allocation failed             */
-    LBM_ERR_TIMEOUT = -6,   /* a bounded device wait gave up               */
+    LBM_ERR_TIMEOUT = -6,   /* a bounded device wait gave up (sticky: the
+                               run's state is no longer valid)        */
     LBM_ERR_UNSUPPORTED = -7,/* option combination not built              */
     LBM_ERR_SIZE = -8       /* grid larger than a fixed-size scratch area  */
 };
@@ -95,6 +96,13 @@ typedef struct {
                           reach FP32 rounding, 4 FP64 rounding on
                           developed flows.  Not built with the batch
                           API or the adjoint                         [0]    */
+    int staging;       /* how the step kernel of the two-buffer layout
+                          gets its inputs: 1 straight into registers;
+                          2 staged in shared memory by bulk
+                          asynchronous copies, a tile ahead (FP32,
+                          FP32D, BF16D, F16D; LBM_ERR_UNSUPPORTED for
+                          F64); 0 the faster of the two for the
+                          storage and tau scheme                     [0]    */
 } lbm_opts;
 
 /* Lattice-unit parameters the library derived from the problem groups

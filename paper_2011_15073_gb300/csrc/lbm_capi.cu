@@ -48,8 +48,10 @@ int map_lattice(int nx, int ny, double n, double Da, double Ra, double Pr, doubl
     if (o.prec < LBM_F64 || o.prec > LBM_F32D || !(o.Ma > 0) || o.Ma > 1 ||
         (o.clamp_mode != 0 && o.clamp_mode != 1) || (o.porous_model != 0 && o.porous_model != 1) ||
         !(o.s_e > 0) || !(o.s_e < 2) || !(o.s_p > 0) || !(o.s_p < 2) || o.resid_interval < 1 ||
-        o.device < -1 || o.tau_iters < 0 || o.tau_iters > LBM_TAU_ITERS_MAX)
+        o.device < -1 || o.tau_iters < 0 || o.tau_iters > LBM_TAU_ITERS_MAX || o.staging < 0 ||
+        o.staging > 2)
         return LBM_ERR_ARG;
+    if (o.staging == 2 && o.prec == LBM_F64) return LBM_ERR_UNSUPPORTED;
     if (o.layout != 0 && o.layout != 1) return LBM_ERR_UNSUPPORTED;
     memset(L, 0, sizeof(*L));
     const double Uc = o.Ma / sqrt(3.0);
@@ -96,6 +98,8 @@ void free_ctx(lbm_ctx *c)
     cudaFree(c->d_part);
     cudaFree(c->d_nuloc);
     cudaFree(c->d_da);
+    cudaFree(c->d_err);
+    cudaFreeHost(c->h_err);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -124,6 +128,14 @@ double stag_floor(const lbm_ctx *c)
 // Copy the 14 distribution planes between host (canonical order, unpadded)
 // and device.  In the in-place layout's canonical form population i of a
 // node lives in plane opp(i).
+// The error word raised by a kernel whose bounded wait gave up: queue its
+// read-back before a stream synchronisation, then report it after.
+cudaError_t read_err(lbm_ctx *c)
+{
+    return cudaMemcpyAsync(c->h_err, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+}
+int err_status(const lbm_ctx *c) { return *c->h_err ? LBM_ERR_TIMEOUT : LBM_OK; }
+
 int copy_planes(lbm_ctx *c, void *host, bool to_host)
 {
     const size_t es = c->dist_elem, n = (size_t)c->nx * c->ny;
@@ -186,6 +198,10 @@ int init_ctx(lbm_ctx *c)
     }
     CK(cudaMalloc(&c->d_small, sizeof(double) * 16));
     CK(cudaMallocHost(&c->h_small, sizeof(double) * 16));
+    CK(cudaMalloc(&c->d_err, sizeof(unsigned)));
+    CK(cudaMallocHost(&c->h_err, sizeof(unsigned)));
+    *c->h_err = 0;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
     CK(cudaMalloc(&c->d_nuloc, sizeof(double) * (size_t)c->ny));
     c->n_part = lbm::residual_blocks(c);
     CK(cudaMalloc(&c->d_part, sizeof(double) * 8 * (size_t)c->n_part));
@@ -215,6 +231,7 @@ void lbm_default_opts(lbm_opts *o)
     o->device = -1;
     o->stag_floor = -1.0;
     o->tau_iters = 0;
+    o->staging = 0;
 }
 
 int lbm_init(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra, double Pr,
@@ -308,8 +325,9 @@ int lbm_synchronize(lbm_ctx *c)
 {
     if (!c) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
+    CK(read_err(c));
     CK(cudaStreamSynchronize(c->stream));
-    return LBM_OK;
+    return err_status(c);
 }
 
 int lbm_fields(lbm_ctx *c, double *rho, double *ux, double *uy, double *T, double *nu)
@@ -326,8 +344,9 @@ int lbm_fields(lbm_ctx *c, double *rho, double *ux, double *uy, double *T, doubl
         if (outs[i])
             CK(cudaMemcpyAsync(outs[i], c->d_stage + i * n, sizeof(double) * n, cudaMemcpyDeviceToHost,
                                c->stream));
+    CK(read_err(c));
     CK(cudaStreamSynchronize(c->stream));
-    return LBM_OK;
+    return err_status(c);
 }
 
 int lbm_nusselt(lbm_ctx *c, double *hot, double *cold, double *local)
@@ -339,10 +358,11 @@ int lbm_nusselt(lbm_ctx *c, double *hot, double *cold, double *local)
     CK(cudaMemcpyAsync(c->h_small, c->d_small, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
     if (local)
         CK(cudaMemcpyAsync(local, c->d_nuloc, sizeof(double) * c->ny, cudaMemcpyDeviceToHost, c->stream));
+    CK(read_err(c));
     CK(cudaStreamSynchronize(c->stream));
     if (hot) *hot = c->h_small[0];
     if (cold) *cold = c->h_small[1];
-    return LBM_OK;
+    return err_status(c);
 }
 
 int lbm_residual(lbm_ctx *c, double *resid)
@@ -355,7 +375,9 @@ int lbm_residual(lbm_ctx *c, double *resid)
     CK(lbm::launch_residual(c, first));
     CK(cudaMemcpyAsync(c->h_small + 2, c->d_small + 2, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                        c->stream));
+    CK(read_err(c));
     CK(cudaStreamSynchronize(c->stream));
+    if (int rc1 = err_status(c)) return rc1;
     c->have_snap = true;
     double r = c->h_small[2];
     if (c->h_small[3] > r) r = c->h_small[3];

@@ -291,9 +291,19 @@ static cudaError_t step_buffers_tau(lbm_ctx *c, const void *src, void *dst, cons
     return cudaGetLastError();
 }
 
+// Inputs staged by bulk copies (lbm_tma.cu) or loaded straight into
+// registers: staging 2 / 1, and 0 picks per storage and tau scheme.
+static bool staged(const lbm_ctx *c)
+{
+    if (c->opts.prec == LBM_F64) return false;
+    if (c->opts.staging != 0) return c->opts.staging == 2;
+    return false;
+}
+
 template <int PREC>
 static cudaError_t step_buffers_t(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
 {
+    if (staged(c)) return launch_step_tma(c, src, dst, tsrc, tdst);
     return c->opts.tau_iters > 0 ? step_buffers_tau<PREC, 1>(c, src, dst, tsrc, tdst)
                                  : step_buffers_tau<PREC, 0>(c, src, dst, tsrc, tdst);
 }

@@ -1,0 +1,264 @@
+// lbm_tma.cu -- the fused pull-scheme step with its inputs staged in shared
+// memory by bulk asynchronous copies (the Tensor Memory Accelerator's
+// cp.async.bulk, completion tracked by an mbarrier), for the storages computed
+// in FP32 (FP32, FP32-deviation, BF16- and FP16-deviation).
+//
+// Work unit: a tile of 256 nodes of one row.  A persistent grid walks the
+// tiles; each 128-thread block keeps two tile stages in shared memory, and
+// while it computes one tile the copy engine fetches the next, so the DRAM
+// latency is hidden by the copy pipeline rather than by resident warps.  Per
+// tile and population plane the block copies the row the plane is pulled
+// from (y - e_y) over the tile's columns plus a 16-byte halo on each side;
+// the lagged-tau variant also copies the tile's tau row.  The arithmetic is
+// the one of the register path (lbm_step.cuh): two nodes per thread on the
+// packed FP32x2 pipe, results stored straight to global memory.  Warps that
+// touch a wall or the ragged end of a row, and the top and bottom rows, run
+// the per-node path with the wall rules from global memory, as there.
+//
+// Every wait on an mbarrier is bounded; a block that gives up raises the
+// context's error word (reported as LBM_ERR_TIMEOUT), waits a bounded time
+// for its copies in flight, and returns.
+#include <stdint.h>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+#include "lbm_step.cuh"
+
+namespace lbm {
+
+constexpr int TMA_TILE = 256;      // nodes per tile
+constexpr uint32_t TMA_SPIN = 1u << 20;  // mbarrier polls before giving up
+
+template <int PREC>
+struct TmaGeom {
+    using S = typename Store<PREC>::S;
+    static constexpr int HALO = 16 / (int)sizeof(S);       // elements in 16 bytes
+    static constexpr int W = TMA_TILE + 2 * HALO;          // elements per staged row
+    static constexpr int ROW_BYTES = W * (int)sizeof(S);   // a multiple of 16
+    // shared bytes of one stage: 14 population rows, then the tau row
+    static constexpr int stage_bytes(int tau) { return 14 * ROW_BYTES + (tau ? 0 : TMA_TILE * 4); }
+};
+
+// Row each plane is pulled from, relative to the tile's row: f_i(x) comes
+// from x - e_i.  Order f0..f8, g0..g4.
+__device__ __forceinline__ int pull_dy(int q)
+{
+    // e_y of f0..f8 = 0,0,1,0,-1,1,1,-1,-1 and of g0..g4 = 0,0,1,0,-1
+    constexpr int EY[14] = {0, 0, 1, 0, -1, 1, 1, -1, -1, 0, 0, 1, 0, -1};
+    return -EY[q];
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < TMA_SPIN; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// Global -> shared bulk copy of `bytes` (multiple of 16, both addresses
+// 16-byte aligned), completing `bytes` transactions on bar.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Issue the copies of tile t into one stage (thread 0 only).  Top and bottom
+// rows copy nothing: their nodes take the per-node path.
+template <int PREC, int TAU>
+__device__ __forceinline__ void tma_issue(const typename Store<PREC>::S *src, const float *tsrc,
+                                          const Phys<float> &p, int tiles_x, int64_t t, unsigned char *stage,
+                                          uint64_t *bar)
+{
+    using G = TmaGeom<PREC>;
+    using S = typename Store<PREC>::S;
+    const int y = (int)(t / tiles_x);
+    const int x0 = (int)(t - (int64_t)y * tiles_x) * TMA_TILE;
+    if (y < 1 || y > p.ny - 2) {
+        mbar_arrive_expect_tx(bar, 0);
+        return;
+    }
+    const int cs = x0 - G::HALO > 0 ? x0 - G::HALO : 0;
+    const int ce = x0 + TMA_TILE + G::HALO < p.pitch ? x0 + TMA_TILE + G::HALO : (int)p.pitch;
+    const uint32_t row_bytes = (uint32_t)(ce - cs) * (uint32_t)sizeof(S);
+    const int t_end = x0 + TMA_TILE < p.pitch ? x0 + TMA_TILE : (int)p.pitch;
+    const uint32_t tau_bytes = TAU ? 0u : (uint32_t)(t_end - x0) * 4u;
+    mbar_arrive_expect_tx(bar, 14u * row_bytes + tau_bytes);
+    const int off = cs - (x0 - G::HALO);   // 0, or HALO at the left end of a row
+#pragma unroll 1
+    for (int q = 0; q < 14; ++q) {
+        const S *row = src + (int64_t)q * p.plane + (int64_t)(y + pull_dy(q)) * p.pitch + cs;
+        bulk_g2s(stage + q * G::ROW_BYTES + off * (int)sizeof(S), row, row_bytes, bar);
+    }
+    if (!TAU) bulk_g2s(stage + 14 * G::ROW_BYTES, tsrc + (int64_t)y * p.pitch + x0, tau_bytes, bar);
+}
+
+// Fast-path body: the warp's 64 nodes and their neighbours are interior.
+// j: staged index of the thread's first node.
+template <int PREC, int FIELD, int TAU>
+__device__ __forceinline__ void tma_tile_fast(const unsigned char *stage, typename Store<PREC>::S *__restrict__ dst,
+                                              float *__restrict__ tdst, const Phys<F2> &p2, int64_t k, int j)
+{
+    using St = Store<PREC>;
+    using G = TmaGeom<PREC>;
+    using S = typename St::S;
+    const S *r[14];
+#pragma unroll
+    for (int q = 0; q < 14; ++q) r[q] = reinterpret_cast<const S *>(stage + q * G::ROW_BYTES);
+    auto pair_l = [&](int q, float rest) {   // nodes' left neighbours (x - 1, x)
+        return F2(St::ld(r[q], j - 1, rest), St::ld(r[q], j, rest));
+    };
+    auto pair_r = [&](int q, float rest) {   // right neighbours (x + 1, x + 2)
+        return F2(St::ld(r[q], j + 1, rest), St::ld(r[q], j + 2, rest));
+    };
+    F2 f[9], g[5];
+    f[0] = St::ld2(r[0], j, float(rest_f(0)));
+    f[1] = pair_l(1, float(rest_f(1)));
+    f[2] = St::ld2(r[2], j, float(rest_f(2)));
+    f[3] = pair_r(3, float(rest_f(3)));
+    f[4] = St::ld2(r[4], j, float(rest_f(4)));
+    f[5] = pair_l(5, float(rest_f(5)));
+    f[6] = pair_r(6, float(rest_f(6)));
+    f[7] = pair_r(7, float(rest_f(7)));
+    f[8] = pair_l(8, float(rest_f(8)));
+    g[0] = St::ld2(r[9], j, float(rest_g(0)));
+    g[1] = pair_l(10, float(rest_g(1)));
+    g[2] = St::ld2(r[11], j, float(rest_g(2)));
+    g[3] = pair_r(12, float(rest_g(3)));
+    g[4] = St::ld2(r[13], j, float(rest_g(4)));
+    const float *trow = reinterpret_cast<const float *>(stage + 14 * G::ROW_BYTES);
+    const F2 t0 = tau_start<TAU, F2, FIELD>(p2, f, g, k, [&] {
+        return F2(*reinterpret_cast<const float2 *>(trow + (j - G::HALO)));
+    });
+    Macro<F2> m;
+    const F2 tau = collide<F2, FIELD>(p2, f, g, t0, m, k);
+    const int64_t P = p2.plane;
+#pragma unroll
+    for (int i = 0; i < 9; i++) St::st2(dst + i * P, k, f[i], float(rest_f(i)));
+#pragma unroll
+    for (int i = 0; i < 5; i++) St::st2(dst + (9 + i) * P, k, g[i], float(rest_g(i)));
+    if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tdst + k) = tau.v;
+}
+
+template <int PREC, int FIELD, int TAU>
+__global__ void __launch_bounds__(128)
+step_tma_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
+                const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2, int tiles_x,
+                int64_t ntiles, unsigned *err)
+{
+    using G = TmaGeom<PREC>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[2];
+    constexpr int SB = G::stage_bytes(TAU);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int64_t t = blockIdx.x;
+    if (tid == 0 && t < ntiles) tma_issue<PREC, TAU>(src, tsrc, p, tiles_x, t, smem, &full[0]);
+    for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
+        const int s = it & 1;
+        const uint32_t parity = (it >> 1) & 1;
+        const int64_t tn = t + gridDim.x;
+        // stage s ^ 1 was released by the barrier that ended the previous tile
+        if (tid == 0 && tn < ntiles) tma_issue<PREC, TAU>(src, tsrc, p, tiles_x, tn, smem + (s ^ 1) * SB, &full[s ^ 1]);
+        const bool ok = mbar_wait_bounded(&full[s], parity);
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) {
+                atomicExch(err, 1u);
+                // let the copies in flight land before the block's shared memory goes
+                mbar_wait_bounded(&full[s], parity);
+                if (tn < ntiles) mbar_wait_bounded(&full[s ^ 1], ((it + 1) >> 1) & 1);
+            }
+            return;
+        }
+        const int y = (int)(t / tiles_x);
+        const int x0 = (int)(t - (int64_t)y * tiles_x) * TMA_TILE;
+        const int xn = x0 + 2 * tid;
+        const int wx = x0 + 2 * (tid & ~31);
+        const bool fast = y > 0 && y < p.ny - 1 && wx > 0 && wx + 64 < p.nx;
+        if (fast) {
+            tma_tile_fast<PREC, FIELD, TAU>(smem + s * SB, dst, tdst, p2, (int64_t)y * p.pitch + xn,
+                                            2 * tid + G::HALO);
+        } else {
+            for (int jn = 0; jn < 2; jn++)
+                if (xn + jn < p.nx) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, xn + jn, y);
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------- launcher
+template <int PREC, int FIELD, int TAU>
+static cudaError_t tma_launch_t(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
+{
+    using St = Store<PREC>;
+    auto *kern = step_tma_kernel<PREC, FIELD, TAU>;
+    const int sb = 2 * TmaGeom<PREC>::stage_bytes(TAU);
+    const int tiles_x = (c->nx + TMA_TILE - 1) / TMA_TILE;
+    const int64_t ntiles = (int64_t)tiles_x * c->ny;
+    int per_sm = 0, nsm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, sb);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)nsm * per_sm;
+    if (grid > ntiles) grid = ntiles;
+    kern<<<(unsigned)grid, 128, sb, c->stream>>>((const typename St::S *)src, (typename St::S *)dst,
+                                                 (const float *)tsrc, (float *)tdst, make_params<float>(c),
+                                                 make_params<F2>(c), tiles_x, ntiles, c->d_err);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t tma_dispatch(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
+{
+    const bool field = c->d_da != nullptr, tau = c->opts.tau_iters > 0;
+    if (field)
+        return tau ? tma_launch_t<PREC, 1, 1>(c, src, dst, tsrc, tdst) : tma_launch_t<PREC, 1, 0>(c, src, dst, tsrc, tdst);
+    return tau ? tma_launch_t<PREC, 0, 1>(c, src, dst, tsrc, tdst) : tma_launch_t<PREC, 0, 0>(c, src, dst, tsrc, tdst);
+}
+
+cudaError_t launch_step_tma(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
+{
+    switch (c->opts.prec) {
+    case LBM_F32: return tma_dispatch<LBM_F32>(c, src, dst, tsrc, tdst);
+    case LBM_F32D: return tma_dispatch<LBM_F32D>(c, src, dst, tsrc, tdst);
+    case LBM_BF16D: return tma_dispatch<LBM_BF16D>(c, src, dst, tsrc, tdst);
+    case LBM_F16D: return tma_dispatch<LBM_F16D>(c, src, dst, tsrc, tdst);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace lbm

@@ -33,10 +33,11 @@ def test_bench_defines_every_leg():
 
 def test_variant_names():
     import bench
-    assert bench.parse_variant("f32") == ("f32", 0, 0)
-    assert bench.parse_variant("f32@aa") == ("f32", 1, 0)
-    assert bench.parse_variant("f32@tau2") == ("f32", 0, 2)
-    assert bench.parse_variant("f32d@aa@tau3") == ("f32d", 1, 3)
+    assert bench.parse_variant("f32") == ("f32", 0, 0, 0)
+    assert bench.parse_variant("f32@aa") == ("f32", 1, 0, 0)
+    assert bench.parse_variant("f32@tau2") == ("f32", 0, 2, 0)
+    assert bench.parse_variant("f32d@aa@tau3") == ("f32d", 1, 3, 0)
+    assert bench.parse_variant("bf16d@tau2@tma") == ("bf16d", 0, 2, 2)
     assert bench.bytes_per_node("f32", 2) == 112 and bench.bytes_per_node("f64", 1) == 224
     with pytest.raises(ValueError):
         bench.parse_variant("f32@bogus")

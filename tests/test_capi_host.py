@@ -49,7 +49,7 @@ def test_default_opts(L):
     assert (o.prec, o.Ma, o.clamp_mode, o.porous_model, o.s_e, o.s_p, o.resid_interval, o.layout) == \
         (0, 0.1, 0, 1, 1.5, 1.5, 1000, 0)
     assert not o.cuda_stream and o.device == -1 and o.stag_floor == -1.0
-    assert o.tau_iters == 0
+    assert o.tau_iters == 0 and o.staging == 0
 
 
 @pytest.mark.parametrize("args,code", [
@@ -75,7 +75,8 @@ def test_init_rejects_bad_arguments(L, args, code):
 @pytest.mark.parametrize("field,value,code", [
     ("prec", 5, -1), ("Ma", 0.0, -1), ("clamp_mode", 2, -1), ("porous_model", 3, -1),
     ("s_e", 2.5, -1), ("s_p", 0.0, -1), ("resid_interval", 0, -1), ("layout", 2, -7),
-    ("device", -2, -1), ("tau_iters", -1, -1), ("tau_iters", 17, -1),
+    ("device", -2, -1), ("tau_iters", -1, -1), ("tau_iters", 17, -1), ("staging", 3, -1),
+    ("staging", -1, -1), ("staging", 2, -7),   # the default storage is F64: no staged kernel
 ])
 def test_init_rejects_bad_options(L, field, value, code):
     from paper_2011_15073_gb300 import lbm
