@@ -4,9 +4,10 @@
 // in FP32 (FP32, FP32-deviation, BF16- and FP16-deviation).
 //
 // Work unit: a tile of 256 nodes of one row.  A persistent grid walks the
-// tiles; each 128-thread block keeps two tile stages in shared memory, and
-// while it computes one tile the copy engine fetches the next, so the DRAM
-// latency is hidden by the copy pipeline rather than by resident warps.  Per
+// tiles; each block keeps 3 (FP32) or 4 (16-bit) tile stages in shared
+// memory, and while its four consumer warps compute one tile a producer warp
+// has the copy engine fetch the next ones, so the DRAM latency is hidden by
+// the copy pipeline rather than by resident warps.  Per
 // tile and population plane the block copies the row the plane is pulled
 // from (y - e_y) over the tile's columns plus a 16-byte halo on each side;
 // the lagged-tau variant also copies the tile's tau row.  The arithmetic is
@@ -37,15 +38,22 @@ struct TmaGeom {
     static constexpr int ROW_BYTES = W * (int)sizeof(S);   // a multiple of 16
     // shared bytes of one stage: 14 population rows, then the tau row
     static constexpr int stage_bytes(int tau) { return 14 * ROW_BYTES + (tau ? 0 : TMA_TILE * 4); }
+    // tiles in flight per block: 3 x 15.8 KB (FP32) or 4 x 8.6 KB (16-bit),
+    // inside the 48 KB a block gets without opting in
+    static constexpr int STAGES = sizeof(S) == 4 ? 3 : 4;
+    // blocks per SM the shared memory allows; registers are capped to match
+    static constexpr int MIN_BLOCKS = sizeof(S) == 4 ? 4 : 5;
 };
 
 // Row each plane is pulled from, relative to the tile's row: f_i(x) comes
 // from x - e_i.  Order f0..f8, g0..g4.
 __device__ __forceinline__ int pull_dy(int q)
 {
-    // e_y of f0..f8 = 0,0,1,0,-1,1,1,-1,-1 and of g0..g4 = 0,0,1,0,-1
-    constexpr int EY[14] = {0, 0, 1, 0, -1, 1, 1, -1, -1, 0, 0, 1, 0, -1};
-    return -EY[q];
+    // e_y = +1 for f2, f5, f6, g2 (planes 2, 5, 6, 11), -1 for f4, f7, f8, g4
+    // (planes 4, 7, 8, 13), 0 otherwise
+    constexpr unsigned UP = (1u << 2) | (1u << 5) | (1u << 6) | (1u << 11);
+    constexpr unsigned DOWN = (1u << 4) | (1u << 7) | (1u << 8) | (1u << 13);
+    return (int)((DOWN >> q) & 1u) - (int)((UP >> q) & 1u);
 }
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p)
@@ -60,6 +68,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
@@ -167,54 +179,72 @@ __device__ __forceinline__ void tma_tile_fast(const unsigned char *stage, typena
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tdst + k) = tau.v;
 }
 
+// Block = 4 consumer warps (64 nodes of the tile each) + 1 producer warp
+// whose lane 0 issues the copies, up to STAGES - 1 tiles ahead.  Stage s has
+// two barriers: full[s] completes when the tile's bytes have landed; empty[s]
+// when the 4 consumer warps are done reading it.
 template <int PREC, int FIELD, int TAU>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(160, TmaGeom<PREC>::MIN_BLOCKS)
 step_tma_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
                 const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2, int tiles_x,
                 int64_t ntiles, unsigned *err)
 {
     using G = TmaGeom<PREC>;
+    constexpr int NS = G::STAGES;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t full[2];
+    __shared__ __align__(8) uint64_t full[NS], empty[NS];
     constexpr int SB = G::stage_bytes(TAU);
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    int64_t t = blockIdx.x;
-    if (tid == 0 && t < ntiles) tma_issue<PREC, TAU>(src, tsrc, p, tiles_x, t, smem, &full[0]);
-    for (uint32_t it = 0; t < ntiles; t += gridDim.x, ++it) {
-        const int s = it & 1;
-        const uint32_t parity = (it >> 1) & 1;
-        const int64_t tn = t + gridDim.x;
-        // stage s ^ 1 was released by the barrier that ended the previous tile
-        if (tid == 0 && tn < ntiles) tma_issue<PREC, TAU>(src, tsrc, p, tiles_x, tn, smem + (s ^ 1) * SB, &full[s ^ 1]);
-        const bool ok = mbar_wait_bounded(&full[s], parity);
-        if (!__syncthreads_and(ok)) {
-            if (tid == 0) {
-                atomicExch(err, 1u);
-                // let the copies in flight land before the block's shared memory goes
-                mbar_wait_bounded(&full[s], parity);
-                if (tn < ntiles) mbar_wait_bounded(&full[s ^ 1], ((it + 1) >> 1) & 1);
+    if (warp == 4) {   // producer
+        if (lane != 0) return;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+            const int s = it % NS;
+            const uint32_t round = it / NS;
+            if (round > 0 && !mbar_wait_bounded(&empty[s], (round - 1) & 1)) {
+                ok = false;
+                break;
             }
+            tma_issue<PREC, TAU>(src, tsrc, p, tiles_x, t, smem + s * SB, &full[s]);
+        }
+        if (!ok) {   // let the copies already issued land before the block's shared memory goes
+            atomicExch(err, 1u);
+            for (uint32_t j = it > (uint32_t)NS ? it - NS : 0; j < it; ++j)
+                mbar_wait_bounded(&full[j % NS], (j / NS) & 1);
+        }
+        return;
+    }
+    uint32_t it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int s = it % NS;
+        const bool ok = mbar_wait_bounded(&full[s], (it / NS) & 1);
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicExch(err, 1u);
             return;
         }
         const int y = (int)(t / tiles_x);
         const int x0 = (int)(t - (int64_t)y * tiles_x) * TMA_TILE;
-        const int xn = x0 + 2 * tid;
-        const int wx = x0 + 2 * (tid & ~31);
+        const int xn = x0 + 2 * (int)threadIdx.x;
+        const int wx = x0 + 64 * warp;
         const bool fast = y > 0 && y < p.ny - 1 && wx > 0 && wx + 64 < p.nx;
         if (fast) {
             tma_tile_fast<PREC, FIELD, TAU>(smem + s * SB, dst, tdst, p2, (int64_t)y * p.pitch + xn,
-                                            2 * tid + G::HALO);
+                                            2 * (int)threadIdx.x + G::HALO);
         } else {
             for (int jn = 0; jn < 2; jn++)
                 if (xn + jn < p.nx) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, xn + jn, y);
         }
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
     }
 }
 
@@ -224,18 +254,18 @@ static cudaError_t tma_launch_t(lbm_ctx *c, const void *src, void *dst, const vo
 {
     using St = Store<PREC>;
     auto *kern = step_tma_kernel<PREC, FIELD, TAU>;
-    const int sb = 2 * TmaGeom<PREC>::stage_bytes(TAU);
+    const int sb = TmaGeom<PREC>::STAGES * TmaGeom<PREC>::stage_bytes(TAU);
     const int tiles_x = (c->nx + TMA_TILE - 1) / TMA_TILE;
     const int64_t ntiles = (int64_t)tiles_x * c->ny;
     int per_sm = 0, nsm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, sb);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 160, sb);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)nsm * per_sm;
     if (grid > ntiles) grid = ntiles;
-    kern<<<(unsigned)grid, 128, sb, c->stream>>>((const typename St::S *)src, (typename St::S *)dst,
+    kern<<<(unsigned)grid, 160, sb, c->stream>>>((const typename St::S *)src, (typename St::S *)dst,
                                                  (const float *)tsrc, (float *)tdst, make_params<float>(c),
                                                  make_params<F2>(c), tiles_x, ntiles, c->d_err);
     return cudaGetLastError();
