@@ -31,10 +31,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_NODE = {"f64": 240, "f32": 120, "f32d": 120, "bf16d": 64, "f16d": 64}
+BYTES_PER_NODE = {"f64": 240, "f32": 120, "f32d": 120, "bf16d": 64, "f16d": 64, "f16s": 64, "bf16s": 64}
 # bytes of the stored lagged tau in those figures (read + write); the
 # node-local implicit tau (tau_iters > 0) moves none
-TAU_BYTES = {"f64": 16, "f32": 8, "f32d": 8, "bf16d": 8, "f16d": 8}
+TAU_BYTES = {"f64": 16, "f32": 8, "f32d": 8, "bf16d": 8, "f16d": 8, "f16s": 8, "bf16s": 8}
 
 
 def parse_variant(v):
@@ -114,8 +114,7 @@ def parse():
                     help="step-kernel inputs: 0 auto, 1 straight to registers, 2 bulk copies to shared memory")
     ap.add_argument("--tau-iters", type=int, default=0,
                     help="0: lagged tau (stored per node); K > 0: node-local implicit tau, K Newton steps")
-    ap.add_argument("--variants", default="f64,f32d,f32@aa,f32@tau2,f32@tma,f32@tau2@tma,bf16d,bf16d@tma,"
-                                          "f16d,f16d@tma",
+    ap.add_argument("--variants", default=DEFAULT_VARIANTS,
                     help="other storage precisions measured beside the headline ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -394,41 +393,59 @@ def study_tables(args):
                           "seconds": time.perf_counter() - t}), flush=True)
 
 
+DEFAULT_VARIANTS = "f64,f32d,f32@aa,f32@tau2,f32@tma,bf16d,f16d,f16s,bf16s,f16s@tau2"
+PRECISION_VARIANTS = ("f64", "f64@tau4", "f32", "f32@tau2", "f32d", "f16d", "bf16d", "f16s", "bf16s")
+
+
 def study_precision(args):
-    """FP32 and 16-bit deviation storage against FP64 storage at the FP64 steady
-    state: the FP64 run goes to a residual of 1e-10 in S steps (continuous
-    power law, so the steady state is unique), every other storage then runs
-    the same S steps from the same rest state; reported are the relative L2
-    errors of u_x, u_y, T and the relative hot-wall Nu difference."""
+    """Storage formats and tau schemes against FP64 storage (lagged tau) at
+    the FP64 steady state: the FP64 run goes to a residual of 1e-10 in S steps
+    (continuous power law, so the steady state is unique); every other
+    variant then runs the same S steps from the same rest state, sampling the
+    hot-wall Nu every 1000 steps over the last 20,000 (stochastic rounding
+    leaves a noise of its own on any one snapshot).  Reported: the relative
+    L2 errors of u_x, u_y, T at the end, the relative Nu difference at the end
+    and of the mean of the samples."""
     import numpy as np
     from paper_2011_15073_gb300 import lbm
     N = args.study_N or 512
+    variants = [v for v in (args.variants.split(",") if args.variants != DEFAULT_VARIANTS else PRECISION_VARIANTS)
+                if v]
     for n in (0.6, 1.0):
         case = dict(n=n, Da=1e-2, Ra=1e5, Pr=6.2, porosity=0.6)
         res = {}
         S = None
-        for prec in ("f64", "f32", "f32d", "f16d", "bf16d"):
+        for v in ["f64"] + [x for x in variants if x != "f64"]:
+            prec, layout, tau_iters, staging = parse_variant(v)
             t = time.perf_counter()
-            with lbm.Cavity(N, N, prec=prec, resid_interval=1000, clamp_mode=1, **case) as cav:
-                if prec == "f64":
+            with lbm.Cavity(N, N, prec=prec, resid_interval=1000, clamp_mode=1, layout=layout, tau_iters=tau_iters,
+                            staging=staging, **case) as cav:
+                samples = []
+                if v == "f64":
                     S, resid, why = cav.run_to_steady(1e-10, args.study_max_steps)
                     stop = ["tol", "stagnated", "max_steps"][why]
+                    samples.append(cav.nusselt()[0])
                 else:
-                    cav.step(S - 1000)
+                    tail = min(20, S // 1000 - 1)
+                    cav.step(S - 1000 * tail)
                     cav.residual()
-                    cav.step(1000)
+                    for _ in range(tail):
+                        cav.step(1000)
+                        samples.append(cav.nusselt()[0])
                     resid, stop = cav.residual(), "same_steps"
                 hot, cold, _ = cav.nusselt()
                 fl = cav.fields()
-            res[prec] = dict(nu=hot, nu_cold=cold, fl=fl, steps=S, resid=resid, stop=stop,
-                             sec=time.perf_counter() - t)
+            res[v] = dict(nu=hot, nu_cold=cold, nu_mean=float(np.mean(samples)), nu_std=float(np.std(samples)),
+                          fl=fl, steps=S, resid=resid, stop=stop, sec=time.perf_counter() - t)
         ref = res["f64"]
-        for prec, r in res.items():
+        for v, r in res.items():
             err = {k: float(np.linalg.norm(r["fl"][k] - ref["fl"][k]) / np.linalg.norm(ref["fl"][k]))
                    for k in ("ux", "uy", "T")}
-            print(json.dumps({"study": "precision", "N": N, **case, "clamp_mode": 1, "prec": prec,
-                              "nu_hot": r["nu"], "nu_cold": r["nu_cold"],
-                              "dnu_rel": (r["nu"] - ref["nu"]) / ref["nu"], "l2_rel": err,
+            print(json.dumps({"study": "precision", "N": N, **case, "clamp_mode": 1, "variant": v,
+                              "nu_hot": r["nu"], "nu_cold": r["nu_cold"], "nu_hot_mean": r["nu_mean"],
+                              "nu_hot_std": r["nu_std"],
+                              "dnu_rel": (r["nu"] - ref["nu"]) / ref["nu"],
+                              "dnu_mean_rel": (r["nu_mean"] - ref["nu"]) / ref["nu"], "l2_rel": err,
                               "steps": r["steps"], "residual": r["resid"], "stop": r["stop"],
                               "seconds": r["sec"]}), flush=True)
 

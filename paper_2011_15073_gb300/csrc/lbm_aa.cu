@@ -32,21 +32,21 @@ __device__ __forceinline__ void push(typename Store<PREC>::S *__restrict__ A, co
     const int64_t k = (int64_t)y * W + x;
     const bool xl = x > 0, xr = x < p.nx - 1, yb = y > 0, yt = y < p.ny - 1;
     // target x + e_i: e1 (1,0) e2 (0,1) e3 (-1,0) e4 (0,-1) e5 (1,1) e6 (-1,1) e7 (-1,-1) e8 (1,-1)
-    St::st(A, 0 * P + k, f[0], R(rest_f(0)));
-    if (xr) St::st(A, 1 * P + k + 1, f[1], R(rest_f(1))); else St::st(A, 3 * P + k, f[1], R(rest_f(3)));
-    if (yt) St::st(A, 2 * P + k + W, f[2], R(rest_f(2))); else St::st(A, 4 * P + k, f[2], R(rest_f(4)));
-    if (xl) St::st(A, 3 * P + k - 1, f[3], R(rest_f(3))); else St::st(A, 1 * P + k, f[3], R(rest_f(1)));
-    if (yb) St::st(A, 4 * P + k - W, f[4], R(rest_f(4))); else St::st(A, 2 * P + k, f[4], R(rest_f(2)));
-    if (xr && yt) St::st(A, 5 * P + k + W + 1, f[5], R(rest_f(5))); else St::st(A, 7 * P + k, f[5], R(rest_f(7)));
-    if (xl && yt) St::st(A, 6 * P + k + W - 1, f[6], R(rest_f(6))); else St::st(A, 8 * P + k, f[6], R(rest_f(8)));
-    if (xl && yb) St::st(A, 7 * P + k - W - 1, f[7], R(rest_f(7))); else St::st(A, 5 * P + k, f[7], R(rest_f(5)));
-    if (xr && yb) St::st(A, 8 * P + k - W + 1, f[8], R(rest_f(8))); else St::st(A, 6 * P + k, f[8], R(rest_f(6)));
+    St::st(A, 0 * P + k, f[0], R(rest_f(0)), p.seed);
+    if (xr) St::st(A, 1 * P + k + 1, f[1], R(rest_f(1)), p.seed); else St::st(A, 3 * P + k, f[1], R(rest_f(3)), p.seed);
+    if (yt) St::st(A, 2 * P + k + W, f[2], R(rest_f(2)), p.seed); else St::st(A, 4 * P + k, f[2], R(rest_f(4)), p.seed);
+    if (xl) St::st(A, 3 * P + k - 1, f[3], R(rest_f(3)), p.seed); else St::st(A, 1 * P + k, f[3], R(rest_f(1)), p.seed);
+    if (yb) St::st(A, 4 * P + k - W, f[4], R(rest_f(4)), p.seed); else St::st(A, 2 * P + k, f[4], R(rest_f(2)), p.seed);
+    if (xr && yt) St::st(A, 5 * P + k + W + 1, f[5], R(rest_f(5)), p.seed); else St::st(A, 7 * P + k, f[5], R(rest_f(7)), p.seed);
+    if (xl && yt) St::st(A, 6 * P + k + W - 1, f[6], R(rest_f(6)), p.seed); else St::st(A, 8 * P + k, f[6], R(rest_f(8)), p.seed);
+    if (xl && yb) St::st(A, 7 * P + k - W - 1, f[7], R(rest_f(7)), p.seed); else St::st(A, 5 * P + k, f[7], R(rest_f(5)), p.seed);
+    if (xr && yb) St::st(A, 8 * P + k - W + 1, f[8], R(rest_f(8)), p.seed); else St::st(A, 6 * P + k, f[8], R(rest_f(6)), p.seed);
     typename Store<PREC>::S *G = A + 9 * P;
-    St::st(G, 0 * P + k, g[0], R(rest_g(0)));
-    if (xr) St::st(G, 1 * P + k + 1, g[1], R(rest_g(1))); else St::st(G, 3 * P + k, p.abb_cold - g[1], R(rest_g(3)));
-    if (yt) St::st(G, 2 * P + k + W, g[2], R(rest_g(2))); else St::st(G, 4 * P + k, g[2], R(rest_g(4)));
-    if (xl) St::st(G, 3 * P + k - 1, g[3], R(rest_g(3))); else St::st(G, 1 * P + k, p.abb_hot - g[3], R(rest_g(1)));
-    if (yb) St::st(G, 4 * P + k - W, g[4], R(rest_g(4))); else St::st(G, 2 * P + k, g[4], R(rest_g(2)));
+    St::st(G, 0 * P + k, g[0], R(rest_g(0)), p.seed);
+    if (xr) St::st(G, 1 * P + k + 1, g[1], R(rest_g(1)), p.seed); else St::st(G, 3 * P + k, p.abb_cold - g[1], R(rest_g(3)), p.seed);
+    if (yt) St::st(G, 2 * P + k + W, g[2], R(rest_g(2)), p.seed); else St::st(G, 4 * P + k, g[2], R(rest_g(4)), p.seed);
+    if (xl) St::st(G, 3 * P + k - 1, g[3], R(rest_g(3)), p.seed); else St::st(G, 1 * P + k, p.abb_hot - g[3], R(rest_g(1)), p.seed);
+    if (yb) St::st(G, 4 * P + k - W, g[4], R(rest_g(4)), p.seed); else St::st(G, 2 * P + k, g[4], R(rest_g(2)), p.seed);
 }
 
 // ------------------------------------------------------- one node / thread
@@ -68,9 +68,9 @@ aa_even_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::Ta
     Macro<R> m;
     const R t = collide<R>(p, f, g, tau_start<TAU, R, 2>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::st(A, opp(i) * P + k, f[i], R(rest_f(opp(i))));
+    for (int i = 0; i < 9; i++) St::st(A, opp(i) * P + k, f[i], R(rest_f(opp(i))), p.seed);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::st(A + 9 * P, opp(i) * P + k, g[i], R(rest_g(opp(i))));
+    for (int i = 0; i < 5; i++) St::st(A + 9 * P, opp(i) * P + k, g[i], R(rest_g(opp(i))), p.seed);
     if constexpr (TAU == 0) tau[k] = typename St::TauS(t);
 }
 
@@ -113,8 +113,8 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
         for (int i = 0; i < 5; i++) g[i] = St::ld(A + 9 * P, i * P + k, float(rest_g(i)));
         Macro<float> m;
         const float t = collide<float>(p, f, g, tau_start<TAU, float, 2>(p, f, g, k, [&] { return tau[k]; }), m, k);
-        for (int i = 0; i < 9; i++) St::st(A, opp(i) * P + k, f[i], float(rest_f(opp(i))));
-        for (int i = 0; i < 5; i++) St::st(A + 9 * P, opp(i) * P + k, g[i], float(rest_g(opp(i))));
+        for (int i = 0; i < 9; i++) St::st(A, opp(i) * P + k, f[i], float(rest_f(opp(i))), p.seed);
+        for (int i = 0; i < 5; i++) St::st(A + 9 * P, opp(i) * P + k, g[i], float(rest_g(opp(i))), p.seed);
         if constexpr (TAU == 0) tau[k] = t;
         return;
     }
@@ -127,9 +127,9 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
     const F2 t0 = tau_start<TAU, F2, 2>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
     const F2 t = collide<F2>(p2, f, g, t0, m, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::st2(A + opp(i) * P, k, f[i], float(rest_f(opp(i))));
+    for (int i = 0; i < 9; i++) St::st2(A + opp(i) * P, k, f[i], float(rest_f(opp(i))), p2.seed);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::st2(A + (9 + opp(i)) * P, k, g[i], float(rest_g(opp(i))));
+    for (int i = 0; i < 5; i++) St::st2(A + (9 + opp(i)) * P, k, g[i], float(rest_g(opp(i))), p2.seed);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tau + k) = t.v;
 }
 
@@ -138,22 +138,24 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
 // shuffle, and the lanes at the warp's ends store the element that belongs
 // to the neighbouring warp's pair on their own.
 template <int PREC>
-__device__ __forceinline__ void push_right(typename Store<PREC>::S *base, int64_t kr, F2 v, float rest, int lane)
+__device__ __forceinline__ void push_right(typename Store<PREC>::S *base, int64_t kr, F2 v, float rest, int lane,
+                                           uint32_t seed)
 {
     using St = Store<PREC>;
     const float prev = __shfl_up_sync(0xffffffffu, v.v.y, 1);
-    if (lane != 0) St::st2(base, kr, F2(prev, v.v.x), rest);
-    else St::st(base, kr + 1, v.v.x, rest);
-    if (lane == 31) St::st(base, kr + 2, v.v.y, rest);
+    if (lane != 0) St::st2(base, kr, F2(prev, v.v.x), rest, seed);
+    else St::st(base, kr + 1, v.v.x, rest, seed);
+    if (lane == 31) St::st(base, kr + 2, v.v.y, rest, seed);
 }
 template <int PREC>
-__device__ __forceinline__ void push_left(typename Store<PREC>::S *base, int64_t kr, F2 v, float rest, int lane)
+__device__ __forceinline__ void push_left(typename Store<PREC>::S *base, int64_t kr, F2 v, float rest, int lane,
+                                          uint32_t seed)
 {
     using St = Store<PREC>;
     const float next = __shfl_down_sync(0xffffffffu, v.v.x, 1);
-    if (lane != 31) St::st2(base, kr, F2(v.v.y, next), rest);
-    else St::st(base, kr, v.v.y, rest);
-    if (lane == 0) St::st(base, kr - 1, v.v.x, rest);
+    if (lane != 31) St::st2(base, kr, F2(v.v.y, next), rest, seed);
+    else St::st(base, kr, v.v.y, rest, seed);
+    if (lane == 0) St::st(base, kr - 1, v.v.x, rest, seed);
 }
 
 template <int PREC, int TAU>
@@ -200,20 +202,20 @@ aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau,
     const F2 t0 = tau_start<TAU, F2, 2>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
     const F2 t = collide<F2>(p2, f, g, t0, m, k);
     // push f*_i(x) into slot i of node x + e_i
-    St::st2(fs, k, f[0], float(rest_f(0)));
-    push_right<PREC>(fs + P, k, f[1], float(rest_f(1)), lane);
-    St::st2(fs + 2 * P, k + W, f[2], float(rest_f(2)));
-    push_left<PREC>(fs + 3 * P, k, f[3], float(rest_f(3)), lane);
-    St::st2(fs + 4 * P, k - W, f[4], float(rest_f(4)));
-    push_right<PREC>(fs + 5 * P, k + W, f[5], float(rest_f(5)), lane);
-    push_left<PREC>(fs + 6 * P, k + W, f[6], float(rest_f(6)), lane);
-    push_left<PREC>(fs + 7 * P, k - W, f[7], float(rest_f(7)), lane);
-    push_right<PREC>(fs + 8 * P, k - W, f[8], float(rest_f(8)), lane);
-    St::st2(gs, k, g[0], float(rest_g(0)));
-    push_right<PREC>(gs + P, k, g[1], float(rest_g(1)), lane);
-    St::st2(gs + 2 * P, k + W, g[2], float(rest_g(2)));
-    push_left<PREC>(gs + 3 * P, k, g[3], float(rest_g(3)), lane);
-    St::st2(gs + 4 * P, k - W, g[4], float(rest_g(4)));
+    St::st2(fs, k, f[0], float(rest_f(0)), p2.seed);
+    push_right<PREC>(fs + P, k, f[1], float(rest_f(1)), lane, p2.seed);
+    St::st2(fs + 2 * P, k + W, f[2], float(rest_f(2)), p2.seed);
+    push_left<PREC>(fs + 3 * P, k, f[3], float(rest_f(3)), lane, p2.seed);
+    St::st2(fs + 4 * P, k - W, f[4], float(rest_f(4)), p2.seed);
+    push_right<PREC>(fs + 5 * P, k + W, f[5], float(rest_f(5)), lane, p2.seed);
+    push_left<PREC>(fs + 6 * P, k + W, f[6], float(rest_f(6)), lane, p2.seed);
+    push_left<PREC>(fs + 7 * P, k - W, f[7], float(rest_f(7)), lane, p2.seed);
+    push_right<PREC>(fs + 8 * P, k - W, f[8], float(rest_f(8)), lane, p2.seed);
+    St::st2(gs, k, g[0], float(rest_g(0)), p2.seed);
+    push_right<PREC>(gs + P, k, g[1], float(rest_g(1)), lane, p2.seed);
+    St::st2(gs + 2 * P, k + W, g[2], float(rest_g(2)), p2.seed);
+    push_left<PREC>(gs + 3 * P, k, g[3], float(rest_g(3)), lane, p2.seed);
+    St::st2(gs + 4 * P, k - W, g[4], float(rest_g(4)), p2.seed);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tau + k) = t.v;
 }
 
@@ -305,6 +307,8 @@ static cudaError_t aa_normalize_t(lbm_ctx *c)
     case LBM_BF16D: return fn<LBM_BF16D>(__VA_ARGS__);             \
     case LBM_F16D: return fn<LBM_F16D>(__VA_ARGS__);               \
     case LBM_F32D: return fn<LBM_F32D>(__VA_ARGS__);               \
+    case LBM_F16S: return fn<LBM_F16S>(__VA_ARGS__);               \
+    case LBM_BF16S: return fn<LBM_BF16S>(__VA_ARGS__);             \
     default: return cudaErrorInvalidValue;                         \
     }
 

@@ -45,7 +45,7 @@ int map_lattice(int nx, int ny, double n, double Da, double Ra, double Pr, doubl
     if (nx < 2 || ny < 2 || ny > 65535 || nx > (1 << 30) || !(n > 0) || !(Da > 0) || !(Ra > 0) || !(Pr > 0) || !(porosity > 0) ||
         porosity > 1 || !isfinite(n) || !isfinite(Da) || !isfinite(Ra) || !isfinite(Pr))
         return LBM_ERR_ARG;
-    if (o.prec < LBM_F64 || o.prec > LBM_F32D || !(o.Ma > 0) || o.Ma > 1 ||
+    if (o.prec < LBM_F64 || o.prec > LBM_BF16S || !(o.Ma > 0) || o.Ma > 1 ||
         (o.clamp_mode != 0 && o.clamp_mode != 1) || (o.porous_model != 0 && o.porous_model != 1) ||
         !(o.s_e > 0) || !(o.s_e < 2) || !(o.s_p > 0) || !(o.s_p < 2) || o.resid_interval < 1 ||
         o.device < -1 || o.tau_iters < 0 || o.tau_iters > LBM_TAU_ITERS_MAX || o.staging < 0 ||
@@ -121,6 +121,8 @@ double stag_floor(const lbm_ctx *c)
     case LBM_F32:
     case LBM_F32D: return 1e-6;
     case LBM_F16D: return 1e-2;
+    case LBM_F16S: return 1e-3;
+    case LBM_BF16S: return 1e-2;
     default: return 1e-1;
     }
 }
@@ -316,8 +318,10 @@ int lbm_step(lbm_ctx *c, int64_t k)
 {
     if (!c || k < 0) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
-    for (int64_t t = 0; t < k; t++) CK(lbm::launch_step(c));
-    c->steps += k;
+    for (int64_t t = 0; t < k; t++) {
+        CK(lbm::launch_step(c));
+        c->steps++;   // also the stochastic rounding's step counter
+    }
     return LBM_OK;
 }
 

@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include "lbm_internal.h"
+#include "lbm_round.cuh"
 
 namespace lbm {
 
@@ -101,6 +102,8 @@ struct Phys {
     // collision, their start tau0 and 3 nu_ref.
     int tau_iters;
     V tau0, nu3;
+    // Seed of the stochastic rounding of this launch (a new one every step).
+    uint32_t seed;
 };
 
 // ------------------------------------------------------------ parameters
@@ -140,6 +143,7 @@ inline Phys<V> make_params(const lbm_ctx *c)
     p.tau_iters = c->opts.tau_iters;
     p.tau0 = V(L.tau0);
     p.nu3 = V(3.0 * L.nu_ref);
+    p.seed = mix32(0x9e3779b9u * (uint32_t)(c->steps + 1) ^ (uint32_t)((uint64_t)c->steps >> 32));
     return p;
 }
 
@@ -164,7 +168,7 @@ struct Store<LBM_F64> {
     using R = double;
     using TauS = double;
     static __device__ __forceinline__ R ld(const S *p, int64_t k, R) { return p[k]; }
-    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R) { p[k] = v; }
+    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R, uint32_t = 0) { p[k] = v; }
 };
 template <>
 struct Store<LBM_F32> {
@@ -172,12 +176,12 @@ struct Store<LBM_F32> {
     using R = float;
     using TauS = float;
     static __device__ __forceinline__ R ld(const S *p, int64_t k, R) { return p[k]; }
-    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R) { p[k] = v; }
+    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R, uint32_t = 0) { p[k] = v; }
     static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float)
     {
         return F2(*reinterpret_cast<const float2 *>(p + k));
     }
-    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float)
+    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float, uint32_t = 0)
     {
         *reinterpret_cast<float2 *>(p + k) = v.v;
     }
@@ -188,12 +192,12 @@ struct Store<LBM_F32D> {
     using R = float;
     using TauS = float;
     static __device__ __forceinline__ R ld(const S *p, int64_t k, R rest) { return rest + p[k]; }
-    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest) { p[k] = v - rest; }
+    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest, uint32_t = 0) { p[k] = v - rest; }
     static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float rest)
     {
         return F2(*reinterpret_cast<const float2 *>(p + k)) + F2(rest);
     }
-    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest)
+    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest, uint32_t = 0)
     {
         *reinterpret_cast<float2 *>(p + k) = (v - F2(rest)).v;
     }
@@ -207,7 +211,7 @@ struct Store<LBM_BF16D> {
     {
         return rest + __bfloat162float(p[k]);
     }
-    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest)
+    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest, uint32_t = 0)
     {
         p[k] = __float2bfloat16_rn(v - rest);
     }
@@ -216,7 +220,7 @@ struct Store<LBM_BF16D> {
         const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(p + k);
         return F2(__bfloat1622float2(h)) + F2(rest);
     }
-    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest)
+    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest, uint32_t = 0)
     {
         *reinterpret_cast<__nv_bfloat162 *>(p + k) = __float22bfloat162_rn((v - F2(rest)).v);
     }
@@ -230,7 +234,7 @@ struct Store<LBM_F16D> {
     {
         return rest + __half2float(p[k]);
     }
-    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest)
+    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest, uint32_t = 0)
     {
         p[k] = __float2half_rn(v - rest);
     }
@@ -239,9 +243,60 @@ struct Store<LBM_F16D> {
         const __half2 h = *reinterpret_cast<const __half2 *>(p + k);
         return F2(__half22float2(h)) + F2(rest);
     }
-    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest)
+    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest, uint32_t = 0)
     {
         *reinterpret_cast<__half2 *>(p + k) = __float22half2_rn((v - F2(rest)).v);
+    }
+};
+
+// FP16 / BF16 deviation storage with stochastic rounding (lbm_round.cuh):
+// the random bits come from the step's seed and the element's address.
+template <>
+struct Store<LBM_F16S> {
+    using S = __half;
+    using R = float;
+    using TauS = float;
+    static __device__ __forceinline__ R ld(const S *p, int64_t k, R rest) { return rest + __half2float(p[k]); }
+    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest, uint32_t seed = 0)
+    {
+        p[k] = sr_half(v - rest, sr_bits(seed, p + k) >> 16);
+    }
+    static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float rest)
+    {
+        const __half2 h = *reinterpret_cast<const __half2 *>(p + k);
+        return F2(__half22float2(h)) + F2(rest);
+    }
+    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest, uint32_t seed = 0)
+    {
+        const uint32_t r = sr_bits(seed, p + k);
+        const F2 d = v - F2(rest);
+        *reinterpret_cast<__half2 *>(p + k) = __halves2half2(sr_half(d.v.x, r & 0xffffu), sr_half(d.v.y, r >> 16));
+    }
+};
+template <>
+struct Store<LBM_BF16S> {
+    using S = __nv_bfloat16;
+    using R = float;
+    using TauS = float;
+    static __device__ __forceinline__ R ld(const S *p, int64_t k, R rest)
+    {
+        return rest + __bfloat162float(p[k]);
+    }
+    static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest, uint32_t seed = 0)
+    {
+        p[k] = sr_bf16(v - rest, sr_bits(seed, p + k) >> 16);
+    }
+    static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float rest)
+    {
+        const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(p + k);
+        return F2(__bfloat1622float2(h)) + F2(rest);
+    }
+    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest, uint32_t seed = 0)
+    {
+        const uint32_t r = sr_bits(seed, p + k);
+        const F2 d = v - F2(rest);
+        *reinterpret_cast<__nv_bfloat162 *>(p + k) =
+            __halves2bfloat162(sr_bf16(d.v.x, r & 0xffffu), sr_bf16(d.v.y, r >> 16));
     }
 };
 

@@ -389,6 +389,8 @@ static cudaError_t export_t(lbm_ctx *c, double *out)
     case LBM_BF16D: return fn<LBM_BF16D>(__VA_ARGS__);             \
     case LBM_F16D: return fn<LBM_F16D>(__VA_ARGS__);               \
     case LBM_F32D: return fn<LBM_F32D>(__VA_ARGS__);               \
+    case LBM_F16S: return fn<LBM_F16S>(__VA_ARGS__);               \
+    case LBM_BF16S: return fn<LBM_BF16S>(__VA_ARGS__);             \
     default: return cudaErrorInvalidValue;                         \
     }
 

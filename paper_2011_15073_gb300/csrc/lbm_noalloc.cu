@@ -141,6 +141,8 @@ extern "C" int lbm_residual_noalloc(lbm_ctx *c, double *d_snapshot, int first, d
     case LBM_BF16D: e = launch<LBM_BF16D>(c, d_snapshot, first ? 1 : 0, d_result, part); break;
     case LBM_F16D: e = launch<LBM_F16D>(c, d_snapshot, first ? 1 : 0, d_result, part); break;
     case LBM_F32D: e = launch<LBM_F32D>(c, d_snapshot, first ? 1 : 0, d_result, part); break;
+    case LBM_F16S: e = launch<LBM_F16S>(c, d_snapshot, first ? 1 : 0, d_result, part); break;
+    case LBM_BF16S: e = launch<LBM_BF16S>(c, d_snapshot, first ? 1 : 0, d_result, part); break;
     default: return LBM_ERR_ARG;
     }
     return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;

@@ -25,9 +25,9 @@ __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restr
     const R t0 = tau_start<TAU, R, FIELD>(p, f, g, k, [&] { return R(tsrc[k]); });
     const R tau = collide<R, FIELD>(p, f, g, t0, m, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::st(dst, i * p.plane + k, f[i], R(rest_f(i)));
+    for (int i = 0; i < 9; i++) St::st(dst, i * p.plane + k, f[i], R(rest_f(i)), p.seed);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::st(dst + 9 * p.plane, i * p.plane + k, g[i], R(rest_g(i)));
+    for (int i = 0; i < 5; i++) St::st(dst + 9 * p.plane, i * p.plane + k, g[i], R(rest_g(i)), p.seed);
     if constexpr (TAU == 0) tdst[k] = typename St::TauS(tau);
 }
 
@@ -83,9 +83,9 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
     Macro<F2> m;
     const F2 tau = collide<F2, FIELD>(p2, f, g, t0, m, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::st2(dst + i * P, k, f[i], float(rest_f(i)));
+    for (int i = 0; i < 9; i++) St::st2(dst + i * P, k, f[i], float(rest_f(i)), p.seed);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::st2(dst + (9 + i) * P, k, g[i], float(rest_g(i)));
+    for (int i = 0; i < 5; i++) St::st2(dst + (9 + i) * P, k, g[i], float(rest_g(i)), p.seed);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tdst + k) = tau.v;
 }
 

@@ -173,9 +173,9 @@ __device__ __forceinline__ void tma_tile_fast(const unsigned char *stage, typena
     const F2 tau = collide<F2, FIELD>(p2, f, g, t0, m, k);
     const int64_t P = p2.plane;
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::st2(dst + i * P, k, f[i], float(rest_f(i)));
+    for (int i = 0; i < 9; i++) St::st2(dst + i * P, k, f[i], float(rest_f(i)), p2.seed);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::st2(dst + (9 + i) * P, k, g[i], float(rest_g(i)));
+    for (int i = 0; i < 5; i++) St::st2(dst + (9 + i) * P, k, g[i], float(rest_g(i)), p2.seed);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tdst + k) = tau.v;
 }
 
@@ -287,6 +287,8 @@ cudaError_t launch_step_tma(lbm_ctx *c, const void *src, void *dst, const void *
     case LBM_F32D: return tma_dispatch<LBM_F32D>(c, src, dst, tsrc, tdst);
     case LBM_BF16D: return tma_dispatch<LBM_BF16D>(c, src, dst, tsrc, tdst);
     case LBM_F16D: return tma_dispatch<LBM_F16D>(c, src, dst, tsrc, tdst);
+    case LBM_F16S: return tma_dispatch<LBM_F16S>(c, src, dst, tsrc, tdst);
+    case LBM_BF16S: return tma_dispatch<LBM_BF16S>(c, src, dst, tsrc, tdst);
     default: return cudaErrorInvalidValue;
     }
 }

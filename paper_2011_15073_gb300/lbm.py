@@ -14,10 +14,12 @@ import numpy as np
 
 from . import _build
 
-F64, F32, BF16D, F16D, F32D = 0, 1, 2, 3, 4
-PREC_NAMES = {"f64": F64, "f32": F32, "bf16d": BF16D, "f16d": F16D, "f32d": F32D}
-STORE_DTYPE = {F64: np.float64, F32: np.float32, BF16D: np.uint16, F16D: np.float16, F32D: np.float32}
-TAU_DTYPE = {F64: np.float64, F32: np.float32, BF16D: np.float32, F16D: np.float32, F32D: np.float32}
+F64, F32, BF16D, F16D, F32D, F16S, BF16S = 0, 1, 2, 3, 4, 5, 6
+PREC_NAMES = {"f64": F64, "f32": F32, "bf16d": BF16D, "f16d": F16D, "f32d": F32D, "f16s": F16S, "bf16s": BF16S}
+STORE_DTYPE = {F64: np.float64, F32: np.float32, BF16D: np.uint16, F16D: np.float16, F32D: np.float32,
+               F16S: np.float16, BF16S: np.uint16}
+TAU_DTYPE = {F64: np.float64, F32: np.float32, BF16D: np.float32, F16D: np.float32, F32D: np.float32,
+             F16S: np.float32, BF16S: np.float32}
 
 ERRORS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_UNSTABLE", -3: "LBM_ERR_NONFINITE",
           -4: "LBM_ERR_CUDA", -5: "LBM_ERR_OOM", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_UNSUPPORTED",

@@ -19,7 +19,8 @@ arithmetic adds about 100 unit roundoffs.
 """
 import numpy as np
 
-EPS = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "f32d": 2.0 ** -24, "bf16d": 2.0 ** -24, "f16d": 2.0 ** -24}
+EPS = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "f32d": 2.0 ** -24, "bf16d": 2.0 ** -24, "f16d": 2.0 ** -24,
+       "f16s": 2.0 ** -24, "bf16s": 2.0 ** -24}
 
 
 def law_tau(gs, lat):

@@ -95,3 +95,28 @@ def test_implicit_tau_reaches_the_lagged_steady_state(lbm):
     assert abs(nu1 - nu0) <= 1e-7 * nu0
     assert np.max(np.abs(v1 - v0)) <= 1e-6 * np.max(v0)
     assert np.max(np.abs(u1 - u0)) <= 1e-6 * np.max(np.abs(u0))
+
+
+def test_stochastic_rounding_reaches_the_fp64_steady_state(lbm):
+    """16-bit storage near a steady state: with round-to-nearest the per-step
+    updates fall below half a spacing and are lost, so the stored state
+    stalls away from the scheme's steady state; stochastic rounding keeps
+    them on average.  48^2, n = 0.6, Da = 1e-2, Ra = 1e5 (continuous law):
+    the FP16 stochastic run's Nu, averaged over its last 20 samples, must
+    match FP64 within 1e-3 and be at least ten times closer than the
+    round-to-nearest run's."""
+    case = dict(n=0.6, Da=1e-2, Ra=1e5, Pr=6.2, porosity=0.6)
+    steps, every, tail = 200_000, 1000, 20
+    nus = {}
+    for prec in ("f64", "f16d", "f16s"):
+        with lbm.Cavity(48, 48, prec=prec, clamp_mode=1, **case) as cav:
+            cav.step(steps - every * tail)
+            s = []
+            for _ in range(tail):
+                cav.step(every)
+                s.append(cav.nusselt()[0])
+        nus[prec] = float(np.mean(s))
+    e_rn = abs(nus["f16d"] - nus["f64"]) / nus["f64"]
+    e_sr = abs(nus["f16s"] - nus["f64"]) / nus["f64"]
+    assert e_sr < 1e-3, nus
+    assert e_sr * 10 < e_rn, nus

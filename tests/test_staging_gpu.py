@@ -38,7 +38,7 @@ def run(lbm, state, nx, ny, c, prec, staging, tau_iters, Da, steps):
         return cav.get_state_f64()
 
 
-@pytest.mark.parametrize("prec", ["f32", "f32d", "bf16d", "f16d"])
+@pytest.mark.parametrize("prec", ["f32", "f32d", "bf16d", "f16d", "f16s", "bf16s"])
 @pytest.mark.parametrize("tau_iters", [0, 2])
 @pytest.mark.parametrize("field", [False, True], ids=["uniform", "field"])
 @pytest.mark.parametrize("size", SIZES, ids=lambda s: f"{s[0]}x{s[1]}")
