@@ -32,21 +32,21 @@ __device__ __forceinline__ void push(typename Store<PREC>::S *__restrict__ A, co
     const int64_t k = (int64_t)y * W + x;
     const bool xl = x > 0, xr = x < p.nx - 1, yb = y > 0, yt = y < p.ny - 1;
     // target x + e_i: e1 (1,0) e2 (0,1) e3 (-1,0) e4 (0,-1) e5 (1,1) e6 (-1,1) e7 (-1,-1) e8 (1,-1)
-    St::st(A, 0 * P + k, f[0], R(rest_f(0)), p.seed);
-    if (xr) St::st(A, 1 * P + k + 1, f[1], R(rest_f(1)), p.seed); else St::st(A, 3 * P + k, f[1], R(rest_f(3)), p.seed);
-    if (yt) St::st(A, 2 * P + k + W, f[2], R(rest_f(2)), p.seed); else St::st(A, 4 * P + k, f[2], R(rest_f(4)), p.seed);
-    if (xl) St::st(A, 3 * P + k - 1, f[3], R(rest_f(3)), p.seed); else St::st(A, 1 * P + k, f[3], R(rest_f(1)), p.seed);
-    if (yb) St::st(A, 4 * P + k - W, f[4], R(rest_f(4)), p.seed); else St::st(A, 2 * P + k, f[4], R(rest_f(2)), p.seed);
-    if (xr && yt) St::st(A, 5 * P + k + W + 1, f[5], R(rest_f(5)), p.seed); else St::st(A, 7 * P + k, f[5], R(rest_f(7)), p.seed);
-    if (xl && yt) St::st(A, 6 * P + k + W - 1, f[6], R(rest_f(6)), p.seed); else St::st(A, 8 * P + k, f[6], R(rest_f(8)), p.seed);
-    if (xl && yb) St::st(A, 7 * P + k - W - 1, f[7], R(rest_f(7)), p.seed); else St::st(A, 5 * P + k, f[7], R(rest_f(5)), p.seed);
-    if (xr && yb) St::st(A, 8 * P + k - W + 1, f[8], R(rest_f(8)), p.seed); else St::st(A, 6 * P + k, f[8], R(rest_f(6)), p.seed);
+    St::sdv(A, 0 * P + k, f[0], R(rest_f(0)), p.seed);
+    if (xr) St::sdv(A, 1 * P + k + 1, f[1], R(rest_f(1)), p.seed); else St::sdv(A, 3 * P + k, f[1], R(rest_f(3)), p.seed);
+    if (yt) St::sdv(A, 2 * P + k + W, f[2], R(rest_f(2)), p.seed); else St::sdv(A, 4 * P + k, f[2], R(rest_f(4)), p.seed);
+    if (xl) St::sdv(A, 3 * P + k - 1, f[3], R(rest_f(3)), p.seed); else St::sdv(A, 1 * P + k, f[3], R(rest_f(1)), p.seed);
+    if (yb) St::sdv(A, 4 * P + k - W, f[4], R(rest_f(4)), p.seed); else St::sdv(A, 2 * P + k, f[4], R(rest_f(2)), p.seed);
+    if (xr && yt) St::sdv(A, 5 * P + k + W + 1, f[5], R(rest_f(5)), p.seed); else St::sdv(A, 7 * P + k, f[5], R(rest_f(7)), p.seed);
+    if (xl && yt) St::sdv(A, 6 * P + k + W - 1, f[6], R(rest_f(6)), p.seed); else St::sdv(A, 8 * P + k, f[6], R(rest_f(8)), p.seed);
+    if (xl && yb) St::sdv(A, 7 * P + k - W - 1, f[7], R(rest_f(7)), p.seed); else St::sdv(A, 5 * P + k, f[7], R(rest_f(5)), p.seed);
+    if (xr && yb) St::sdv(A, 8 * P + k - W + 1, f[8], R(rest_f(8)), p.seed); else St::sdv(A, 6 * P + k, f[8], R(rest_f(6)), p.seed);
     typename Store<PREC>::S *G = A + 9 * P;
-    St::st(G, 0 * P + k, g[0], R(rest_g(0)), p.seed);
-    if (xr) St::st(G, 1 * P + k + 1, g[1], R(rest_g(1)), p.seed); else St::st(G, 3 * P + k, p.abb_cold - g[1], R(rest_g(3)), p.seed);
-    if (yt) St::st(G, 2 * P + k + W, g[2], R(rest_g(2)), p.seed); else St::st(G, 4 * P + k, g[2], R(rest_g(4)), p.seed);
-    if (xl) St::st(G, 3 * P + k - 1, g[3], R(rest_g(3)), p.seed); else St::st(G, 1 * P + k, p.abb_hot - g[3], R(rest_g(1)), p.seed);
-    if (yb) St::st(G, 4 * P + k - W, g[4], R(rest_g(4)), p.seed); else St::st(G, 2 * P + k, g[4], R(rest_g(2)), p.seed);
+    St::sdv(G, 0 * P + k, g[0], R(rest_g(0)), p.seed);
+    if (xr) St::sdv(G, 1 * P + k + 1, g[1], R(rest_g(1)), p.seed); else St::sdv(G, 3 * P + k, p.abbd_cold - g[1], R(rest_g(3)), p.seed);
+    if (yt) St::sdv(G, 2 * P + k + W, g[2], R(rest_g(2)), p.seed); else St::sdv(G, 4 * P + k, g[2], R(rest_g(4)), p.seed);
+    if (xl) St::sdv(G, 3 * P + k - 1, g[3], R(rest_g(3)), p.seed); else St::sdv(G, 1 * P + k, p.abbd_hot - g[3], R(rest_g(1)), p.seed);
+    if (yb) St::sdv(G, 4 * P + k - W, g[4], R(rest_g(4)), p.seed); else St::sdv(G, 2 * P + k, g[4], R(rest_g(2)), p.seed);
 }
 
 // ------------------------------------------------------- one node / thread
@@ -62,15 +62,15 @@ aa_even_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::Ta
     const int64_t P = p.plane, k = (int64_t)y * p.pitch + x;
     R f[9], g[5];
 #pragma unroll
-    for (int i = 0; i < 9; i++) f[i] = St::ld(A, i * P + k, R(rest_f(i)));
+    for (int i = 0; i < 9; i++) f[i] = St::ldd(A, i * P + k, R(rest_f(i)));
 #pragma unroll
-    for (int i = 0; i < 5; i++) g[i] = St::ld(A + 9 * P, i * P + k, R(rest_g(i)));
+    for (int i = 0; i < 5; i++) g[i] = St::ldd(A + 9 * P, i * P + k, R(rest_g(i)));
     Macro<R> m;
-    const R t = collide<R>(p, f, g, tau_start<TAU, R, 2>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
+    const R t = collide<R, 2, 1>(p, f, g, tau_start<TAU, R, 2, 1>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::st(A, opp(i) * P + k, f[i], R(rest_f(opp(i))), p.seed);
+    for (int i = 0; i < 9; i++) St::sdv(A, opp(i) * P + k, f[i], R(rest_f(opp(i))), p.seed);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::st(A + 9 * P, opp(i) * P + k, g[i], R(rest_g(opp(i))), p.seed);
+    for (int i = 0; i < 5; i++) St::sdv(A + 9 * P, opp(i) * P + k, g[i], R(rest_g(opp(i))), p.seed);
     if constexpr (TAU == 0) tau[k] = typename St::TauS(t);
 }
 
@@ -81,9 +81,9 @@ __device__ __forceinline__ void odd_node(typename Store<PREC>::S *__restrict__ A
 {
     const int64_t k = (int64_t)y * p.pitch + x;
     R f[9], g[5];
-    pull<PREC, R, true>(A, p, x, y, f, g);
+    pull<PREC, R, true, 1>(A, p, x, y, f, g);
     Macro<R> m;
-    const R t = collide<R>(p, f, g, tau_start<TAU, R, 2>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
+    const R t = collide<R, 2, 1>(p, f, g, tau_start<TAU, R, 2, 1>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
     push<PREC, R>(A, p, x, y, f, g);
     if constexpr (TAU == 0) tau[k] = typename Store<PREC>::TauS(t);
 }
@@ -109,27 +109,28 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
     const int64_t P = p.plane, k = (int64_t)y * p.pitch + x0;
     if (x0 + 1 >= p.nx) {   // ragged end of the row: one node
         float f[9], g[5];
-        for (int i = 0; i < 9; i++) f[i] = St::ld(A, i * P + k, float(rest_f(i)));
-        for (int i = 0; i < 5; i++) g[i] = St::ld(A + 9 * P, i * P + k, float(rest_g(i)));
+        for (int i = 0; i < 9; i++) f[i] = St::ldd(A, i * P + k, float(rest_f(i)));
+        for (int i = 0; i < 5; i++) g[i] = St::ldd(A + 9 * P, i * P + k, float(rest_g(i)));
         Macro<float> m;
-        const float t = collide<float>(p, f, g, tau_start<TAU, float, 2>(p, f, g, k, [&] { return tau[k]; }), m, k);
-        for (int i = 0; i < 9; i++) St::st(A, opp(i) * P + k, f[i], float(rest_f(opp(i))), p.seed);
-        for (int i = 0; i < 5; i++) St::st(A + 9 * P, opp(i) * P + k, g[i], float(rest_g(opp(i))), p.seed);
+        const float t =
+            collide<float, 2, 1>(p, f, g, tau_start<TAU, float, 2, 1>(p, f, g, k, [&] { return tau[k]; }), m, k);
+        for (int i = 0; i < 9; i++) St::sdv(A, opp(i) * P + k, f[i], float(rest_f(opp(i))), p.seed);
+        for (int i = 0; i < 5; i++) St::sdv(A + 9 * P, opp(i) * P + k, g[i], float(rest_g(opp(i))), p.seed);
         if constexpr (TAU == 0) tau[k] = t;
         return;
     }
     F2 f[9], g[5];
 #pragma unroll
-    for (int i = 0; i < 9; i++) f[i] = St::ld2(A + i * P, k, float(rest_f(i)));
+    for (int i = 0; i < 9; i++) f[i] = St::ldd2(A + i * P, k, float(rest_f(i)));
 #pragma unroll
-    for (int i = 0; i < 5; i++) g[i] = St::ld2(A + (9 + i) * P, k, float(rest_g(i)));
+    for (int i = 0; i < 5; i++) g[i] = St::ldd2(A + (9 + i) * P, k, float(rest_g(i)));
     Macro<F2> m;
-    const F2 t0 = tau_start<TAU, F2, 2>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
-    const F2 t = collide<F2>(p2, f, g, t0, m, k);
+    const F2 t0 = tau_start<TAU, F2, 2, 1>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
+    const F2 t = collide<F2, 2, 1>(p2, f, g, t0, m, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::st2(A + opp(i) * P, k, f[i], float(rest_f(opp(i))), p2.seed);
+    for (int i = 0; i < 9; i++) St::sdv2(A + opp(i) * P, k, f[i], float(rest_f(opp(i))), p2.seed);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::st2(A + (9 + opp(i)) * P, k, g[i], float(rest_g(opp(i))), p2.seed);
+    for (int i = 0; i < 5; i++) St::sdv2(A + (9 + opp(i)) * P, k, g[i], float(rest_g(opp(i))), p2.seed);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tau + k) = t.v;
 }
 
@@ -143,9 +144,9 @@ __device__ __forceinline__ void push_right(typename Store<PREC>::S *base, int64_
 {
     using St = Store<PREC>;
     const float prev = __shfl_up_sync(0xffffffffu, v.v.y, 1);
-    if (lane != 0) St::st2(base, kr, F2(prev, v.v.x), rest, seed);
-    else St::st(base, kr + 1, v.v.x, rest, seed);
-    if (lane == 31) St::st(base, kr + 2, v.v.y, rest, seed);
+    if (lane != 0) St::sdv2(base, kr, F2(prev, v.v.x), rest, seed);
+    else St::sdv(base, kr + 1, v.v.x, rest, seed);
+    if (lane == 31) St::sdv(base, kr + 2, v.v.y, rest, seed);
 }
 template <int PREC>
 __device__ __forceinline__ void push_left(typename Store<PREC>::S *base, int64_t kr, F2 v, float rest, int lane,
@@ -153,9 +154,9 @@ __device__ __forceinline__ void push_left(typename Store<PREC>::S *base, int64_t
 {
     using St = Store<PREC>;
     const float next = __shfl_down_sync(0xffffffffu, v.v.x, 1);
-    if (lane != 31) St::st2(base, kr, F2(v.v.y, next), rest, seed);
-    else St::st(base, kr, v.v.y, rest, seed);
-    if (lane == 0) St::st(base, kr - 1, v.v.x, rest, seed);
+    if (lane != 31) St::sdv2(base, kr, F2(v.v.y, next), rest, seed);
+    else St::sdv(base, kr, v.v.y, rest, seed);
+    if (lane == 0) St::sdv(base, kr - 1, v.v.x, rest, seed);
 }
 
 template <int PREC, int TAU>
@@ -180,42 +181,42 @@ aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau,
     const bool l0 = lane == 0, l31 = lane == 31;
     // gather f_i(x) = f*_i(x - e_i), kept in slot opp(i) of node x - e_i
     F2 f[9], g[5];
-    f[0] = St::ld2(fs, k, float(rest_f(0)));
-    f[1] = from_left(St::ld2(fs + 3 * P, k, float(rest_f(3))), l0 ? St::ld(fs + 3 * P, k - 1, float(rest_f(3))) : 0.f, lane);
-    f[2] = St::ld2(fs + 4 * P, k - W, float(rest_f(4)));
-    f[3] = from_right(St::ld2(fs + P, k, float(rest_f(1))), l31 ? St::ld(fs + P, k + 2, float(rest_f(1))) : 0.f, lane);
-    f[4] = St::ld2(fs + 2 * P, k + W, float(rest_f(2)));
-    f[5] = from_left(St::ld2(fs + 7 * P, k - W, float(rest_f(7))),
-                     l0 ? St::ld(fs + 7 * P, k - W - 1, float(rest_f(7))) : 0.f, lane);
-    f[6] = from_right(St::ld2(fs + 8 * P, k - W, float(rest_f(8))),
-                      l31 ? St::ld(fs + 8 * P, k - W + 2, float(rest_f(8))) : 0.f, lane);
-    f[7] = from_right(St::ld2(fs + 5 * P, k + W, float(rest_f(5))),
-                      l31 ? St::ld(fs + 5 * P, k + W + 2, float(rest_f(5))) : 0.f, lane);
-    f[8] = from_left(St::ld2(fs + 6 * P, k + W, float(rest_f(6))),
-                     l0 ? St::ld(fs + 6 * P, k + W - 1, float(rest_f(6))) : 0.f, lane);
-    g[0] = St::ld2(gs, k, float(rest_g(0)));
-    g[1] = from_left(St::ld2(gs + 3 * P, k, float(rest_g(3))), l0 ? St::ld(gs + 3 * P, k - 1, float(rest_g(3))) : 0.f, lane);
-    g[2] = St::ld2(gs + 4 * P, k - W, float(rest_g(4)));
-    g[3] = from_right(St::ld2(gs + P, k, float(rest_g(1))), l31 ? St::ld(gs + P, k + 2, float(rest_g(1))) : 0.f, lane);
-    g[4] = St::ld2(gs + 2 * P, k + W, float(rest_g(2)));
+    f[0] = St::ldd2(fs, k, float(rest_f(0)));
+    f[1] = from_left(St::ldd2(fs + 3 * P, k, float(rest_f(3))), l0 ? St::ldd(fs + 3 * P, k - 1, float(rest_f(3))) : 0.f, lane);
+    f[2] = St::ldd2(fs + 4 * P, k - W, float(rest_f(4)));
+    f[3] = from_right(St::ldd2(fs + P, k, float(rest_f(1))), l31 ? St::ldd(fs + P, k + 2, float(rest_f(1))) : 0.f, lane);
+    f[4] = St::ldd2(fs + 2 * P, k + W, float(rest_f(2)));
+    f[5] = from_left(St::ldd2(fs + 7 * P, k - W, float(rest_f(7))),
+                     l0 ? St::ldd(fs + 7 * P, k - W - 1, float(rest_f(7))) : 0.f, lane);
+    f[6] = from_right(St::ldd2(fs + 8 * P, k - W, float(rest_f(8))),
+                      l31 ? St::ldd(fs + 8 * P, k - W + 2, float(rest_f(8))) : 0.f, lane);
+    f[7] = from_right(St::ldd2(fs + 5 * P, k + W, float(rest_f(5))),
+                      l31 ? St::ldd(fs + 5 * P, k + W + 2, float(rest_f(5))) : 0.f, lane);
+    f[8] = from_left(St::ldd2(fs + 6 * P, k + W, float(rest_f(6))),
+                     l0 ? St::ldd(fs + 6 * P, k + W - 1, float(rest_f(6))) : 0.f, lane);
+    g[0] = St::ldd2(gs, k, float(rest_g(0)));
+    g[1] = from_left(St::ldd2(gs + 3 * P, k, float(rest_g(3))), l0 ? St::ldd(gs + 3 * P, k - 1, float(rest_g(3))) : 0.f, lane);
+    g[2] = St::ldd2(gs + 4 * P, k - W, float(rest_g(4)));
+    g[3] = from_right(St::ldd2(gs + P, k, float(rest_g(1))), l31 ? St::ldd(gs + P, k + 2, float(rest_g(1))) : 0.f, lane);
+    g[4] = St::ldd2(gs + 2 * P, k + W, float(rest_g(2)));
     Macro<F2> m;
-    const F2 t0 = tau_start<TAU, F2, 2>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
-    const F2 t = collide<F2>(p2, f, g, t0, m, k);
+    const F2 t0 = tau_start<TAU, F2, 2, 1>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
+    const F2 t = collide<F2, 2, 1>(p2, f, g, t0, m, k);
     // push f*_i(x) into slot i of node x + e_i
-    St::st2(fs, k, f[0], float(rest_f(0)), p2.seed);
+    St::sdv2(fs, k, f[0], float(rest_f(0)), p2.seed);
     push_right<PREC>(fs + P, k, f[1], float(rest_f(1)), lane, p2.seed);
-    St::st2(fs + 2 * P, k + W, f[2], float(rest_f(2)), p2.seed);
+    St::sdv2(fs + 2 * P, k + W, f[2], float(rest_f(2)), p2.seed);
     push_left<PREC>(fs + 3 * P, k, f[3], float(rest_f(3)), lane, p2.seed);
-    St::st2(fs + 4 * P, k - W, f[4], float(rest_f(4)), p2.seed);
+    St::sdv2(fs + 4 * P, k - W, f[4], float(rest_f(4)), p2.seed);
     push_right<PREC>(fs + 5 * P, k + W, f[5], float(rest_f(5)), lane, p2.seed);
     push_left<PREC>(fs + 6 * P, k + W, f[6], float(rest_f(6)), lane, p2.seed);
     push_left<PREC>(fs + 7 * P, k - W, f[7], float(rest_f(7)), lane, p2.seed);
     push_right<PREC>(fs + 8 * P, k - W, f[8], float(rest_f(8)), lane, p2.seed);
-    St::st2(gs, k, g[0], float(rest_g(0)), p2.seed);
+    St::sdv2(gs, k, g[0], float(rest_g(0)), p2.seed);
     push_right<PREC>(gs + P, k, g[1], float(rest_g(1)), lane, p2.seed);
-    St::st2(gs + 2 * P, k + W, g[2], float(rest_g(2)), p2.seed);
+    St::sdv2(gs + 2 * P, k + W, g[2], float(rest_g(2)), p2.seed);
     push_left<PREC>(gs + 3 * P, k, g[3], float(rest_g(3)), lane, p2.seed);
-    St::st2(gs + 4 * P, k - W, g[4], float(rest_g(4)), p2.seed);
+    St::sdv2(gs + 4 * P, k - W, g[4], float(rest_g(4)), p2.seed);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tau + k) = t.v;
 }
 
@@ -234,12 +235,12 @@ aa_normalize_kernel(typename Store<PREC>::S *__restrict__ A, Phys<typename Store
     if (x >= p.nx) return;
     const int64_t P = p.plane, W = p.pitch, k = (int64_t)y * W + x;
     const bool xl = x > 0, xr = x < p.nx - 1, yt = y < p.ny - 1;
-    auto swap = [&](typename Store<PREC>::S *base, int i, int64_t kt, bool flow) {
-        const R ri = R(flow ? rest_f(i) : rest_g(i)), ro = R(flow ? rest_f(opp(i)) : rest_g(opp(i)));
-        const R a = St::ld(base, i * P + kt, ri);
-        const R b = St::ld(base, opp(i) * P + k, ro);
-        St::st(base, i * P + kt, b, ri);
-        St::st(base, opp(i) * P + k, a, ro);
+    // opposite directions have equal weights, so the stored representation
+    // (value or deviation) moves between the two slots unchanged
+    auto swap = [&](typename Store<PREC>::S *base, int i, int64_t kt, bool) {
+        const typename Store<PREC>::S a = base[i * P + kt];
+        base[i * P + kt] = base[opp(i) * P + k];
+        base[opp(i) * P + k] = a;
     };
     if (xr) swap(A, 1, k + 1, true);
     if (yt) swap(A, 2, k + W, true);
@@ -248,8 +249,8 @@ aa_normalize_kernel(typename Store<PREC>::S *__restrict__ A, Phys<typename Store
     typename Store<PREC>::S *G = A + 9 * P;
     if (xr) swap(G, 1, k + 1, false);
     if (yt) swap(G, 2, k + W, false);
-    if (!xl) St::st(G, 1 * P + k, p.abb_hot - St::ld(G, 1 * P + k, R(rest_g(1))), R(rest_g(1)));
-    if (!xr) St::st(G, 3 * P + k, p.abb_cold - St::ld(G, 3 * P + k, R(rest_g(3))), R(rest_g(3)));
+    if (!xl) St::sdv(G, 1 * P + k, p.abbd_hot - St::ldd(G, 1 * P + k, R(rest_g(1))), R(rest_g(1)), p.seed);
+    if (!xr) St::sdv(G, 3 * P + k, p.abbd_cold - St::ldd(G, 3 * P + k, R(rest_g(3))), R(rest_g(3)), p.seed);
 }
 
 // ------------------------------------------------------------- launchers

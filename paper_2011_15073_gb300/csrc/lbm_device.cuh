@@ -93,6 +93,7 @@ struct Phys {
     V gbeta, Tm;
     V omegaT, s_e, s_p;
     V abb_hot, abb_cold;   // 2 w T_wall for the anti-bounce-back (w = 1/6)
+    V abbd_hot, abbd_cold; // the same on deviations from w T_m: 2 w (T_wall - T_m)
     // Per-node Darcy numbers (lbm_set_darcy_field), or null for the uniform
     // permeability above: a plane of the compute type (float for the F2
     // paths), indexed like the state planes; K = Da L2.
@@ -137,6 +138,8 @@ inline Phys<V> make_params(const lbm_ctx *c)
     p.s_p = V(L.s_p);
     p.abb_hot = V(2.0 / 6.0 * L.T_hot);
     p.abb_cold = V(2.0 / 6.0 * L.T_cold);
+    p.abbd_hot = V(2.0 / 6.0 * (L.T_hot - L.Tm));
+    p.abbd_cold = V(2.0 / 6.0 * (L.T_cold - L.Tm));
     p.da = c->d_da;
     p.L2 = V(L.L * L.L);
     p.eFe = V(L.eps * L.Feps);
@@ -169,6 +172,8 @@ struct Store<LBM_F64> {
     using TauS = double;
     static __device__ __forceinline__ R ld(const S *p, int64_t k, R) { return p[k]; }
     static __device__ __forceinline__ void st(S *p, int64_t k, R v, R, uint32_t = 0) { p[k] = v; }
+    static __device__ __forceinline__ R ldd(const S *p, int64_t k, R rest) { return p[k] - rest; }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R rest, uint32_t = 0) { p[k] = d + rest; }
 };
 template <>
 struct Store<LBM_F32> {
@@ -177,6 +182,16 @@ struct Store<LBM_F32> {
     using TauS = float;
     static __device__ __forceinline__ R ld(const S *p, int64_t k, R) { return p[k]; }
     static __device__ __forceinline__ void st(S *p, int64_t k, R v, R, uint32_t = 0) { p[k] = v; }
+    static __device__ __forceinline__ R ldd(const S *p, int64_t k, R rest) { return p[k] - rest; }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R rest, uint32_t = 0) { p[k] = d + rest; }
+    static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float rest)
+    {
+        return F2(*reinterpret_cast<const float2 *>(p + k)) - F2(rest);
+    }
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float rest, uint32_t = 0)
+    {
+        *reinterpret_cast<float2 *>(p + k) = (d + F2(rest)).v;
+    }
     static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float)
     {
         return F2(*reinterpret_cast<const float2 *>(p + k));
@@ -201,6 +216,16 @@ struct Store<LBM_F32D> {
     {
         *reinterpret_cast<float2 *>(p + k) = (v - F2(rest)).v;
     }
+    static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return p[k]; }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t = 0) { p[k] = d; }
+    static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
+    {
+        return F2(*reinterpret_cast<const float2 *>(p + k));
+    }
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t = 0)
+    {
+        *reinterpret_cast<float2 *>(p + k) = d.v;
+    }
 };
 template <>
 struct Store<LBM_BF16D> {
@@ -223,6 +248,16 @@ struct Store<LBM_BF16D> {
     static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest, uint32_t = 0)
     {
         *reinterpret_cast<__nv_bfloat162 *>(p + k) = __float22bfloat162_rn((v - F2(rest)).v);
+    }
+    static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __bfloat162float(p[k]); }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t = 0) { p[k] = __float2bfloat16_rn(d); }
+    static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
+    {
+        return F2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p + k)));
+    }
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t = 0)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p + k) = __float22bfloat162_rn(d.v);
     }
 };
 template <>
@@ -247,6 +282,16 @@ struct Store<LBM_F16D> {
     {
         *reinterpret_cast<__half2 *>(p + k) = __float22half2_rn((v - F2(rest)).v);
     }
+    static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __half2float(p[k]); }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t = 0) { p[k] = __float2half_rn(d); }
+    static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
+    {
+        return F2(__half22float2(*reinterpret_cast<const __half2 *>(p + k)));
+    }
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t = 0)
+    {
+        *reinterpret_cast<__half2 *>(p + k) = __float22half2_rn(d.v);
+    }
 };
 
 // FP16 / BF16 deviation storage with stochastic rounding (lbm_round.cuh):
@@ -270,6 +315,20 @@ struct Store<LBM_F16S> {
     {
         const uint32_t r = sr_bits(seed, p + k);
         const F2 d = v - F2(rest);
+        *reinterpret_cast<__half2 *>(p + k) = __halves2half2(sr_half(d.v.x, r & 0xffffu), sr_half(d.v.y, r >> 16));
+    }
+    static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __half2float(p[k]); }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t seed = 0)
+    {
+        p[k] = sr_half(d, sr_bits(seed, p + k) >> 16);
+    }
+    static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
+    {
+        return F2(__half22float2(*reinterpret_cast<const __half2 *>(p + k)));
+    }
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t seed = 0)
+    {
+        const uint32_t r = sr_bits(seed, p + k);
         *reinterpret_cast<__half2 *>(p + k) = __halves2half2(sr_half(d.v.x, r & 0xffffu), sr_half(d.v.y, r >> 16));
     }
 };
@@ -298,6 +357,21 @@ struct Store<LBM_BF16S> {
         *reinterpret_cast<__nv_bfloat162 *>(p + k) =
             __halves2bfloat162(sr_bf16(d.v.x, r & 0xffffu), sr_bf16(d.v.y, r >> 16));
     }
+    static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __bfloat162float(p[k]); }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t seed = 0)
+    {
+        p[k] = sr_bf16(d, sr_bits(seed, p + k) >> 16);
+    }
+    static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
+    {
+        return F2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p + k)));
+    }
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t seed = 0)
+    {
+        const uint32_t r = sr_bits(seed, p + k);
+        *reinterpret_cast<__nv_bfloat162 *>(p + k) =
+            __halves2bfloat162(sr_bf16(d.v.x, r & 0xffffu), sr_bf16(d.v.y, r >> 16));
+    }
 };
 
 // ----------------------------------------------------------- pull streaming
@@ -316,7 +390,10 @@ __host__ __device__ constexpr int opp(int i)
 // e5 (1,1), e6 (-1,1), e7 (-1,-1), e8 (1,-1).
 // REV = true reads a state whose post-collision population f*_i(x) is kept
 // in plane opp(i) (the in-place AA layout after an even step).
-template <int PREC, class R, bool REV = false>
+// DEV = 1 returns deviations from the rest state (f_i - w_i, g_i - w_i T_m);
+// the bounce-back rules keep their form (opposite weights are equal), the
+// anti-bounce-back becomes -g* + 2 w (T_w - T_m).
+template <int PREC, class R, bool REV = false, int DEV = 0>
 __device__ __forceinline__ void pull(const typename Store<PREC>::S *__restrict__ src,
                                      const Phys<R> &p, int x, int y, R f[9], R g[5])
 {
@@ -325,21 +402,24 @@ __device__ __forceinline__ void pull(const typename Store<PREC>::S *__restrict__
     const int64_t k = (int64_t)y * W + x;
     const bool xl = x > 0, xr = x < p.nx - 1, yb = y > 0, yt = y < p.ny - 1;
 #define PL(i) ((REV ? opp(i) : (i)) * P)
-    f[0] = St::ld(src, PL(0) + k, R(rest_f(0)));
-    f[1] = xl ? St::ld(src, PL(1) + k - 1, R(rest_f(1))) : St::ld(src, PL(3) + k, R(rest_f(3)));
-    f[2] = yb ? St::ld(src, PL(2) + k - W, R(rest_f(2))) : St::ld(src, PL(4) + k, R(rest_f(4)));
-    f[3] = xr ? St::ld(src, PL(3) + k + 1, R(rest_f(3))) : St::ld(src, PL(1) + k, R(rest_f(1)));
-    f[4] = yt ? St::ld(src, PL(4) + k + W, R(rest_f(4))) : St::ld(src, PL(2) + k, R(rest_f(2)));
-    f[5] = (xl && yb) ? St::ld(src, PL(5) + k - W - 1, R(rest_f(5))) : St::ld(src, PL(7) + k, R(rest_f(7)));
-    f[6] = (xr && yb) ? St::ld(src, PL(6) + k - W + 1, R(rest_f(6))) : St::ld(src, PL(8) + k, R(rest_f(8)));
-    f[7] = (xr && yt) ? St::ld(src, PL(7) + k + W + 1, R(rest_f(7))) : St::ld(src, PL(5) + k, R(rest_f(5)));
-    f[8] = (xl && yt) ? St::ld(src, PL(8) + k + W - 1, R(rest_f(8))) : St::ld(src, PL(6) + k, R(rest_f(6)));
+#define LD(base, idx, rest) (DEV ? St::ldd(base, idx, rest) : St::ld(base, idx, rest))
+    f[0] = LD(src, PL(0) + k, R(rest_f(0)));
+    f[1] = xl ? LD(src, PL(1) + k - 1, R(rest_f(1))) : LD(src, PL(3) + k, R(rest_f(3)));
+    f[2] = yb ? LD(src, PL(2) + k - W, R(rest_f(2))) : LD(src, PL(4) + k, R(rest_f(4)));
+    f[3] = xr ? LD(src, PL(3) + k + 1, R(rest_f(3))) : LD(src, PL(1) + k, R(rest_f(1)));
+    f[4] = yt ? LD(src, PL(4) + k + W, R(rest_f(4))) : LD(src, PL(2) + k, R(rest_f(2)));
+    f[5] = (xl && yb) ? LD(src, PL(5) + k - W - 1, R(rest_f(5))) : LD(src, PL(7) + k, R(rest_f(7)));
+    f[6] = (xr && yb) ? LD(src, PL(6) + k - W + 1, R(rest_f(6))) : LD(src, PL(8) + k, R(rest_f(8)));
+    f[7] = (xr && yt) ? LD(src, PL(7) + k + W + 1, R(rest_f(7))) : LD(src, PL(5) + k, R(rest_f(5)));
+    f[8] = (xl && yt) ? LD(src, PL(8) + k + W - 1, R(rest_f(8))) : LD(src, PL(6) + k, R(rest_f(6)));
     const typename Store<PREC>::S *gs = src + 9 * P;
-    g[0] = St::ld(gs, PL(0) + k, R(rest_g(0)));
-    g[1] = xl ? St::ld(gs, PL(1) + k - 1, R(rest_g(1))) : p.abb_hot - St::ld(gs, PL(3) + k, R(rest_g(3)));
-    g[2] = yb ? St::ld(gs, PL(2) + k - W, R(rest_g(2))) : St::ld(gs, PL(4) + k, R(rest_g(4)));
-    g[3] = xr ? St::ld(gs, PL(3) + k + 1, R(rest_g(3))) : p.abb_cold - St::ld(gs, PL(1) + k, R(rest_g(1)));
-    g[4] = yt ? St::ld(gs, PL(4) + k + W, R(rest_g(4))) : St::ld(gs, PL(2) + k, R(rest_g(2)));
+    const R ah = DEV ? p.abbd_hot : p.abb_hot, ac = DEV ? p.abbd_cold : p.abb_cold;
+    g[0] = LD(gs, PL(0) + k, R(rest_g(0)));
+    g[1] = xl ? LD(gs, PL(1) + k - 1, R(rest_g(1))) : ah - LD(gs, PL(3) + k, R(rest_g(3)));
+    g[2] = yb ? LD(gs, PL(2) + k - W, R(rest_g(2))) : LD(gs, PL(4) + k, R(rest_g(4)));
+    g[3] = xr ? LD(gs, PL(3) + k + 1, R(rest_g(3))) : ac - LD(gs, PL(1) + k, R(rest_g(1)));
+    g[4] = yt ? LD(gs, PL(4) + k + W, R(rest_g(4))) : LD(gs, PL(2) + k, R(rest_g(2)));
+#undef LD
 #undef PL
 }
 
@@ -363,7 +443,8 @@ __device__ __forceinline__ F2 from_right(F2 a, float halo, int lane)
 template <class V>
 struct Macro {
     V rho, irho, T, ux, uy, Fx, Fy, nu_prev;
-    V nu;  // apparent viscosity chosen by the collision (set by collide)
+    V nu;        // apparent viscosity chosen by the collision (set by collide)
+    V drho, dT;  // rho - 1 and T - T_m (accurate in the deviation form)
 };
 
 // Porous coefficients of node k when a per-node Darcy field is set:
@@ -407,18 +488,25 @@ __device__ __forceinline__ Porous<V> porous_at(const Phys<V> &p, int64_t k)
 // u = v / (c0 + sqrt(c0^2 + c1 |v|)), c0 = (1 + eps nu / (2K)) / 2, with the
 // apparent viscosity of the lagged relaxation time; then the total force
 // F = -eps nu u / K - eps F_eps |u| u / sqrt K + eps G.
-template <class V, int FIELD = 2>
+// DEV = 1: f and g are deviations from the rest state (f_i - w_i,
+// g_i - w_i T_m), so the zeroth moments are rho - 1 and T - T_m; every other
+// moment used is the same linear form of the deviations.
+template <class V, int FIELD = 2, int DEV = 0>
 __device__ __forceinline__ Macro<V> macro(const Phys<V> &p, const V f[9], const V g[5], V tau_prev, int64_t k)
 {
     Macro<V> m;
     const Porous<V> q = porous_at<V, FIELD>(p, k);
     const V sax = (f[1] + f[2]) + (f[3] + f[4]);
     const V sdg = (f[5] + f[6]) + (f[7] + f[8]);
-    m.rho = f[0] + sax + sdg;
+    const V r0 = f[0] + sax + sdg;
+    m.rho = DEV ? r0 + V(1) : r0;
+    m.drho = DEV ? r0 : r0 - V(1);
     const V jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     const V jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    m.T = g[0] + (g[1] + g[2]) + (g[3] + g[4]);
-    const V Gy = p.gbeta * (m.T - p.Tm);
+    const V t0 = g[0] + (g[1] + g[2]) + (g[3] + g[4]);
+    m.T = DEV ? t0 + p.Tm : t0;
+    m.dT = DEV ? t0 : t0 - p.Tm;
+    const V Gy = p.gbeta * m.dT;
     m.irho = vrcp(m.rho);
     const V vx = jx * m.irho;
     const V vy = vfma(p.half_eps, Gy, jy * m.irho);
@@ -487,20 +575,23 @@ __device__ __forceinline__ F2 tau_newton(const Phys<F2> &p, F2 tau, F2 gs, F2 bc
               tau_newton_s(tau.v.y, gs.v.y, bc.v.y, ss.v.y, g1, g2, nm1, Dhi, p.clamp_mode, nu3));
 }
 
-template <class V, int FIELD = 2>
+template <class V, int FIELD = 2, int DEV = 0>
 __device__ __forceinline__ V implicit_tau(const Phys<V> &p, const V f[9], const V g[5], int64_t k)
 {
     const Porous<V> q = porous_at<V, FIELD>(p, k);
-    // moments that do not depend on tau (as in macro() and collide())
+    // moments that do not depend on tau (as in macro() and collide(); DEV as
+    // there)
     const V sax = (f[1] + f[2]) + (f[3] + f[4]);
     const V sdg = (f[5] + f[6]) + (f[7] + f[8]);
-    const V rho = f[0] + sax + sdg;
+    const V r0 = f[0] + sax + sdg;
+    const V rho = DEV ? r0 + V(1) : r0;
     const V jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
     const V jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    const V T = g[0] + (g[1] + g[2]) + (g[3] + g[4]);
+    const V t0 = g[0] + (g[1] + g[2]) + (g[3] + g[4]);
+    const V dT = DEV ? t0 : t0 - p.Tm;
     const V irho = vrcp(rho);
     const V vx = jx * irho;
-    const V vy = vfma(p.half_eps, p.gbeta * (T - p.Tm), jy * irho);
+    const V vy = vfma(p.half_eps, p.gbeta * dT, jy * irho);
     const V c1v = q.c1 * vsqrt(vfma(vx, vx, vy * vy));
     const V e = vfma(V(2), sdg, vfma(V(-4), f[0], -sax));
     const V pxx = (f[1] + f[3]) - (f[2] + f[4]);
@@ -515,7 +606,7 @@ __device__ __forceinline__ V implicit_tau(const Phys<V> &p, const V f[9], const 
         const V iden = vrcp(c0 + vsqrt(vfma(c0, c0, c1v)));
         const V ux = vx * iden, uy = vy * iden;
         const V u2e3 = V(3) * vfma(ux, ux, uy * uy) * p.inv_eps;
-        const V e_eq = vfma(rho, u2e3, V(-2) * rho);
+        const V e_eq = vfma(rho, u2e3, V(-2) * (DEV ? r0 : rho));
         const V w = vrcp(tau);
         const V A = V(1.4 / 6.0) * (e - e_eq);
         const V B = V(0.5) * w * (pxx - rie * vfma(ux, ux, -(uy * uy)));
@@ -529,11 +620,11 @@ __device__ __forceinline__ V implicit_tau(const Phys<V> &p, const V f[9], const 
 
 // tau the collision of a node starts from: TAU 0 the stored lagged value
 // (loaded only then), TAU 1 the implicit solve.
-template <int TAU, class V, int FIELD, class Load>
+template <int TAU, class V, int FIELD, int DEV = 0, class Load>
 __device__ __forceinline__ V tau_start(const Phys<V> &p, const V f[9], const V g[5], int64_t k, Load load)
 {
     if constexpr (TAU == 1)
-        return implicit_tau<V, FIELD>(p, f, g, k);
+        return implicit_tau<V, FIELD, DEV>(p, f, g, k);
     else
         return load();
 }
@@ -542,12 +633,12 @@ __device__ __forceinline__ V tau_start(const Phys<V> &p, const V f[9], const V g
 // Returns the new relaxation time; m receives the macroscopic moments and the
 // apparent lattice viscosity of this collision.  k is the node's offset in a
 // plane (used only to read a per-node Darcy field).
-template <class V, int FIELD = 2>
+template <class V, int FIELD = 2, int DEV = 0>
 __device__ __forceinline__ V collide(const Phys<V> &p, V f[9], V g[5], V tau_prev, Macro<V> &m, int64_t k)
 {
-    m = macro<V, FIELD>(p, f, g, tau_prev, k);
+    m = macro<V, FIELD, DEV>(p, f, g, tau_prev, k);
     const V rho = m.rho, ux = m.ux, uy = m.uy;
-    // raw moments
+    // raw moments (DEV: e + 2 and eps - 1, their rest values removed)
     const V sax = (f[1] + f[2]) + (f[3] + f[4]);
     const V sdg = (f[5] + f[6]) + (f[7] + f[8]);
     const V e = vfma(V(2), sdg, vfma(V(-4), f[0], -sax));
@@ -559,8 +650,10 @@ __device__ __forceinline__ V collide(const Phys<V> &p, V f[9], V g[5], V tau_pre
     // equilibria
     const V rie = rho * p.inv_eps;
     const V u2e3 = V(3) * vfma(ux, ux, uy * uy) * p.inv_eps;
-    const V e_eq = vfma(rho, u2e3, V(-2) * rho);
-    const V ep_eq = rho - rho * u2e3;
+    // DEV: e_eq + 2 = rho u2e3 - 2 (rho - 1), eps_eq - 1 = (rho - 1) - rho u2e3
+    const V r0 = DEV ? m.drho : rho;
+    const V e_eq = vfma(rho, u2e3, V(-2) * r0);
+    const V ep_eq = r0 - rho * u2e3;
     const V pxx_eq = rie * vfma(ux, ux, -(uy * uy));
     const V pxy_eq = rie * (ux * uy);
     // strain rate from the non-equilibrium moments with the lagged tau:
@@ -591,7 +684,7 @@ __device__ __forceinline__ V collide(const Phys<V> &p, V f[9], V g[5], V tau_pre
     const V pxxs = vfma(hw, Fxx, vfma(-w, pxx - pxx_eq, pxx));
     const V pxys = vfma(hw, Fxy, vfma(-w, pxy - pxy_eq, pxy));
     // f* = M^T diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) m*
-    const V a0 = rho * V(1.0 / 9.0), a1 = es * V(1.0 / 36.0), a2 = eps_s * V(1.0 / 36.0);
+    const V a0 = r0 * V(1.0 / 9.0), a1 = es * V(1.0 / 36.0), a2 = eps_s * V(1.0 / 36.0);
     const V a3 = jxs * V(1.0 / 6.0), a4 = qxs * V(1.0 / 12.0);
     const V a5 = jys * V(1.0 / 6.0), a6 = qys * V(1.0 / 12.0);
     const V a7 = pxxs * V(0.25), a8 = pxys * V(0.25);
@@ -609,16 +702,17 @@ __device__ __forceinline__ V collide(const Phys<V> &p, V f[9], V g[5], V tau_pre
     f[7] = b_dg - xd - yd + a8;
     f[8] = b_dg + xd - yd - a8;
     // thermal MRT: n = N g, n* = n - S_T (n - n_eq), n_eq = (T, T u, -2T/3, 0)
-    const V T = m.T;
+    // (DEV: n_0 and n_3 without their rest values T_m and -2 T_m / 3)
+    const V T = m.T, T0 = DEV ? m.dT : m.T;
     const V n1 = g[1] - g[3], n2 = g[2] - g[4];
     const V n3 = vfma(V(-4), g[0], (g[1] + g[2]) + (g[3] + g[4]));
     const V n4 = (g[1] + g[3]) - (g[2] + g[4]);
     const V n1s = vfma(-p.omegaT, vfma(-T, ux, n1), n1);
     const V n2s = vfma(-p.omegaT, vfma(-T, uy, n2), n2);
-    const V n3s = vfma(-p.s_e, vfma(V(2.0 / 3.0), T, n3), n3);
+    const V n3s = vfma(-p.s_e, vfma(V(2.0 / 3.0), T0, n3), n3);
     const V n4s = vfma(-p.s_p, n4, n4);
     // g* = N^T diag(1/5, 1/2, 1/2, 1/20, 1/4) n*
-    const V t0 = T * V(0.2), t3 = n3s * V(0.05), t4 = n4s * V(0.25);
+    const V t0 = T0 * V(0.2), t3 = n3s * V(0.05), t4 = n4s * V(0.25);
     const V h1 = n1s * V(0.5), h2 = n2s * V(0.5);
     const V t03 = t0 + t3;
     g[0] = vfma(V(-0.2), n3s, t0);

@@ -9,7 +9,10 @@ namespace lbm {
 
 // Pull, collide and store one node (wall rules included).  TAU 0: the
 // collision starts from the stored lagged tau and stores its new tau; TAU 1:
-// from the node-local implicit tau, and no tau is read or written.
+// from the node-local implicit tau, and no tau is read or written.  The
+// arithmetic runs on deviations from the rest state (DEV form of pull,
+// macro and collide), which keeps the small per-step changes of a nearly
+// steady state out of the rounding of O(1) population values.
 template <int PREC, class R, int FIELD = 2, int TAU = 0>
 __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restrict__ src,
                                           typename Store<PREC>::S *__restrict__ dst,
@@ -20,14 +23,14 @@ __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restr
     using St = Store<PREC>;
     const int64_t k = (int64_t)y * p.pitch + x;
     R f[9], g[5];
-    pull<PREC, R>(src, p, x, y, f, g);
+    pull<PREC, R, false, 1>(src, p, x, y, f, g);
     Macro<R> m;
-    const R t0 = tau_start<TAU, R, FIELD>(p, f, g, k, [&] { return R(tsrc[k]); });
-    const R tau = collide<R, FIELD>(p, f, g, t0, m, k);
+    const R t0 = tau_start<TAU, R, FIELD, 1>(p, f, g, k, [&] { return R(tsrc[k]); });
+    const R tau = collide<R, FIELD, 1>(p, f, g, t0, m, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::st(dst, i * p.plane + k, f[i], R(rest_f(i)), p.seed);
+    for (int i = 0; i < 9; i++) St::sdv(dst, i * p.plane + k, f[i], R(rest_f(i)), p.seed);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::st(dst + 9 * p.plane, i * p.plane + k, g[i], R(rest_g(i)), p.seed);
+    for (int i = 0; i < 5; i++) St::sdv(dst + 9 * p.plane, i * p.plane + k, g[i], R(rest_g(i)), p.seed);
     if constexpr (TAU == 0) tdst[k] = typename St::TauS(tau);
 }
 
@@ -61,31 +64,31 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
     const S *gs = src + 9 * P;
     const bool l0 = lane == 0, l31 = lane == 31;
     F2 f[9], g[5];
-    f[0] = St::ld2(fs, k, float(rest_f(0)));
-    f[1] = from_left(St::ld2(fs + P, k, float(rest_f(1))), l0 ? St::ld(fs + P, k - 1, float(rest_f(1))) : 0.f, lane);
-    f[2] = St::ld2(fs + 2 * P, k - W, float(rest_f(2)));
-    f[3] = from_right(St::ld2(fs + 3 * P, k, float(rest_f(3))), l31 ? St::ld(fs + 3 * P, k + 2, float(rest_f(3))) : 0.f, lane);
-    f[4] = St::ld2(fs + 4 * P, k + W, float(rest_f(4)));
-    f[5] = from_left(St::ld2(fs + 5 * P, k - W, float(rest_f(5))),
-                     l0 ? St::ld(fs + 5 * P, k - W - 1, float(rest_f(5))) : 0.f, lane);
-    f[6] = from_right(St::ld2(fs + 6 * P, k - W, float(rest_f(6))),
-                      l31 ? St::ld(fs + 6 * P, k - W + 2, float(rest_f(6))) : 0.f, lane);
-    f[7] = from_right(St::ld2(fs + 7 * P, k + W, float(rest_f(7))),
-                      l31 ? St::ld(fs + 7 * P, k + W + 2, float(rest_f(7))) : 0.f, lane);
-    f[8] = from_left(St::ld2(fs + 8 * P, k + W, float(rest_f(8))),
-                     l0 ? St::ld(fs + 8 * P, k + W - 1, float(rest_f(8))) : 0.f, lane);
-    g[0] = St::ld2(gs, k, float(rest_g(0)));
-    g[1] = from_left(St::ld2(gs + P, k, float(rest_g(1))), l0 ? St::ld(gs + P, k - 1, float(rest_g(1))) : 0.f, lane);
-    g[2] = St::ld2(gs + 2 * P, k - W, float(rest_g(2)));
-    g[3] = from_right(St::ld2(gs + 3 * P, k, float(rest_g(3))), l31 ? St::ld(gs + 3 * P, k + 2, float(rest_g(3))) : 0.f, lane);
-    g[4] = St::ld2(gs + 4 * P, k + W, float(rest_g(4)));
-    const F2 t0 = tau_start<TAU, F2, FIELD>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tsrc + k)); });
+    f[0] = St::ldd2(fs, k, float(rest_f(0)));
+    f[1] = from_left(St::ldd2(fs + P, k, float(rest_f(1))), l0 ? St::ldd(fs + P, k - 1, float(rest_f(1))) : 0.f, lane);
+    f[2] = St::ldd2(fs + 2 * P, k - W, float(rest_f(2)));
+    f[3] = from_right(St::ldd2(fs + 3 * P, k, float(rest_f(3))), l31 ? St::ldd(fs + 3 * P, k + 2, float(rest_f(3))) : 0.f, lane);
+    f[4] = St::ldd2(fs + 4 * P, k + W, float(rest_f(4)));
+    f[5] = from_left(St::ldd2(fs + 5 * P, k - W, float(rest_f(5))),
+                     l0 ? St::ldd(fs + 5 * P, k - W - 1, float(rest_f(5))) : 0.f, lane);
+    f[6] = from_right(St::ldd2(fs + 6 * P, k - W, float(rest_f(6))),
+                      l31 ? St::ldd(fs + 6 * P, k - W + 2, float(rest_f(6))) : 0.f, lane);
+    f[7] = from_right(St::ldd2(fs + 7 * P, k + W, float(rest_f(7))),
+                      l31 ? St::ldd(fs + 7 * P, k + W + 2, float(rest_f(7))) : 0.f, lane);
+    f[8] = from_left(St::ldd2(fs + 8 * P, k + W, float(rest_f(8))),
+                     l0 ? St::ldd(fs + 8 * P, k + W - 1, float(rest_f(8))) : 0.f, lane);
+    g[0] = St::ldd2(gs, k, float(rest_g(0)));
+    g[1] = from_left(St::ldd2(gs + P, k, float(rest_g(1))), l0 ? St::ldd(gs + P, k - 1, float(rest_g(1))) : 0.f, lane);
+    g[2] = St::ldd2(gs + 2 * P, k - W, float(rest_g(2)));
+    g[3] = from_right(St::ldd2(gs + 3 * P, k, float(rest_g(3))), l31 ? St::ldd(gs + 3 * P, k + 2, float(rest_g(3))) : 0.f, lane);
+    g[4] = St::ldd2(gs + 4 * P, k + W, float(rest_g(4)));
+    const F2 t0 = tau_start<TAU, F2, FIELD, 1>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tsrc + k)); });
     Macro<F2> m;
-    const F2 tau = collide<F2, FIELD>(p2, f, g, t0, m, k);
+    const F2 tau = collide<F2, FIELD, 1>(p2, f, g, t0, m, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::st2(dst + i * P, k, f[i], float(rest_f(i)), p.seed);
+    for (int i = 0; i < 9; i++) St::sdv2(dst + i * P, k, f[i], float(rest_f(i)), p.seed);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::st2(dst + (9 + i) * P, k, g[i], float(rest_g(i)), p.seed);
+    for (int i = 0; i < 5; i++) St::sdv2(dst + (9 + i) * P, k, g[i], float(rest_g(i)), p.seed);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tdst + k) = tau.v;
 }
 

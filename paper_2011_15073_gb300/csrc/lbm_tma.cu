@@ -145,37 +145,37 @@ __device__ __forceinline__ void tma_tile_fast(const unsigned char *stage, typena
 #pragma unroll
     for (int q = 0; q < 14; ++q) r[q] = reinterpret_cast<const S *>(stage + q * G::ROW_BYTES);
     auto pair_l = [&](int q, float rest) {   // nodes' left neighbours (x - 1, x)
-        return F2(St::ld(r[q], j - 1, rest), St::ld(r[q], j, rest));
+        return F2(St::ldd(r[q], j - 1, rest), St::ldd(r[q], j, rest));
     };
     auto pair_r = [&](int q, float rest) {   // right neighbours (x + 1, x + 2)
-        return F2(St::ld(r[q], j + 1, rest), St::ld(r[q], j + 2, rest));
+        return F2(St::ldd(r[q], j + 1, rest), St::ldd(r[q], j + 2, rest));
     };
     F2 f[9], g[5];
-    f[0] = St::ld2(r[0], j, float(rest_f(0)));
+    f[0] = St::ldd2(r[0], j, float(rest_f(0)));
     f[1] = pair_l(1, float(rest_f(1)));
-    f[2] = St::ld2(r[2], j, float(rest_f(2)));
+    f[2] = St::ldd2(r[2], j, float(rest_f(2)));
     f[3] = pair_r(3, float(rest_f(3)));
-    f[4] = St::ld2(r[4], j, float(rest_f(4)));
+    f[4] = St::ldd2(r[4], j, float(rest_f(4)));
     f[5] = pair_l(5, float(rest_f(5)));
     f[6] = pair_r(6, float(rest_f(6)));
     f[7] = pair_r(7, float(rest_f(7)));
     f[8] = pair_l(8, float(rest_f(8)));
-    g[0] = St::ld2(r[9], j, float(rest_g(0)));
+    g[0] = St::ldd2(r[9], j, float(rest_g(0)));
     g[1] = pair_l(10, float(rest_g(1)));
-    g[2] = St::ld2(r[11], j, float(rest_g(2)));
+    g[2] = St::ldd2(r[11], j, float(rest_g(2)));
     g[3] = pair_r(12, float(rest_g(3)));
-    g[4] = St::ld2(r[13], j, float(rest_g(4)));
+    g[4] = St::ldd2(r[13], j, float(rest_g(4)));
     const float *trow = reinterpret_cast<const float *>(stage + 14 * G::ROW_BYTES);
-    const F2 t0 = tau_start<TAU, F2, FIELD>(p2, f, g, k, [&] {
+    const F2 t0 = tau_start<TAU, F2, FIELD, 1>(p2, f, g, k, [&] {
         return F2(*reinterpret_cast<const float2 *>(trow + (j - G::HALO)));
     });
     Macro<F2> m;
-    const F2 tau = collide<F2, FIELD>(p2, f, g, t0, m, k);
+    const F2 tau = collide<F2, FIELD, 1>(p2, f, g, t0, m, k);
     const int64_t P = p2.plane;
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::st2(dst + i * P, k, f[i], float(rest_f(i)), p2.seed);
+    for (int i = 0; i < 9; i++) St::sdv2(dst + i * P, k, f[i], float(rest_f(i)), p2.seed);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::st2(dst + (9 + i) * P, k, g[i], float(rest_g(i)), p2.seed);
+    for (int i = 0; i < 5; i++) St::sdv2(dst + (9 + i) * P, k, g[i], float(rest_g(i)), p2.seed);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tdst + k) = tau.v;
 }
 
