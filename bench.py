@@ -34,6 +34,9 @@ sys.path.insert(0, ROOT)
 BYTES_PER_NODE = {"f64": 240, "f32": 120, "f32d": 120, "bf16d": 64, "f16d": 64, "f16s": 64, "bf16s": 64}
 # bytes of the stored lagged tau in those figures (read + write); the
 # node-local implicit tau (tau_iters > 0) moves none
+STORAGE_NAMES = {"f64": "FP64", "f32": "FP32", "f32d": "FP32 deviation-from-rest", "bf16d": "BF16 deviation",
+                 "f16d": "FP16 deviation", "f16s": "FP16 deviation (x2^15, stochastic rounding)",
+                 "bf16s": "BF16 deviation (stochastic rounding)"}
 TAU_BYTES = {"f64": 16, "f32": 8, "f32d": 8, "bf16d": 8, "f16d": 8, "f16s": 8, "bf16s": 8}
 
 
@@ -109,7 +112,8 @@ def parse():
     ap.add_argument("--delta", type=int, default=1000,
                     help="fused time steps per bench step (the convergence-check interval)")
     ap.add_argument("--variant-delta", type=int, default=200)
-    ap.add_argument("--prec", default="f32")
+    ap.add_argument("--prec", default="f32d",
+                    help="storage of the headline run (f32d: FP32 deviations from the rest state)")
     ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2],
                     help="step-kernel inputs: 0 auto, 1 straight to registers, 2 bulk copies to shared memory")
     ap.add_argument("--tau-iters", type=int, default=0,
@@ -393,7 +397,7 @@ def study_tables(args):
                           "seconds": time.perf_counter() - t}), flush=True)
 
 
-DEFAULT_VARIANTS = "f64,f32d,f32@aa,f32@tau2,f32@tma,bf16d,f16d,f16s,bf16s,f16s@tau2"
+DEFAULT_VARIANTS = "f64,f32,f32d@aa,f32d@tau2,f32d@tma,bf16d,f16d,f16s,bf16s,f16s@tau2"
 PRECISION_VARIANTS = ("f64", "f64@tau4", "f32", "f32@tau2", "f32d", "f16d", "bf16d", "f16s", "bf16s")
 
 
@@ -652,10 +656,11 @@ def main():
     line = {
         "metric": "fused MRT step MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == "f64" else "f32",
         "data": "synthetic",
         "config": {"workload": f"cavity {N}x{N}, n={CASE['n']}, Da={CASE['Da']}, Ra={CASE['Ra']}, "
-                               f"Pr={CASE['Pr']}, porosity={CASE['porosity']}, {prec} storage, "
+                               f"Pr={CASE['Pr']}, porosity={CASE['porosity']}, {STORAGE_NAMES[prec]} storage, "
                                + (f"implicit tau ({args.tau_iters} Newton steps)" if args.tau_iters
                                   else "lagged tau") +
                                f"; bench step = {delta} fused steps + Nu + residual",

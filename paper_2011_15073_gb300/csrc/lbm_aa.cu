@@ -31,22 +31,23 @@ __device__ __forceinline__ void push(typename Store<PREC>::S *__restrict__ A, co
     const int64_t P = p.plane, W = p.pitch;
     const int64_t k = (int64_t)y * W + x;
     const bool xl = x > 0, xr = x < p.nx - 1, yb = y > 0, yt = y < p.ny - 1;
+    uint32_t rng = rng_init(p.seed, k);   // random bits of the stochastic-rounding storages
     // target x + e_i: e1 (1,0) e2 (0,1) e3 (-1,0) e4 (0,-1) e5 (1,1) e6 (-1,1) e7 (-1,-1) e8 (1,-1)
-    St::sdv(A, 0 * P + k, f[0], R(rest_f(0)), p.seed);
-    if (xr) St::sdv(A, 1 * P + k + 1, f[1], R(rest_f(1)), p.seed); else St::sdv(A, 3 * P + k, f[1], R(rest_f(3)), p.seed);
-    if (yt) St::sdv(A, 2 * P + k + W, f[2], R(rest_f(2)), p.seed); else St::sdv(A, 4 * P + k, f[2], R(rest_f(4)), p.seed);
-    if (xl) St::sdv(A, 3 * P + k - 1, f[3], R(rest_f(3)), p.seed); else St::sdv(A, 1 * P + k, f[3], R(rest_f(1)), p.seed);
-    if (yb) St::sdv(A, 4 * P + k - W, f[4], R(rest_f(4)), p.seed); else St::sdv(A, 2 * P + k, f[4], R(rest_f(2)), p.seed);
-    if (xr && yt) St::sdv(A, 5 * P + k + W + 1, f[5], R(rest_f(5)), p.seed); else St::sdv(A, 7 * P + k, f[5], R(rest_f(7)), p.seed);
-    if (xl && yt) St::sdv(A, 6 * P + k + W - 1, f[6], R(rest_f(6)), p.seed); else St::sdv(A, 8 * P + k, f[6], R(rest_f(8)), p.seed);
-    if (xl && yb) St::sdv(A, 7 * P + k - W - 1, f[7], R(rest_f(7)), p.seed); else St::sdv(A, 5 * P + k, f[7], R(rest_f(5)), p.seed);
-    if (xr && yb) St::sdv(A, 8 * P + k - W + 1, f[8], R(rest_f(8)), p.seed); else St::sdv(A, 6 * P + k, f[8], R(rest_f(6)), p.seed);
+    St::sdv(A, 0 * P + k, f[0], R(rest_f(0)), rng);
+    if (xr) St::sdv(A, 1 * P + k + 1, f[1], R(rest_f(1)), rng); else St::sdv(A, 3 * P + k, f[1], R(rest_f(3)), rng);
+    if (yt) St::sdv(A, 2 * P + k + W, f[2], R(rest_f(2)), rng); else St::sdv(A, 4 * P + k, f[2], R(rest_f(4)), rng);
+    if (xl) St::sdv(A, 3 * P + k - 1, f[3], R(rest_f(3)), rng); else St::sdv(A, 1 * P + k, f[3], R(rest_f(1)), rng);
+    if (yb) St::sdv(A, 4 * P + k - W, f[4], R(rest_f(4)), rng); else St::sdv(A, 2 * P + k, f[4], R(rest_f(2)), rng);
+    if (xr && yt) St::sdv(A, 5 * P + k + W + 1, f[5], R(rest_f(5)), rng); else St::sdv(A, 7 * P + k, f[5], R(rest_f(7)), rng);
+    if (xl && yt) St::sdv(A, 6 * P + k + W - 1, f[6], R(rest_f(6)), rng); else St::sdv(A, 8 * P + k, f[6], R(rest_f(8)), rng);
+    if (xl && yb) St::sdv(A, 7 * P + k - W - 1, f[7], R(rest_f(7)), rng); else St::sdv(A, 5 * P + k, f[7], R(rest_f(5)), rng);
+    if (xr && yb) St::sdv(A, 8 * P + k - W + 1, f[8], R(rest_f(8)), rng); else St::sdv(A, 6 * P + k, f[8], R(rest_f(6)), rng);
     typename Store<PREC>::S *G = A + 9 * P;
-    St::sdv(G, 0 * P + k, g[0], R(rest_g(0)), p.seed);
-    if (xr) St::sdv(G, 1 * P + k + 1, g[1], R(rest_g(1)), p.seed); else St::sdv(G, 3 * P + k, p.abbd_cold - g[1], R(rest_g(3)), p.seed);
-    if (yt) St::sdv(G, 2 * P + k + W, g[2], R(rest_g(2)), p.seed); else St::sdv(G, 4 * P + k, g[2], R(rest_g(4)), p.seed);
-    if (xl) St::sdv(G, 3 * P + k - 1, g[3], R(rest_g(3)), p.seed); else St::sdv(G, 1 * P + k, p.abbd_hot - g[3], R(rest_g(1)), p.seed);
-    if (yb) St::sdv(G, 4 * P + k - W, g[4], R(rest_g(4)), p.seed); else St::sdv(G, 2 * P + k, g[4], R(rest_g(2)), p.seed);
+    St::sdv(G, 0 * P + k, g[0], R(rest_g(0)), rng);
+    if (xr) St::sdv(G, 1 * P + k + 1, g[1], R(rest_g(1)), rng); else St::sdv(G, 3 * P + k, p.abbd_cold - g[1], R(rest_g(3)), rng);
+    if (yt) St::sdv(G, 2 * P + k + W, g[2], R(rest_g(2)), rng); else St::sdv(G, 4 * P + k, g[2], R(rest_g(4)), rng);
+    if (xl) St::sdv(G, 3 * P + k - 1, g[3], R(rest_g(3)), rng); else St::sdv(G, 1 * P + k, p.abbd_hot - g[3], R(rest_g(1)), rng);
+    if (yb) St::sdv(G, 4 * P + k - W, g[4], R(rest_g(4)), rng); else St::sdv(G, 2 * P + k, g[4], R(rest_g(2)), rng);
 }
 
 // ------------------------------------------------------- one node / thread
@@ -67,10 +68,11 @@ aa_even_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::Ta
     for (int i = 0; i < 5; i++) g[i] = St::ldd(A + 9 * P, i * P + k, R(rest_g(i)));
     Macro<R> m;
     const R t = collide<R, 2, 1>(p, f, g, tau_start<TAU, R, 2, 1>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
+    uint32_t rng = rng_init(p.seed, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::sdv(A, opp(i) * P + k, f[i], R(rest_f(opp(i))), p.seed);
+    for (int i = 0; i < 9; i++) St::sdv(A, opp(i) * P + k, f[i], R(rest_f(opp(i))), rng);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::sdv(A + 9 * P, opp(i) * P + k, g[i], R(rest_g(opp(i))), p.seed);
+    for (int i = 0; i < 5; i++) St::sdv(A + 9 * P, opp(i) * P + k, g[i], R(rest_g(opp(i))), rng);
     if constexpr (TAU == 0) tau[k] = typename St::TauS(t);
 }
 
@@ -114,8 +116,9 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
         Macro<float> m;
         const float t =
             collide<float, 2, 1>(p, f, g, tau_start<TAU, float, 2, 1>(p, f, g, k, [&] { return tau[k]; }), m, k);
-        for (int i = 0; i < 9; i++) St::sdv(A, opp(i) * P + k, f[i], float(rest_f(opp(i))), p.seed);
-        for (int i = 0; i < 5; i++) St::sdv(A + 9 * P, opp(i) * P + k, g[i], float(rest_g(opp(i))), p.seed);
+        uint32_t rng = rng_init(p.seed, k);
+        for (int i = 0; i < 9; i++) St::sdv(A, opp(i) * P + k, f[i], float(rest_f(opp(i))), rng);
+        for (int i = 0; i < 5; i++) St::sdv(A + 9 * P, opp(i) * P + k, g[i], float(rest_g(opp(i))), rng);
         if constexpr (TAU == 0) tau[k] = t;
         return;
     }
@@ -127,10 +130,11 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
     Macro<F2> m;
     const F2 t0 = tau_start<TAU, F2, 2, 1>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
     const F2 t = collide<F2, 2, 1>(p2, f, g, t0, m, k);
+    uint32_t rng = rng_init(p2.seed, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::sdv2(A + opp(i) * P, k, f[i], float(rest_f(opp(i))), p2.seed);
+    for (int i = 0; i < 9; i++) St::sdv2(A + opp(i) * P, k, f[i], float(rest_f(opp(i))), rng);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::sdv2(A + (9 + opp(i)) * P, k, g[i], float(rest_g(opp(i))), p2.seed);
+    for (int i = 0; i < 5; i++) St::sdv2(A + (9 + opp(i)) * P, k, g[i], float(rest_g(opp(i))), rng);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tau + k) = t.v;
 }
 
@@ -140,23 +144,23 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
 // to the neighbouring warp's pair on their own.
 template <int PREC>
 __device__ __forceinline__ void push_right(typename Store<PREC>::S *base, int64_t kr, F2 v, float rest, int lane,
-                                           uint32_t seed)
+                                           uint32_t &rng)
 {
     using St = Store<PREC>;
     const float prev = __shfl_up_sync(0xffffffffu, v.v.y, 1);
-    if (lane != 0) St::sdv2(base, kr, F2(prev, v.v.x), rest, seed);
-    else St::sdv(base, kr + 1, v.v.x, rest, seed);
-    if (lane == 31) St::sdv(base, kr + 2, v.v.y, rest, seed);
+    if (lane != 0) St::sdv2(base, kr, F2(prev, v.v.x), rest, rng);
+    else St::sdv(base, kr + 1, v.v.x, rest, rng);
+    if (lane == 31) St::sdv(base, kr + 2, v.v.y, rest, rng);
 }
 template <int PREC>
 __device__ __forceinline__ void push_left(typename Store<PREC>::S *base, int64_t kr, F2 v, float rest, int lane,
-                                          uint32_t seed)
+                                          uint32_t &rng)
 {
     using St = Store<PREC>;
     const float next = __shfl_down_sync(0xffffffffu, v.v.x, 1);
-    if (lane != 31) St::sdv2(base, kr, F2(v.v.y, next), rest, seed);
-    else St::sdv(base, kr, v.v.y, rest, seed);
-    if (lane == 0) St::sdv(base, kr - 1, v.v.x, rest, seed);
+    if (lane != 31) St::sdv2(base, kr, F2(v.v.y, next), rest, rng);
+    else St::sdv(base, kr, v.v.y, rest, rng);
+    if (lane == 0) St::sdv(base, kr - 1, v.v.x, rest, rng);
 }
 
 template <int PREC, int TAU>
@@ -202,21 +206,22 @@ aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau,
     Macro<F2> m;
     const F2 t0 = tau_start<TAU, F2, 2, 1>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
     const F2 t = collide<F2, 2, 1>(p2, f, g, t0, m, k);
+    uint32_t rng = rng_init(p2.seed, k);
     // push f*_i(x) into slot i of node x + e_i
-    St::sdv2(fs, k, f[0], float(rest_f(0)), p2.seed);
-    push_right<PREC>(fs + P, k, f[1], float(rest_f(1)), lane, p2.seed);
-    St::sdv2(fs + 2 * P, k + W, f[2], float(rest_f(2)), p2.seed);
-    push_left<PREC>(fs + 3 * P, k, f[3], float(rest_f(3)), lane, p2.seed);
-    St::sdv2(fs + 4 * P, k - W, f[4], float(rest_f(4)), p2.seed);
-    push_right<PREC>(fs + 5 * P, k + W, f[5], float(rest_f(5)), lane, p2.seed);
-    push_left<PREC>(fs + 6 * P, k + W, f[6], float(rest_f(6)), lane, p2.seed);
-    push_left<PREC>(fs + 7 * P, k - W, f[7], float(rest_f(7)), lane, p2.seed);
-    push_right<PREC>(fs + 8 * P, k - W, f[8], float(rest_f(8)), lane, p2.seed);
-    St::sdv2(gs, k, g[0], float(rest_g(0)), p2.seed);
-    push_right<PREC>(gs + P, k, g[1], float(rest_g(1)), lane, p2.seed);
-    St::sdv2(gs + 2 * P, k + W, g[2], float(rest_g(2)), p2.seed);
-    push_left<PREC>(gs + 3 * P, k, g[3], float(rest_g(3)), lane, p2.seed);
-    St::sdv2(gs + 4 * P, k - W, g[4], float(rest_g(4)), p2.seed);
+    St::sdv2(fs, k, f[0], float(rest_f(0)), rng);
+    push_right<PREC>(fs + P, k, f[1], float(rest_f(1)), lane, rng);
+    St::sdv2(fs + 2 * P, k + W, f[2], float(rest_f(2)), rng);
+    push_left<PREC>(fs + 3 * P, k, f[3], float(rest_f(3)), lane, rng);
+    St::sdv2(fs + 4 * P, k - W, f[4], float(rest_f(4)), rng);
+    push_right<PREC>(fs + 5 * P, k + W, f[5], float(rest_f(5)), lane, rng);
+    push_left<PREC>(fs + 6 * P, k + W, f[6], float(rest_f(6)), lane, rng);
+    push_left<PREC>(fs + 7 * P, k - W, f[7], float(rest_f(7)), lane, rng);
+    push_right<PREC>(fs + 8 * P, k - W, f[8], float(rest_f(8)), lane, rng);
+    St::sdv2(gs, k, g[0], float(rest_g(0)), rng);
+    push_right<PREC>(gs + P, k, g[1], float(rest_g(1)), lane, rng);
+    St::sdv2(gs + 2 * P, k + W, g[2], float(rest_g(2)), rng);
+    push_left<PREC>(gs + 3 * P, k, g[3], float(rest_g(3)), lane, rng);
+    St::sdv2(gs + 4 * P, k - W, g[4], float(rest_g(4)), rng);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tau + k) = t.v;
 }
 
@@ -249,8 +254,9 @@ aa_normalize_kernel(typename Store<PREC>::S *__restrict__ A, Phys<typename Store
     typename Store<PREC>::S *G = A + 9 * P;
     if (xr) swap(G, 1, k + 1, false);
     if (yt) swap(G, 2, k + W, false);
-    if (!xl) St::sdv(G, 1 * P + k, p.abbd_hot - St::ldd(G, 1 * P + k, R(rest_g(1))), R(rest_g(1)), p.seed);
-    if (!xr) St::sdv(G, 3 * P + k, p.abbd_cold - St::ldd(G, 3 * P + k, R(rest_g(3))), R(rest_g(3)), p.seed);
+    uint32_t rng = rng_init(p.seed, k);
+    if (!xl) St::sdv(G, 1 * P + k, p.abbd_hot - St::ldd(G, 1 * P + k, R(rest_g(1))), R(rest_g(1)), rng);
+    if (!xr) St::sdv(G, 3 * P + k, p.abbd_cold - St::ldd(G, 3 * P + k, R(rest_g(3))), R(rest_g(3)), rng);
 }
 
 // ------------------------------------------------------------- launchers

@@ -173,7 +173,7 @@ struct Store<LBM_F64> {
     static __device__ __forceinline__ R ld(const S *p, int64_t k, R) { return p[k]; }
     static __device__ __forceinline__ void st(S *p, int64_t k, R v, R, uint32_t = 0) { p[k] = v; }
     static __device__ __forceinline__ R ldd(const S *p, int64_t k, R rest) { return p[k] - rest; }
-    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R rest, uint32_t = 0) { p[k] = d + rest; }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R rest, uint32_t &) { p[k] = d + rest; }
 };
 template <>
 struct Store<LBM_F32> {
@@ -183,12 +183,12 @@ struct Store<LBM_F32> {
     static __device__ __forceinline__ R ld(const S *p, int64_t k, R) { return p[k]; }
     static __device__ __forceinline__ void st(S *p, int64_t k, R v, R, uint32_t = 0) { p[k] = v; }
     static __device__ __forceinline__ R ldd(const S *p, int64_t k, R rest) { return p[k] - rest; }
-    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R rest, uint32_t = 0) { p[k] = d + rest; }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R rest, uint32_t &) { p[k] = d + rest; }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float rest)
     {
         return F2(*reinterpret_cast<const float2 *>(p + k)) - F2(rest);
     }
-    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float rest, uint32_t = 0)
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float rest, uint32_t &)
     {
         *reinterpret_cast<float2 *>(p + k) = (d + F2(rest)).v;
     }
@@ -217,12 +217,12 @@ struct Store<LBM_F32D> {
         *reinterpret_cast<float2 *>(p + k) = (v - F2(rest)).v;
     }
     static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return p[k]; }
-    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t = 0) { p[k] = d; }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t &) { p[k] = d; }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
     {
         return F2(*reinterpret_cast<const float2 *>(p + k));
     }
-    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t = 0)
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &)
     {
         *reinterpret_cast<float2 *>(p + k) = d.v;
     }
@@ -250,12 +250,12 @@ struct Store<LBM_BF16D> {
         *reinterpret_cast<__nv_bfloat162 *>(p + k) = __float22bfloat162_rn((v - F2(rest)).v);
     }
     static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __bfloat162float(p[k]); }
-    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t = 0) { p[k] = __float2bfloat16_rn(d); }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t &) { p[k] = __float2bfloat16_rn(d); }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
     {
         return F2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p + k)));
     }
-    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t = 0)
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &)
     {
         *reinterpret_cast<__nv_bfloat162 *>(p + k) = __float22bfloat162_rn(d.v);
     }
@@ -283,53 +283,58 @@ struct Store<LBM_F16D> {
         *reinterpret_cast<__half2 *>(p + k) = __float22half2_rn((v - F2(rest)).v);
     }
     static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __half2float(p[k]); }
-    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t = 0) { p[k] = __float2half_rn(d); }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t &) { p[k] = __float2half_rn(d); }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
     {
         return F2(__half22float2(*reinterpret_cast<const __half2 *>(p + k)));
     }
-    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t = 0)
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &)
     {
         *reinterpret_cast<__half2 *>(p + k) = __float22half2_rn(d.v);
     }
 };
 
-// FP16 / BF16 deviation storage with stochastic rounding (lbm_round.cuh):
-// the random bits come from the step's seed and the element's address.
+// FP16 / BF16 deviation storage with stochastic rounding (lbm_round.cuh).
+// The FP16 form stores the deviation scaled by 2^15, which moves deviations
+// down to 2e-9 into the normal range of FP16 (and keeps |d| < 2 finite): a
+// custom 16-bit format with the exponent range shifted to where the
+// deviations live.  The kernels' stores draw their random bits from a
+// per-thread stream (`rng`: rng_init() of the step's seed and the node, then
+// one xorshift32 step per stored pair); import and export use the
+// element's address instead.
+constexpr float F16S_SCALE = 32768.0f, F16S_ISCALE = 1.0f / 32768.0f;
 template <>
 struct Store<LBM_F16S> {
     using S = __half;
     using R = float;
     using TauS = float;
-    static __device__ __forceinline__ R ld(const S *p, int64_t k, R rest) { return rest + __half2float(p[k]); }
+    static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __half2float(p[k]) * F16S_ISCALE; }
+    static __device__ __forceinline__ R ld(const S *p, int64_t k, R rest) { return rest + ldd(p, k, rest); }
     static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest, uint32_t seed = 0)
     {
-        p[k] = sr_half(v - rest, sr_bits(seed, p + k) >> 16);
-    }
-    static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float rest)
-    {
-        const __half2 h = *reinterpret_cast<const __half2 *>(p + k);
-        return F2(__half22float2(h)) + F2(rest);
-    }
-    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest, uint32_t seed = 0)
-    {
-        const uint32_t r = sr_bits(seed, p + k);
-        const F2 d = v - F2(rest);
-        *reinterpret_cast<__half2 *>(p + k) = __halves2half2(sr_half(d.v.x, r & 0xffffu), sr_half(d.v.y, r >> 16));
-    }
-    static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __half2float(p[k]); }
-    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t seed = 0)
-    {
-        p[k] = sr_half(d, sr_bits(seed, p + k) >> 16);
+        p[k] = sr_half((v - rest) * F16S_SCALE, sr_bits(seed, p + k) >> 16);
     }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
     {
-        return F2(__half22float2(*reinterpret_cast<const __half2 *>(p + k)));
+        return F2(__half22float2(*reinterpret_cast<const __half2 *>(p + k))) * F2(F16S_ISCALE);
     }
-    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t seed = 0)
+    static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float rest) { return ldd2(p, k, rest) + F2(rest); }
+    static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest, uint32_t seed = 0)
     {
         const uint32_t r = sr_bits(seed, p + k);
+        const F2 d = (v - F2(rest)) * F2(F16S_SCALE);
         *reinterpret_cast<__half2 *>(p + k) = __halves2half2(sr_half(d.v.x, r & 0xffffu), sr_half(d.v.y, r >> 16));
+    }
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t &rng)
+    {
+        rng = xorshift32(rng);
+        p[k] = sr_half(d * F16S_SCALE, rng >> 16);
+    }
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &rng)
+    {
+        rng = xorshift32(rng);
+        const F2 ds = d * F2(F16S_SCALE);
+        *reinterpret_cast<__half2 *>(p + k) = __halves2half2(sr_half(ds.v.x, rng & 0xffffu), sr_half(ds.v.y, rng >> 16));
     }
 };
 template <>
@@ -358,19 +363,20 @@ struct Store<LBM_BF16S> {
             __halves2bfloat162(sr_bf16(d.v.x, r & 0xffffu), sr_bf16(d.v.y, r >> 16));
     }
     static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __bfloat162float(p[k]); }
-    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t seed = 0)
+    static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t &rng)
     {
-        p[k] = sr_bf16(d, sr_bits(seed, p + k) >> 16);
+        rng = xorshift32(rng);
+        p[k] = sr_bf16(d, rng >> 16);
     }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
     {
         return F2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p + k)));
     }
-    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t seed = 0)
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &rng)
     {
-        const uint32_t r = sr_bits(seed, p + k);
+        rng = xorshift32(rng);
         *reinterpret_cast<__nv_bfloat162 *>(p + k) =
-            __halves2bfloat162(sr_bf16(d.v.x, r & 0xffffu), sr_bf16(d.v.y, r >> 16));
+            __halves2bfloat162(sr_bf16(d.v.x, rng & 0xffffu), sr_bf16(d.v.y, rng >> 16));
     }
 };
 

@@ -60,6 +60,23 @@ __host__ __device__ __forceinline__ float u2f(uint32_t u)
 #endif
 }
 
+// Marsaglia's xorshift32 (J. Stat. Softw. 8(14), 2003), shifts 13, 17, 5:
+// the per-thread stream of random bits between hashed seeds.
+__host__ __device__ __forceinline__ uint32_t xorshift32(uint32_t x)
+{
+    x ^= x << 13;
+    x ^= x >> 17;
+    x ^= x << 5;
+    return x;
+}
+
+// Start of a thread's stream for the node at plane offset k in the launch
+// with seed `seed` (never 0, which xorshift32 would keep).
+__host__ __device__ __forceinline__ uint32_t rng_init(uint32_t seed, int64_t k)
+{
+    return mix32(seed ^ (uint32_t)k ^ (uint32_t)((uint64_t)k >> 32) * 0x9e3779b9u) | 1u;
+}
+
 // FP32 -> FP16 with stochastic rounding, r16 = 16 random bits.
 // * Half normals (|x| >= 2^-14): the FP32 bits below the half's last place
 //   are the low 13 mantissa bits; adding a uniform integer in [0, 2^13) to

@@ -27,10 +27,11 @@ __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restr
     Macro<R> m;
     const R t0 = tau_start<TAU, R, FIELD, 1>(p, f, g, k, [&] { return R(tsrc[k]); });
     const R tau = collide<R, FIELD, 1>(p, f, g, t0, m, k);
+    uint32_t rng = rng_init(p.seed, k);   // random bits of the stochastic-rounding storages
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::sdv(dst, i * p.plane + k, f[i], R(rest_f(i)), p.seed);
+    for (int i = 0; i < 9; i++) St::sdv(dst, i * p.plane + k, f[i], R(rest_f(i)), rng);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::sdv(dst + 9 * p.plane, i * p.plane + k, g[i], R(rest_g(i)), p.seed);
+    for (int i = 0; i < 5; i++) St::sdv(dst + 9 * p.plane, i * p.plane + k, g[i], R(rest_g(i)), rng);
     if constexpr (TAU == 0) tdst[k] = typename St::TauS(tau);
 }
 
@@ -85,10 +86,11 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
     const F2 t0 = tau_start<TAU, F2, FIELD, 1>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tsrc + k)); });
     Macro<F2> m;
     const F2 tau = collide<F2, FIELD, 1>(p2, f, g, t0, m, k);
+    uint32_t rng = rng_init(p.seed, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::sdv2(dst + i * P, k, f[i], float(rest_f(i)), p.seed);
+    for (int i = 0; i < 9; i++) St::sdv2(dst + i * P, k, f[i], float(rest_f(i)), rng);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::sdv2(dst + (9 + i) * P, k, g[i], float(rest_g(i)), p.seed);
+    for (int i = 0; i < 5; i++) St::sdv2(dst + (9 + i) * P, k, g[i], float(rest_g(i)), rng);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tdst + k) = tau.v;
 }
 

@@ -172,10 +172,11 @@ __device__ __forceinline__ void tma_tile_fast(const unsigned char *stage, typena
     Macro<F2> m;
     const F2 tau = collide<F2, FIELD, 1>(p2, f, g, t0, m, k);
     const int64_t P = p2.plane;
+    uint32_t rng = rng_init(p2.seed, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::sdv2(dst + i * P, k, f[i], float(rest_f(i)), p2.seed);
+    for (int i = 0; i < 9; i++) St::sdv2(dst + i * P, k, f[i], float(rest_f(i)), rng);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::sdv2(dst + (9 + i) * P, k, g[i], float(rest_g(i)), p2.seed);
+    for (int i = 0; i < 5; i++) St::sdv2(dst + (9 + i) * P, k, g[i], float(rest_g(i)), rng);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tdst + k) = tau.v;
 }
 
