@@ -49,8 +49,8 @@ def parse_variant(v):
             layout = 1
         elif m.startswith("tau") and m[3:].isdigit():
             tau_iters = int(m[3:])
-        elif m in ("tma", "reg"):
-            staging = 2 if m == "tma" else 1
+        elif m in ("tma", "reg", "rows"):
+            staging = {"reg": 1, "tma": 2, "rows": 3}[m]
         else:
             raise ValueError(f"unknown variant modifier {m!r} in {v!r}")
     return parts[0], layout, tau_iters, staging
@@ -114,8 +114,9 @@ def parse():
     ap.add_argument("--variant-delta", type=int, default=200)
     ap.add_argument("--prec", default="f32d",
                     help="storage of the headline run (f32d: FP32 deviations from the rest state)")
-    ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2],
-                    help="step-kernel inputs: 0 auto, 1 straight to registers, 2 bulk copies to shared memory")
+    ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="step-kernel inputs: 0 auto, 1 straight to registers, 2 bulk copies to shared memory, "
+                         "3 per-warp async row pipeline (16-bit storages)")
     ap.add_argument("--tau-iters", type=int, default=0,
                     help="0: lagged tau (stored per node); K > 0: node-local implicit tau, K Newton steps")
     ap.add_argument("--variants", default=DEFAULT_VARIANTS,
@@ -397,7 +398,8 @@ def study_tables(args):
                           "seconds": time.perf_counter() - t}), flush=True)
 
 
-DEFAULT_VARIANTS = "f64,f32,f32d@aa,f32d@tau2,f32d@tma,bf16d,f16d,f16s,bf16s,f16s@tau2"
+DEFAULT_VARIANTS = ("f64,f32,f32d@aa,f32d@tau2,f32d@tma,bf16d,f16d,f16s,bf16s,f16s@tau2,"
+                    "f16d@rows,f16s@rows,bf16s@rows,f16s@tau2@rows")
 PRECISION_VARIANTS = ("f64", "f64@tau4", "f32", "f32@tau2", "f32d", "f16d", "bf16d", "f16s", "bf16s")
 
 
@@ -619,7 +621,8 @@ def main():
     peak, peak_src = hbm_peak()
     bpn_main = bytes_per_node(prec, args.tau_iters)
     achieved = bpn_main * N * N / kern / 1e9
-    key_main = prec + (f"@tau{args.tau_iters}" if args.tau_iters else "") + ("@tma" if args.staging == 2 else "")
+    key_main = prec + (f"@tau{args.tau_iters}" if args.tau_iters else "") + \
+        {0: "", 1: "@reg", 2: "@tma", 3: "@rows"}[args.staging]
     variants = {}
     for v in [p for p in args.variants.split(",") if p and p != key_main]:
         vs, vd = 2, args.variant_delta
@@ -632,7 +635,8 @@ def main():
                        "bytes_per_node": bpn, "achieved_GBs": av, "frac_of_hbm": av / peak,
                        "layout": "aa (in place)" if vl else "ab (two buffers)",
                        "tau": f"implicit, {vt} Newton steps" if vt else "lagged (stored)",
-                       "staging": {0: "auto", 1: "registers", 2: "bulk copies to shared memory"}[vg],
+                       "staging": {0: "auto", 1: "registers", 2: "bulk copies to shared memory",
+                                   3: "per-warp async row pipeline"}[vg],
                        "nu_hot": nuv}
         if v == "f64":
             ipn = recorded("f64_fp64_inst_per_node")
@@ -670,7 +674,7 @@ def main():
                      "frac": achieved / peak, "traffic": recorded_traffic(key_main, N),
                      "peak_source": peak_src,
                      "kernel": ("step_kernel" if prec == "f64" else "step_tma_kernel" if args.staging == 2
-                                else "step2_kernel") + f"<{key_main}>",
+                                else "step_rows_kernel" if args.staging == 3 else "step2_kernel") + f"<{key_main}>",
                      "bytes_per_node": bpn_main, "avg_launch_us": kern * 1e6},
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -105,10 +105,12 @@ typedef struct {
     int staging;       /* how the step kernel of the two-buffer layout
                           gets its inputs: 1 straight into registers;
                           2 staged in shared memory by bulk
-                          asynchronous copies, a tile ahead (FP32,
-                          FP32D, BF16D, F16D; LBM_ERR_UNSUPPORTED for
-                          F64); 0 the faster of the two for the
-                          storage and tau scheme                     [0]    */
+                          asynchronous copies, a tile ahead (not for
+                          F64); 3 into registers with the next row's
+                          loads issued before the current row's
+                          arithmetic (16-bit storages only); others
+                          get LBM_ERR_UNSUPPORTED; 0 the fastest
+                          for the storage                            [0]    */
 } lbm_opts;
 
 /* Lattice-unit parameters the library derived from the problem groups

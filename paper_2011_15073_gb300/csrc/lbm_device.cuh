@@ -259,6 +259,12 @@ struct Store<LBM_BF16D> {
     {
         *reinterpret_cast<__nv_bfloat162 *>(p + k) = __float22bfloat162_rn(d.v);
     }
+    // raw 16-bit words (as loaded) -> deviations
+    static __device__ __forceinline__ F2 dec2(uint32_t w)
+    {
+        return F2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+    static __device__ __forceinline__ float dec1(unsigned short h) { return __uint_as_float((uint32_t)h << 16); }
 };
 template <>
 struct Store<LBM_F16D> {
@@ -292,13 +298,24 @@ struct Store<LBM_F16D> {
     {
         *reinterpret_cast<__half2 *>(p + k) = __float22half2_rn(d.v);
     }
+    // raw 16-bit words (as loaded) -> deviations
+    static __device__ __forceinline__ F2 dec2(uint32_t w)
+    {
+        return F2(__half22float2(*reinterpret_cast<const __half2 *>(&w)));
+    }
+    static __device__ __forceinline__ float dec1(unsigned short h)
+    {
+        return __half2float(*reinterpret_cast<const __half *>(&h));
+    }
 };
 
 // FP16 / BF16 deviation storage with stochastic rounding (lbm_round.cuh).
 // The FP16 form stores the deviation scaled by 2^15, which moves deviations
 // down to 2e-9 into the normal range of FP16 (and keeps |d| < 2 finite): a
 // custom 16-bit format with the exponent range shifted to where the
-// deviations live.  The kernels' stores draw their random bits from a
+// deviations live.  Its rounding is sr_half_normal: below 2e-9 (scaled
+// 2^-14) values are truncated toward zero, a bias under 2e-12 in deviation
+// units, far below FP32's resolution of the populations themselves.  The kernels' stores draw their random bits from a
 // per-thread stream (`rng`: rng_init() of the step's seed and the node, then
 // one xorshift32 step per stored pair); import and export use the
 // element's address instead.
@@ -312,7 +329,7 @@ struct Store<LBM_F16S> {
     static __device__ __forceinline__ R ld(const S *p, int64_t k, R rest) { return rest + ldd(p, k, rest); }
     static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest, uint32_t seed = 0)
     {
-        p[k] = sr_half((v - rest) * F16S_SCALE, sr_bits(seed, p + k) >> 16);
+        p[k] = sr_half_normal((v - rest) * F16S_SCALE, sr_bits(seed, p + k) >> 16);
     }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
     {
@@ -323,18 +340,27 @@ struct Store<LBM_F16S> {
     {
         const uint32_t r = sr_bits(seed, p + k);
         const F2 d = (v - F2(rest)) * F2(F16S_SCALE);
-        *reinterpret_cast<__half2 *>(p + k) = __halves2half2(sr_half(d.v.x, r & 0xffffu), sr_half(d.v.y, r >> 16));
+        *reinterpret_cast<__half2 *>(p + k) = __halves2half2(sr_half_normal(d.v.x, r & 0xffffu), sr_half_normal(d.v.y, r >> 16));
     }
     static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t &rng)
     {
         rng = xorshift32(rng);
-        p[k] = sr_half(d * F16S_SCALE, rng >> 16);
+        p[k] = sr_half_normal(d * F16S_SCALE, rng >> 16);
     }
     static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &rng)
     {
         rng = xorshift32(rng);
         const F2 ds = d * F2(F16S_SCALE);
-        *reinterpret_cast<__half2 *>(p + k) = __halves2half2(sr_half(ds.v.x, rng & 0xffffu), sr_half(ds.v.y, rng >> 16));
+        *reinterpret_cast<__half2 *>(p + k) = __halves2half2(sr_half_normal(ds.v.x, rng & 0xffffu), sr_half_normal(ds.v.y, rng >> 16));
+    }
+    // raw 16-bit words (as loaded) -> deviations
+    static __device__ __forceinline__ F2 dec2(uint32_t w)
+    {
+        return F2(__half22float2(*reinterpret_cast<const __half2 *>(&w))) * F2(F16S_ISCALE);
+    }
+    static __device__ __forceinline__ float dec1(unsigned short h)
+    {
+        return __half2float(*reinterpret_cast<const __half *>(&h)) * F16S_ISCALE;
     }
 };
 template <>
@@ -378,6 +404,12 @@ struct Store<LBM_BF16S> {
         *reinterpret_cast<__nv_bfloat162 *>(p + k) =
             __halves2bfloat162(sr_bf16(d.v.x, rng & 0xffffu), sr_bf16(d.v.y, rng >> 16));
     }
+    // raw 16-bit words (as loaded) -> deviations
+    static __device__ __forceinline__ F2 dec2(uint32_t w)
+    {
+        return F2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+    static __device__ __forceinline__ float dec1(unsigned short h) { return __uint_as_float((uint32_t)h << 16); }
 };
 
 // ----------------------------------------------------------- pull streaming

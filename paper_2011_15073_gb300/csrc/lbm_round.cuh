@@ -103,6 +103,16 @@ __host__ __device__ __forceinline__ __half sr_half(float x, uint32_t r16)
     return __float2half_rz(u2f(b));
 }
 
+// The half-normal branch alone, for the scaled FP16 storage whose values
+// sit in the normal range: one integer add and one conversion.  Magnitudes
+// below 2^-14 (FP16's smallest normal) are then truncated toward zero on the
+// subnormal grid instead of rounded stochastically: the result is still one
+// of the two neighbours, biased toward zero by less than one spacing, 2^-24.
+__host__ __device__ __forceinline__ __half sr_half_normal(float x, uint32_t r16)
+{
+    return __float2half_rz(u2f(f2u(x) + ((r16 & 0xffffu) >> 3)));
+}
+
 // FP32 -> BF16 with stochastic rounding: BF16 keeps the top 16 bits of the
 // FP32 pattern, so the dither is the 16 random bits themselves (FP32
 // subnormals are not stored: |deviation| >= 2^-126 or 0 in practice).

@@ -34,13 +34,17 @@ static float bf16_next_away(__nv_bfloat16 h)
     return __bfloat162float(n);
 }
 
-static int check(float x, bool half)
+// kind 0: sr_half, 1: sr_bf16, 2: sr_half_normal (unbiased only for
+// |x| >= 2^-14; below, biased toward zero by less than one spacing)
+static int check_kind(float x, int kind)
 {
+    const bool half = kind != 1;
     const float lo = half ? __half2float(__float2half_rz(x)) : __bfloat162float(__float2bfloat16_rz(x));
     const float hi = half ? half_next_away(__float2half_rz(x)) : bf16_next_away(__float2bfloat16_rz(x));
     double sum = 0.0;
     for (uint32_t r = 0; r < 65536u; ++r) {
-        const float v = half ? __half2float(sr_half(x, r)) : __bfloat162float(sr_bf16(x, r));
+        const float v = kind == 0 ? __half2float(sr_half(x, r))
+                                  : kind == 1 ? __bfloat162float(sr_bf16(x, r)) : __half2float(sr_half_normal(x, r));
         if (lo == x ? v != x : (v != lo && v != hi)) {
             printf("FAIL bracket %s x=%.9g r=%u v=%.9g lo=%.9g hi=%.9g\n", half ? "half" : "bf16", x, r, v, lo, hi);
             return 1;
@@ -48,13 +52,16 @@ static int check(float x, bool half)
         sum += v;
     }
     const double mean = sum / 65536.0;
-    const double tol = fabs((double)hi - (double)lo) * (1.0 / 4096.0);
+    const bool sub = kind == 2 && fabs(x) < 6.103515625e-05;
+    const double tol = fabs((double)hi - (double)lo) * (sub ? 1.0 : 1.0 / 4096.0);
     if (fabs(mean - (double)x) > tol) {
         printf("FAIL mean %s x=%.9g mean=%.12g tol=%.3g\n", half ? "half" : "bf16", x, mean, tol);
         return 1;
     }
     return 0;
 }
+
+static int check(float x, bool half) { return half ? check_kind(x, 0) + check_kind(x, 2) : check_kind(x, 1); }
 
 int main()
 {
