@@ -49,8 +49,8 @@ def parse_variant(v):
             layout = 1
         elif m.startswith("tau") and m[3:].isdigit():
             tau_iters = int(m[3:])
-        elif m in ("tma", "reg", "rows"):
-            staging = {"reg": 1, "tma": 2, "rows": 3}[m]
+        elif m in ("tma", "reg"):
+            staging = {"reg": 1, "tma": 2}[m]
         else:
             raise ValueError(f"unknown variant modifier {m!r} in {v!r}")
     return parts[0], layout, tau_iters, staging
@@ -61,6 +61,7 @@ def bytes_per_node(prec, tau_iters=0):
 CASE = dict(n=0.6, Da=1e-3, Ra=1e5, Pr=6.2, porosity=0.6)
 FALLBACK_HBM_GBS = 6800.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+PRECISION_FILE = os.path.join(ROOT, "profiles", "precision_study_256.txt")
 
 
 def kernel_source_hash():
@@ -75,12 +76,12 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded(key, N=None):
-    """A figure from the committed ncu summary ``profiles/traffic.txt``
-    (lines: key N value source_hash), or None if absent or taken from other
-    CUDA sources.  N=None accepts any grid size."""
+def recorded(key, N=None, path=None):
+    """A figure from a committed measurement summary (default
+    ``profiles/traffic.txt``; lines: key N value source_hash), or None if
+    absent or taken from other CUDA sources.  N=None accepts any grid size."""
     try:
-        with open(TRAFFIC_FILE) as fh:
+        with open(path or TRAFFIC_FILE) as fh:
             for line in fh:
                 parts = line.split()
                 if len(parts) == 4 and not line.startswith("#") and parts[0] == key and \
@@ -90,6 +91,13 @@ def recorded(key, N=None):
     except OSError:
         pass
     return None
+
+
+def recorded_dnu(storage):
+    """Largest |relative Nu difference| to FP64 storage at steady state over
+    the precision study's cases (256^2, n = 0.6 and 1.0; mean of the last 20
+    samples) for this storage, from ``profiles/precision_study_256.txt``."""
+    return recorded(storage, None, PRECISION_FILE)
 
 
 def recorded_traffic(prec, N):
@@ -114,9 +122,8 @@ def parse():
     ap.add_argument("--variant-delta", type=int, default=200)
     ap.add_argument("--prec", default="f32d",
                     help="storage of the headline run (f32d: FP32 deviations from the rest state)")
-    ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="step-kernel inputs: 0 auto, 1 straight to registers, 2 bulk copies to shared memory, "
-                         "3 per-warp async row pipeline (16-bit storages)")
+    ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2],
+                    help="step-kernel inputs: 0 auto, 1 straight to registers, 2 bulk copies to shared memory")
     ap.add_argument("--tau-iters", type=int, default=0,
                     help="0: lagged tau (stored per node); K > 0: node-local implicit tau, K Newton steps")
     ap.add_argument("--variants", default=DEFAULT_VARIANTS,
@@ -226,6 +233,26 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def reduced_storage_summary(variants, prec, mlups):
+    """The fastest reduced-storage form (fewer bytes per node than FP64)
+    whose recorded steady-state |dNu|/Nu is at most 1e-3, against FP64
+    storage measured in the same run."""
+    f64 = variants.get("f64")
+    if not f64:
+        return None
+    cands = [(v["MLUPS"], k, v.get("dnu_rel_vs_f64_256")) for k, v in variants.items()
+             if k != "f64" and v.get("dnu_rel_vs_f64_256") is not None and v["dnu_rel_vs_f64_256"] <= 1e-3]
+    main_dnu = recorded_dnu(prec)
+    if main_dnu is not None and main_dnu <= 1e-3:
+        cands.append((mlups, prec, main_dnu))
+    if not cands:
+        return None
+    best = max(cands)
+    return {"variant": best[1], "MLUPS": best[0], "dnu_rel_vs_f64": best[2],
+            "speedup_vs_f64_storage": best[0] / f64["MLUPS"], "f64_MLUPS": f64["MLUPS"],
+            "dnu_source": "profiles/precision_study_256.txt (256^2 steady state)"}
 
 
 def max_over_ranks(value, world, device):
@@ -398,8 +425,7 @@ def study_tables(args):
                           "seconds": time.perf_counter() - t}), flush=True)
 
 
-DEFAULT_VARIANTS = ("f64,f32,f32d@aa,f32d@tau2,f32d@tma,bf16d,f16d,f16s,bf16s,f16s@tau2,"
-                    "f16d@rows,f16s@rows,bf16s@rows,f16s@tau2@rows")
+DEFAULT_VARIANTS = "f64,f32,f32d@aa,f32d@tau2,f32d@tma,bf16d,f16d,f16s,bf16s,f16s@tau2"
 PRECISION_VARIANTS = ("f64", "f64@tau4", "f32", "f32@tau2", "f32d", "f16d", "bf16d", "f16s", "bf16s")
 
 
@@ -622,7 +648,7 @@ def main():
     bpn_main = bytes_per_node(prec, args.tau_iters)
     achieved = bpn_main * N * N / kern / 1e9
     key_main = prec + (f"@tau{args.tau_iters}" if args.tau_iters else "") + \
-        {0: "", 1: "@reg", 2: "@tma", 3: "@rows"}[args.staging]
+        {0: "", 1: "@reg", 2: "@tma"}[args.staging]
     variants = {}
     for v in [p for p in args.variants.split(",") if p and p != key_main]:
         vs, vd = 2, args.variant_delta
@@ -635,8 +661,8 @@ def main():
                        "bytes_per_node": bpn, "achieved_GBs": av, "frac_of_hbm": av / peak,
                        "layout": "aa (in place)" if vl else "ab (two buffers)",
                        "tau": f"implicit, {vt} Newton steps" if vt else "lagged (stored)",
-                       "staging": {0: "auto", 1: "registers", 2: "bulk copies to shared memory",
-                                   3: "per-warp async row pipeline"}[vg],
+                       "dnu_rel_vs_f64_256": recorded_dnu(vp),
+                       "staging": {0: "auto", 1: "registers", 2: "bulk copies to shared memory"}[vg],
                        "nu_hot": nuv}
         if v == "f64":
             ipn = recorded("f64_fp64_inst_per_node")
@@ -674,7 +700,7 @@ def main():
                      "frac": achieved / peak, "traffic": recorded_traffic(key_main, N),
                      "peak_source": peak_src,
                      "kernel": ("step_kernel" if prec == "f64" else "step_tma_kernel" if args.staging == 2
-                                else "step_rows_kernel" if args.staging == 3 else "step2_kernel") + f"<{key_main}>",
+                                else "step2_kernel") + f"<{key_main}>",
                      "bytes_per_node": bpn_main, "avg_launch_us": kern * 1e6},
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -682,6 +708,7 @@ def main():
         "clocks": clk.summary(),
         "nu_hot": nu,
         "variants": variants,
+        "reduced_storage": reduced_storage_summary(variants, prec, mlups),
     }
     print(json.dumps(line), flush=True)
 

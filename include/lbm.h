@@ -105,12 +105,9 @@ typedef struct {
     int staging;       /* how the step kernel of the two-buffer layout
                           gets its inputs: 1 straight into registers;
                           2 staged in shared memory by bulk
-                          asynchronous copies, a tile ahead (not for
-                          F64); 3 into registers with the next row's
-                          loads issued before the current row's
-                          arithmetic (16-bit storages only); others
-                          get LBM_ERR_UNSUPPORTED; 0 the fastest
-                          for the storage                            [0]    */
+                          asynchronous copies, a tile ahead (F64 gets
+                          LBM_ERR_UNSUPPORTED); 0 the faster of the
+                          two for the storage (today always 1)       [0]    */
 } lbm_opts;
 
 /* Lattice-unit parameters the library derived from the problem groups

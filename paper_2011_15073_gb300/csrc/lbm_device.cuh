@@ -259,12 +259,6 @@ struct Store<LBM_BF16D> {
     {
         *reinterpret_cast<__nv_bfloat162 *>(p + k) = __float22bfloat162_rn(d.v);
     }
-    // raw 16-bit words (as loaded) -> deviations
-    static __device__ __forceinline__ F2 dec2(uint32_t w)
-    {
-        return F2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-    }
-    static __device__ __forceinline__ float dec1(unsigned short h) { return __uint_as_float((uint32_t)h << 16); }
 };
 template <>
 struct Store<LBM_F16D> {
@@ -298,15 +292,6 @@ struct Store<LBM_F16D> {
     {
         *reinterpret_cast<__half2 *>(p + k) = __float22half2_rn(d.v);
     }
-    // raw 16-bit words (as loaded) -> deviations
-    static __device__ __forceinline__ F2 dec2(uint32_t w)
-    {
-        return F2(__half22float2(*reinterpret_cast<const __half2 *>(&w)));
-    }
-    static __device__ __forceinline__ float dec1(unsigned short h)
-    {
-        return __half2float(*reinterpret_cast<const __half *>(&h));
-    }
 };
 
 // FP16 / BF16 deviation storage with stochastic rounding (lbm_round.cuh).
@@ -315,10 +300,11 @@ struct Store<LBM_F16D> {
 // custom 16-bit format with the exponent range shifted to where the
 // deviations live.  Its rounding is sr_half_normal: below 2e-9 (scaled
 // 2^-14) values are truncated toward zero, a bias under 2e-12 in deviation
-// units, far below FP32's resolution of the populations themselves.  The kernels' stores draw their random bits from a
-// per-thread stream (`rng`: rng_init() of the step's seed and the node, then
-// one xorshift32 step per stored pair); import and export use the
-// element's address instead.
+// units, far below FP32's resolution of the populations themselves.  The
+// kernels' random bits: rng_init() hashes the step's seed and the node once,
+// then rng_next() advances a Weyl sequence by one add per stored pair (each
+// draw is uniform because the start is; the pairs of one node share it).
+// Import uses the element's address for its random bits.
 constexpr float F16S_SCALE = 32768.0f, F16S_ISCALE = 1.0f / 32768.0f;
 template <>
 struct Store<LBM_F16S> {
@@ -344,23 +330,14 @@ struct Store<LBM_F16S> {
     }
     static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t &rng)
     {
-        rng = xorshift32(rng);
+        rng = rng_next(rng);
         p[k] = sr_half_normal(d * F16S_SCALE, rng >> 16);
     }
     static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &rng)
     {
-        rng = xorshift32(rng);
+        rng = rng_next(rng);
         const F2 ds = d * F2(F16S_SCALE);
-        *reinterpret_cast<__half2 *>(p + k) = __halves2half2(sr_half_normal(ds.v.x, rng & 0xffffu), sr_half_normal(ds.v.y, rng >> 16));
-    }
-    // raw 16-bit words (as loaded) -> deviations
-    static __device__ __forceinline__ F2 dec2(uint32_t w)
-    {
-        return F2(__half22float2(*reinterpret_cast<const __half2 *>(&w))) * F2(F16S_ISCALE);
-    }
-    static __device__ __forceinline__ float dec1(unsigned short h)
-    {
-        return __half2float(*reinterpret_cast<const __half *>(&h)) * F16S_ISCALE;
+        *reinterpret_cast<uint32_t *>(p + k) = sr_half2_normal(ds.v.x, ds.v.y, rng);
     }
 };
 template <>
@@ -391,7 +368,7 @@ struct Store<LBM_BF16S> {
     static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __bfloat162float(p[k]); }
     static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t &rng)
     {
-        rng = xorshift32(rng);
+        rng = rng_next(rng);
         p[k] = sr_bf16(d, rng >> 16);
     }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
@@ -400,16 +377,9 @@ struct Store<LBM_BF16S> {
     }
     static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &rng)
     {
-        rng = xorshift32(rng);
-        *reinterpret_cast<__nv_bfloat162 *>(p + k) =
-            __halves2bfloat162(sr_bf16(d.v.x, rng & 0xffffu), sr_bf16(d.v.y, rng >> 16));
+        rng = rng_next(rng);
+        *reinterpret_cast<uint32_t *>(p + k) = sr_bf16x2(d.v.x, d.v.y, rng);
     }
-    // raw 16-bit words (as loaded) -> deviations
-    static __device__ __forceinline__ F2 dec2(uint32_t w)
-    {
-        return F2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-    }
-    static __device__ __forceinline__ float dec1(unsigned short h) { return __uint_as_float((uint32_t)h << 16); }
 };
 
 // ----------------------------------------------------------- pull streaming

@@ -72,9 +72,6 @@ cudaError_t launch_aa_step(lbm_ctx *c);
 // The same step with the inputs staged by bulk asynchronous copies
 // (lbm_tma.cu; FP32-arithmetic storages only).
 cudaError_t launch_step_tma(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst);
-// The register path with a row of loads in flight ahead (lbm_step_rows.cu;
-// 16-bit storages only).
-cudaError_t launch_step_rows(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst);
 cudaError_t launch_aa_normalize(lbm_ctx *c);
 int residual_blocks(const lbm_ctx *c);
 

@@ -292,8 +292,8 @@ static cudaError_t step_buffers_tau(lbm_ctx *c, const void *src, void *dst, cons
 }
 
 // How the step kernel gets its inputs: 1 straight into registers, 2 staged
-// by bulk copies (lbm_tma.cu), 3 into registers a row ahead (lbm_step_rows.cu,
-// 16-bit storages); 0 picks per storage.
+// by bulk copies (lbm_tma.cu); 0 picks per storage (the register path, the
+// faster one measured for every storage).
 static int staging_of(const lbm_ctx *c)
 {
     if (c->opts.prec == LBM_F64) return 1;
@@ -306,7 +306,6 @@ static cudaError_t step_buffers_t(lbm_ctx *c, const void *src, void *dst, const 
 {
     const int how = staging_of(c);
     if (how == 2) return launch_step_tma(c, src, dst, tsrc, tdst);
-    if (how == 3) return launch_step_rows(c, src, dst, tsrc, tdst);
     return c->opts.tau_iters > 0 ? step_buffers_tau<PREC, 1>(c, src, dst, tsrc, tdst)
                                  : step_buffers_tau<PREC, 0>(c, src, dst, tsrc, tdst);
 }

@@ -60,22 +60,16 @@ __host__ __device__ __forceinline__ float u2f(uint32_t u)
 #endif
 }
 
-// Marsaglia's xorshift32 (J. Stat. Softw. 8(14), 2003), shifts 13, 17, 5:
-// the per-thread stream of random bits between hashed seeds.
-__host__ __device__ __forceinline__ uint32_t xorshift32(uint32_t x)
-{
-    x ^= x << 13;
-    x ^= x >> 17;
-    x ^= x << 5;
-    return x;
-}
-
-// Start of a thread's stream for the node at plane offset k in the launch
-// with seed `seed` (never 0, which xorshift32 would keep).
+// Start of a thread's random bits for the node at plane offset k in the
+// launch with seed `seed`, and the next draw: a Weyl sequence (golden-ratio
+// increment), one add per draw.  Every draw is uniform over 32 bits because
+// the hashed start is; draws of one node are correlated with each other,
+// which leaves each rounding unbiased.
 __host__ __device__ __forceinline__ uint32_t rng_init(uint32_t seed, int64_t k)
 {
-    return mix32(seed ^ (uint32_t)k ^ (uint32_t)((uint64_t)k >> 32) * 0x9e3779b9u) | 1u;
+    return mix32(seed ^ (uint32_t)k ^ (uint32_t)((uint64_t)k >> 32) * 0x9e3779b9u);
 }
+__host__ __device__ __forceinline__ uint32_t rng_next(uint32_t r) { return r + 0x9e3779b9u; }
 
 // FP32 -> FP16 with stochastic rounding, r16 = 16 random bits.
 // * Half normals (|x| >= 2^-14): the FP32 bits below the half's last place
@@ -111,6 +105,24 @@ __host__ __device__ __forceinline__ __half sr_half(float x, uint32_t r16)
 __host__ __device__ __forceinline__ __half sr_half_normal(float x, uint32_t r16)
 {
     return __float2half_rz(u2f(f2u(x) + ((r16 & 0xffffu) >> 3)));
+}
+
+// Two values at once, as packed 16-bit pairs (x in the low half): the same
+// dithers as sr_half_normal(x, r & 0xffff), sr_half_normal(y, r >> 16) and
+// sr_bf16 likewise, with one packed truncating conversion.
+__device__ __forceinline__ uint32_t sr_half2_normal(float x, float y, uint32_t r)
+{
+    const float xd = u2f(f2u(x) + ((r & 0xffffu) >> 3)), yd = u2f(f2u(y) + (r >> 19));
+    uint32_t out;
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(out) : "f"(yd), "f"(xd));
+    return out;
+}
+__device__ __forceinline__ uint32_t sr_bf16x2(float x, float y, uint32_t r)
+{
+    const float xd = u2f(f2u(x) + (r & 0xffffu)), yd = u2f(f2u(y) + (r >> 16));
+    uint32_t out;
+    asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(out) : "f"(yd), "f"(xd));
+    return out;
 }
 
 // FP32 -> BF16 with stochastic rounding: BF16 keeps the top 16 bits of the

@@ -38,7 +38,6 @@ def test_variant_names():
     assert bench.parse_variant("f32@tau2") == ("f32", 0, 2, 0)
     assert bench.parse_variant("f32d@aa@tau3") == ("f32d", 1, 3, 0)
     assert bench.parse_variant("bf16d@tau2@tma") == ("bf16d", 0, 2, 2)
-    assert bench.parse_variant("f16s@rows") == ("f16s", 0, 0, 3)
     assert bench.bytes_per_node("f32", 2) == 112 and bench.bytes_per_node("f64", 1) == 224
     with pytest.raises(ValueError):
         bench.parse_variant("f32@bogus")

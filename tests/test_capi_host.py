@@ -76,8 +76,8 @@ def test_init_rejects_bad_arguments(L, args, code):
     ("prec", 7, -1), ("prec", -1, -1), ("Ma", 0.0, -1), ("clamp_mode", 2, -1), ("porous_model", 3, -1),
     ("s_e", 2.5, -1), ("s_p", 0.0, -1), ("resid_interval", 0, -1), ("layout", 2, -7),
     ("device", -2, -1), ("tau_iters", -1, -1), ("tau_iters", 17, -1),
-    ("staging", -1, -1), ("staging", 2, -7), ("staging", 3, -7), ("staging", 4, -1),
-    # (the default storage is F64: neither staged kernel is built for it)
+    ("staging", -1, -1), ("staging", 2, -7), ("staging", 3, -1),
+    # (the default storage is F64: the staged kernel is not built for it)
 ])
 def test_init_rejects_bad_options(L, field, value, code):
     from paper_2011_15073_gb300 import lbm
