@@ -33,21 +33,21 @@ __device__ __forceinline__ void push(typename Store<PREC>::S *__restrict__ A, co
     const bool xl = x > 0, xr = x < p.nx - 1, yb = y > 0, yt = y < p.ny - 1;
     uint32_t rng = rng_init(p.seed, k);   // random bits of the stochastic-rounding storages
     // target x + e_i: e1 (1,0) e2 (0,1) e3 (-1,0) e4 (0,-1) e5 (1,1) e6 (-1,1) e7 (-1,-1) e8 (1,-1)
-    St::sdv(A, 0 * P + k, f[0], R(rest_f(0)), rng);
-    if (xr) St::sdv(A, 1 * P + k + 1, f[1], R(rest_f(1)), rng); else St::sdv(A, 3 * P + k, f[1], R(rest_f(3)), rng);
-    if (yt) St::sdv(A, 2 * P + k + W, f[2], R(rest_f(2)), rng); else St::sdv(A, 4 * P + k, f[2], R(rest_f(4)), rng);
-    if (xl) St::sdv(A, 3 * P + k - 1, f[3], R(rest_f(3)), rng); else St::sdv(A, 1 * P + k, f[3], R(rest_f(1)), rng);
-    if (yb) St::sdv(A, 4 * P + k - W, f[4], R(rest_f(4)), rng); else St::sdv(A, 2 * P + k, f[4], R(rest_f(2)), rng);
-    if (xr && yt) St::sdv(A, 5 * P + k + W + 1, f[5], R(rest_f(5)), rng); else St::sdv(A, 7 * P + k, f[5], R(rest_f(7)), rng);
-    if (xl && yt) St::sdv(A, 6 * P + k + W - 1, f[6], R(rest_f(6)), rng); else St::sdv(A, 8 * P + k, f[6], R(rest_f(8)), rng);
-    if (xl && yb) St::sdv(A, 7 * P + k - W - 1, f[7], R(rest_f(7)), rng); else St::sdv(A, 5 * P + k, f[7], R(rest_f(5)), rng);
-    if (xr && yb) St::sdv(A, 8 * P + k - W + 1, f[8], R(rest_f(8)), rng); else St::sdv(A, 6 * P + k, f[8], R(rest_f(6)), rng);
+    stf<PREC>(A, 0 * P + k, f[0], R(rest_f(0)), rng);
+    if (xr) stf<PREC>(A, 1 * P + k + 1, f[1], R(rest_f(1)), rng); else stf<PREC>(A, 3 * P + k, f[1], R(rest_f(3)), rng);
+    if (yt) stf<PREC>(A, 2 * P + k + W, f[2], R(rest_f(2)), rng); else stf<PREC>(A, 4 * P + k, f[2], R(rest_f(4)), rng);
+    if (xl) stf<PREC>(A, 3 * P + k - 1, f[3], R(rest_f(3)), rng); else stf<PREC>(A, 1 * P + k, f[3], R(rest_f(1)), rng);
+    if (yb) stf<PREC>(A, 4 * P + k - W, f[4], R(rest_f(4)), rng); else stf<PREC>(A, 2 * P + k, f[4], R(rest_f(2)), rng);
+    if (xr && yt) stf<PREC>(A, 5 * P + k + W + 1, f[5], R(rest_f(5)), rng); else stf<PREC>(A, 7 * P + k, f[5], R(rest_f(7)), rng);
+    if (xl && yt) stf<PREC>(A, 6 * P + k + W - 1, f[6], R(rest_f(6)), rng); else stf<PREC>(A, 8 * P + k, f[6], R(rest_f(8)), rng);
+    if (xl && yb) stf<PREC>(A, 7 * P + k - W - 1, f[7], R(rest_f(7)), rng); else stf<PREC>(A, 5 * P + k, f[7], R(rest_f(5)), rng);
+    if (xr && yb) stf<PREC>(A, 8 * P + k - W + 1, f[8], R(rest_f(8)), rng); else stf<PREC>(A, 6 * P + k, f[8], R(rest_f(6)), rng);
     typename Store<PREC>::S *G = A + 9 * P;
-    St::sdv(G, 0 * P + k, g[0], R(rest_g(0)), rng);
-    if (xr) St::sdv(G, 1 * P + k + 1, g[1], R(rest_g(1)), rng); else St::sdv(G, 3 * P + k, p.abbd_cold - g[1], R(rest_g(3)), rng);
-    if (yt) St::sdv(G, 2 * P + k + W, g[2], R(rest_g(2)), rng); else St::sdv(G, 4 * P + k, g[2], R(rest_g(4)), rng);
-    if (xl) St::sdv(G, 3 * P + k - 1, g[3], R(rest_g(3)), rng); else St::sdv(G, 1 * P + k, p.abbd_hot - g[3], R(rest_g(1)), rng);
-    if (yb) St::sdv(G, 4 * P + k - W, g[4], R(rest_g(4)), rng); else St::sdv(G, 2 * P + k, g[4], R(rest_g(2)), rng);
+    stf<PREC>(G, 0 * P + k, g[0], R(rest_g(0)), rng);
+    if (xr) stf<PREC>(G, 1 * P + k + 1, g[1], R(rest_g(1)), rng); else stf<PREC>(G, 3 * P + k, (dev_form<PREC>() ? p.abbd_cold : p.abb_cold) - g[1], R(rest_g(3)), rng);
+    if (yt) stf<PREC>(G, 2 * P + k + W, g[2], R(rest_g(2)), rng); else stf<PREC>(G, 4 * P + k, g[2], R(rest_g(4)), rng);
+    if (xl) stf<PREC>(G, 3 * P + k - 1, g[3], R(rest_g(3)), rng); else stf<PREC>(G, 1 * P + k, (dev_form<PREC>() ? p.abbd_hot : p.abb_hot) - g[3], R(rest_g(1)), rng);
+    if (yb) stf<PREC>(G, 4 * P + k - W, g[4], R(rest_g(4)), rng); else stf<PREC>(G, 2 * P + k, g[4], R(rest_g(2)), rng);
 }
 
 // ------------------------------------------------------- one node / thread
@@ -63,16 +63,17 @@ aa_even_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::Ta
     const int64_t P = p.plane, k = (int64_t)y * p.pitch + x;
     R f[9], g[5];
 #pragma unroll
-    for (int i = 0; i < 9; i++) f[i] = St::ldd(A, i * P + k, R(rest_f(i)));
+    for (int i = 0; i < 9; i++) f[i] = ldf<PREC>(A, i * P + k, R(rest_f(i)));
 #pragma unroll
-    for (int i = 0; i < 5; i++) g[i] = St::ldd(A + 9 * P, i * P + k, R(rest_g(i)));
+    for (int i = 0; i < 5; i++) g[i] = ldf<PREC>(A + 9 * P, i * P + k, R(rest_g(i)));
     Macro<R> m;
-    const R t = collide<R, 2, 1>(p, f, g, tau_start<TAU, R, 2, 1>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
+    constexpr int DEV = dev_form<PREC>();
+    const R t = collide<R, 2, DEV>(p, f, g, tau_start<TAU, R, 2, DEV>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
     uint32_t rng = rng_init(p.seed, k);
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::sdv(A, opp(i) * P + k, f[i], R(rest_f(opp(i))), rng);
+    for (int i = 0; i < 9; i++) stf<PREC>(A, opp(i) * P + k, f[i], R(rest_f(opp(i))), rng);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::sdv(A + 9 * P, opp(i) * P + k, g[i], R(rest_g(opp(i))), rng);
+    for (int i = 0; i < 5; i++) stf<PREC>(A + 9 * P, opp(i) * P + k, g[i], R(rest_g(opp(i))), rng);
     if constexpr (TAU == 0) tau[k] = typename St::TauS(t);
 }
 
@@ -83,9 +84,10 @@ __device__ __forceinline__ void odd_node(typename Store<PREC>::S *__restrict__ A
 {
     const int64_t k = (int64_t)y * p.pitch + x;
     R f[9], g[5];
-    pull<PREC, R, true, 1>(A, p, x, y, f, g);
+    constexpr int DEV = dev_form<PREC>();
+    pull<PREC, R, true, DEV>(A, p, x, y, f, g);
     Macro<R> m;
-    const R t = collide<R, 2, 1>(p, f, g, tau_start<TAU, R, 2, 1>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
+    const R t = collide<R, 2, DEV>(p, f, g, tau_start<TAU, R, 2, DEV>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
     push<PREC, R>(A, p, x, y, f, g);
     if constexpr (TAU == 0) tau[k] = typename Store<PREC>::TauS(t);
 }

@@ -382,6 +382,33 @@ struct Store<LBM_BF16S> {
     }
 };
 
+// Which form the step kernels run in: deviations from the rest state for the
+// storages computed in FP32 (DEV 1), full values for FP64 (its rounding is far
+// below the per-step changes of a steady state, and the rest-value
+// subtraction and addition would cost FP64-pipe instructions).  ldf / stf
+// load and store a population in that form.
+template <int PREC>
+constexpr int dev_form()
+{
+    return PREC == LBM_F64 ? 0 : 1;
+}
+template <int PREC, class R>
+__device__ __forceinline__ R ldf(const typename Store<PREC>::S *p, int64_t k, R rest)
+{
+    if constexpr (dev_form<PREC>())
+        return Store<PREC>::ldd(p, k, rest);
+    else
+        return Store<PREC>::ld(p, k, rest);
+}
+template <int PREC, class R>
+__device__ __forceinline__ void stf(typename Store<PREC>::S *p, int64_t k, R v, R rest, uint32_t &rng)
+{
+    if constexpr (dev_form<PREC>())
+        Store<PREC>::sdv(p, k, v, rest, rng);
+    else
+        Store<PREC>::st(p, k, v, rest);
+}
+
 // ----------------------------------------------------------- pull streaming
 // Opposite directions: 1<->3, 2<->4, 5<->7, 6<->8 (D2Q5 uses the first five).
 __host__ __device__ constexpr int opp(int i)

@@ -9,10 +9,11 @@ namespace lbm {
 
 // Pull, collide and store one node (wall rules included).  TAU 0: the
 // collision starts from the stored lagged tau and stores its new tau; TAU 1:
-// from the node-local implicit tau, and no tau is read or written.  The
-// arithmetic runs on deviations from the rest state (DEV form of pull,
-// macro and collide), which keeps the small per-step changes of a nearly
-// steady state out of the rounding of O(1) population values.
+// from the node-local implicit tau, and no tau is read or written.  For the
+// FP32-arithmetic storages the arithmetic runs on deviations from the rest
+// state (DEV form of pull, macro and collide), which keeps the small
+// per-step changes of a nearly steady state out of the rounding of O(1)
+// population values; FP64 runs on full values (dev_form).
 template <int PREC, class R, int FIELD = 2, int TAU = 0>
 __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restrict__ src,
                                           typename Store<PREC>::S *__restrict__ dst,
@@ -23,15 +24,16 @@ __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restr
     using St = Store<PREC>;
     const int64_t k = (int64_t)y * p.pitch + x;
     R f[9], g[5];
-    pull<PREC, R, false, 1>(src, p, x, y, f, g);
+    constexpr int DEV = dev_form<PREC>();
+    pull<PREC, R, false, DEV>(src, p, x, y, f, g);
     Macro<R> m;
-    const R t0 = tau_start<TAU, R, FIELD, 1>(p, f, g, k, [&] { return R(tsrc[k]); });
-    const R tau = collide<R, FIELD, 1>(p, f, g, t0, m, k);
+    const R t0 = tau_start<TAU, R, FIELD, DEV>(p, f, g, k, [&] { return R(tsrc[k]); });
+    const R tau = collide<R, FIELD, DEV>(p, f, g, t0, m, k);
     uint32_t rng = rng_init(p.seed, k);   // random bits of the stochastic-rounding storages
 #pragma unroll
-    for (int i = 0; i < 9; i++) St::sdv(dst, i * p.plane + k, f[i], R(rest_f(i)), rng);
+    for (int i = 0; i < 9; i++) stf<PREC>(dst, i * p.plane + k, f[i], R(rest_f(i)), rng);
 #pragma unroll
-    for (int i = 0; i < 5; i++) St::sdv(dst + 9 * p.plane, i * p.plane + k, g[i], R(rest_g(i)), rng);
+    for (int i = 0; i < 5; i++) stf<PREC>(dst + 9 * p.plane, i * p.plane + k, g[i], R(rest_g(i)), rng);
     if constexpr (TAU == 0) tdst[k] = typename St::TauS(tau);
 }
 
