@@ -273,11 +273,11 @@ def whole_job_units(world, N, delta, steps):
     return world * N * N * delta * steps
 
 
-def time_ours(lbm, torch, N, prec, steps, warmup, delta, stream, layout=0, tau_iters=0, staging=0):
+def time_ours(lbm, torch, N, prec, steps, warmup, delta, stream, layout=0, tau_iters=0, staging=0, graph_steps=0):
     """Device-resident run: returns (seconds for `steps` bench steps, avg fused
     kernel seconds, kernels launched in the timed region, Nu)."""
     cav = lbm.Cavity(N, N, prec=prec, cuda_stream=stream, layout=layout, tau_iters=tau_iters, staging=staging,
-                     **CASE)
+                     graph_steps=graph_steps, **CASE)
     try:
         cav.residual()   # first call stores the snapshot
         for _ in range(warmup):
@@ -674,6 +674,11 @@ def main():
                                            "peak": peak_inst, "frac": ach / peak_inst,
                                            "fp64_inst_per_node": ipn,
                                            "peak_source": "2 FP64 lanes/SM/cycle x 152 SMs x max SM clock"}
+    # launch-bound small grid: one launch per step against replayed step graphs
+    small = {"grid": [256, 256], "storage": "f32d", "fused_steps": 2 * 5000}
+    for key, gs in (("MLUPS_one_launch_per_step", -1), ("MLUPS_replayed_graphs", 0)):
+        ts, _, _, _ = time_ours(lbm, torch, 256, "f32d", 2, 1, 5000, stream, graph_steps=gs)
+        small[key] = 256 * 256 * 5000 * 2 / ts / 1e6
     e2e = None
     if not args.no_e2e:
         es = max(2, args.steps // 2)
@@ -709,6 +714,7 @@ def main():
         "nu_hot": nu,
         "variants": variants,
         "reduced_storage": reduced_storage_summary(variants, prec, mlups),
+        "small_grid": small,
     }
     print(json.dumps(line), flush=True)
 

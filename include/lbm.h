@@ -108,6 +108,20 @@ typedef struct {
                           asynchronous copies, a tile ahead (F64 gets
                           LBM_ERR_UNSUPPORTED); 0 the faster of the
                           two for the storage (today always 1)       [0]    */
+    int graph_steps;   /* lbm_step replays a CUDA graph of this many
+                          steps (rounded up to even) instead of one
+                          launch per step, which pays on small,
+                          launch-bound grids: 0 auto (64 steps for
+                          grids of at most 512 x 512 nodes whose
+                          storage is not F16S / BF16S, else none);
+                          -1 never; G > 0 always (F16S / BF16S get
+                          LBM_ERR_UNSUPPORTED: a replayed graph would
+                          repeat the stochastic rounding's seeds).
+                          Results are identical either way.  The graph
+                          is captured on the context's stream at the
+                          first use (and again after
+                          lbm_set_darcy_field); none is used while the
+                          stream is already being captured          [0]    */
 } lbm_opts;
 
 /* Lattice-unit parameters the library derived from the problem groups

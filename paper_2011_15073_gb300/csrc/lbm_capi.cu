@@ -23,6 +23,49 @@ static thread_local char g_last_cuda[256] = "";
 
 namespace {
 
+// ---- replayed step graphs (lbm_opts.graph_steps)
+void drop_graphs(lbm_ctx *c)
+{
+    for (int i = 0; i < 2; i++)
+        if (c->step_graph[i]) {
+            cudaGraphExecDestroy(c->step_graph[i]);
+            c->step_graph[i] = nullptr;
+        }
+}
+
+int graph_len_for(const lbm_ctx *c)
+{
+    const int g = c->opts.graph_steps;
+    if (g < 0) return 0;
+    if (g > 0) return (g + 1) & ~1;
+    const bool sr = c->opts.prec == LBM_F16S || c->opts.prec == LBM_BF16S;
+    return (!sr && (int64_t)c->nx * c->ny <= 512 * 512) ? 64 : 0;
+}
+
+int graph_parity(const lbm_ctx *c) { return c->opts.layout == 1 ? (c->aa_form_o ? 1 : 0) : c->cur; }
+
+// Capture G step launches on the context's stream into an executable graph
+// for the current parity.  Launching records nothing while capturing, and G
+// is even, so the buffer state is back where it started afterwards.
+int capture_steps(lbm_ctx *c, int G, int par)
+{
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_UNSUPPORTED;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < G && e == cudaSuccess; i++) e = lbm::launch_step(c);
+    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph[par], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) c->step_graph[par] = nullptr;
+    CK(e);
+    return LBM_OK;
+}
+
+
 size_t store_elem(int prec) { return prec == LBM_F64 ? 8 : ((prec == LBM_F32 || prec == LBM_F32D) ? 4 : 2); }
 size_t tau_elem(int prec) { return prec == LBM_F64 ? 8 : 4; }
 
@@ -49,8 +92,9 @@ int map_lattice(int nx, int ny, double n, double Da, double Ra, double Pr, doubl
         (o.clamp_mode != 0 && o.clamp_mode != 1) || (o.porous_model != 0 && o.porous_model != 1) ||
         !(o.s_e > 0) || !(o.s_e < 2) || !(o.s_p > 0) || !(o.s_p < 2) || o.resid_interval < 1 ||
         o.device < -1 || o.tau_iters < 0 || o.tau_iters > LBM_TAU_ITERS_MAX || o.staging < 0 ||
-        o.staging > 2)
+        o.staging > 2 || o.graph_steps < -1)
         return LBM_ERR_ARG;
+    if (o.graph_steps > 0 && (o.prec == LBM_F16S || o.prec == LBM_BF16S)) return LBM_ERR_UNSUPPORTED;
     if (o.staging == 2 && o.prec == LBM_F64) return LBM_ERR_UNSUPPORTED;
     if (o.layout != 0 && o.layout != 1) return LBM_ERR_UNSUPPORTED;
     memset(L, 0, sizeof(*L));
@@ -100,6 +144,7 @@ void free_ctx(lbm_ctx *c)
     cudaFree(c->d_da);
     cudaFree(c->d_err);
     cudaFreeHost(c->h_err);
+    drop_graphs(c);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -234,6 +279,7 @@ void lbm_default_opts(lbm_opts *o)
     o->stag_floor = -1.0;
     o->tau_iters = 0;
     o->staging = 0;
+    o->graph_steps = 0;
 }
 
 int lbm_init(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra, double Pr,
@@ -275,6 +321,8 @@ int lbm_set_darcy_field(lbm_ctx *c, const double *Da)
 {
     if (!c) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    drop_graphs(c);   // captured launches hold the old field pointer
     if (!Da) {
         CK(cudaStreamSynchronize(c->stream));
         cudaFree(c->d_da);
@@ -318,7 +366,24 @@ int lbm_step(lbm_ctx *c, int64_t k)
 {
     if (!c || k < 0) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
-    for (int64_t t = 0; t < k; t++) {
+    int64_t t = 0;
+    const int G = graph_len_for(c);
+    if (G > 0 && k >= G) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        CK(cudaStreamIsCapturing(c->stream, &cs));
+        while (cs == cudaStreamCaptureStatusNone && k - t >= G) {
+            const int par = graph_parity(c);
+            if (!c->step_graph[par]) {
+                const int rc = capture_steps(c, G, par);
+                if (rc == LBM_ERR_UNSUPPORTED) break;   // this stream cannot be captured: plain launches
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(c->step_graph[par], c->stream));
+            c->steps += G;   // an even number of steps leaves the parity as it was
+            t += G;
+        }
+    }
+    for (; t < k; t++) {
         CK(lbm::launch_step(c));
         c->steps++;   // also the stochastic rounding's step counter
     }

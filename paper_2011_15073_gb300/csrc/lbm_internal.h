@@ -47,6 +47,10 @@ struct lbm_ctx {
     void *d_da = nullptr;        // per-node Darcy numbers (compute type), or null
     unsigned *d_err = nullptr;   // raised by a kernel whose bounded wait gave up
     unsigned *h_err = nullptr;   // pinned mirror of d_err
+    // Replayed step graphs (lbm_step), one per parity of the buffer state
+    // (two-buffer: which buffer is current; in place: odd-step form).
+    cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
+    int graph_len = 0;
     bool have_snap = false;
     bool aa_form_o = false;      // in-place layout: state in the odd-step form
     int64_t steps = 0;

@@ -41,7 +41,8 @@ class Opts(ctypes.Structure):
                 ("porous_model", ctypes.c_int), ("s_e", ctypes.c_double), ("s_p", ctypes.c_double),
                 ("resid_interval", ctypes.c_int), ("layout", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
-                ("stag_floor", ctypes.c_double), ("tau_iters", ctypes.c_int), ("staging", ctypes.c_int)]
+                ("stag_floor", ctypes.c_double), ("tau_iters", ctypes.c_int), ("staging", ctypes.c_int),
+                ("graph_steps", ctypes.c_int)]
 
 
 class Lattice(ctypes.Structure):

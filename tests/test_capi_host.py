@@ -49,7 +49,7 @@ def test_default_opts(L):
     assert (o.prec, o.Ma, o.clamp_mode, o.porous_model, o.s_e, o.s_p, o.resid_interval, o.layout) == \
         (0, 0.1, 0, 1, 1.5, 1.5, 1000, 0)
     assert not o.cuda_stream and o.device == -1 and o.stag_floor == -1.0
-    assert o.tau_iters == 0 and o.staging == 0
+    assert o.tau_iters == 0 and o.staging == 0 and o.graph_steps == 0
 
 
 @pytest.mark.parametrize("args,code", [
@@ -76,7 +76,7 @@ def test_init_rejects_bad_arguments(L, args, code):
     ("prec", 7, -1), ("prec", -1, -1), ("Ma", 0.0, -1), ("clamp_mode", 2, -1), ("porous_model", 3, -1),
     ("s_e", 2.5, -1), ("s_p", 0.0, -1), ("resid_interval", 0, -1), ("layout", 2, -7),
     ("device", -2, -1), ("tau_iters", -1, -1), ("tau_iters", 17, -1),
-    ("staging", -1, -1), ("staging", 2, -7), ("staging", 3, -1),
+    ("staging", -1, -1), ("staging", 2, -7), ("staging", 3, -1), ("graph_steps", -2, -1),
     # (the default storage is F64: the staged kernel is not built for it)
 ])
 def test_init_rejects_bad_options(L, field, value, code):
@@ -135,3 +135,12 @@ def test_batch_refuses_implicit_tau(L):
     h = ctypes.c_void_p()
     assert L.lbm_batch_create(ctypes.byref(h), ctypes.byref(case), 1, ctypes.byref(o)) == -7
     assert h.value is None
+
+
+def test_graphs_refused_for_stochastic_storages(L):
+    """A replayed graph would repeat the stochastic rounding's seeds."""
+    from paper_2011_15073_gb300 import lbm
+    for prec in ("f16s", "bf16s"):
+        o = lbm.default_opts(prec=prec, graph_steps=16)
+        h = ctypes.c_void_p()
+        assert L.lbm_init(ctypes.byref(h), 8, 8, 0.6, 1e-2, 1e5, 6.2, 0.6, ctypes.byref(o)) == -7
