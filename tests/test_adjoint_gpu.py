@@ -118,3 +118,34 @@ def test_fp32_adjoint_close_to_fp64(mods):
     assert np.linalg.norm(d32 - d64) <= 1e-2 * np.linalg.norm(d64)
     assert n32 == pytest.approx(n64, rel=1e-2)
     assert R32 == pytest.approx(R64, rel=1e-2)
+
+
+def test_autograd_function_carries_the_adjoint(mods):
+    """hot_wall_nusselt's gradients through torch.autograd equal the C call's,
+    and a directional central difference of its value (FP64)."""
+    inputs, lbm = mods
+    from paper_2011_15073_gb300.autograd import hot_wall_nusselt
+    nx, ny, steps = 40, 32, 400
+    Da = torch.tensor(inputs.darcy_field(17, nx, ny), dtype=torch.float64, requires_grad=True)
+    n = torch.tensor(CASE["n"], dtype=torch.float64, requires_grad=True)
+    Ra = torch.tensor(CASE["Ra"], dtype=torch.float64, requires_grad=True)
+    kw = dict(Pr=CASE["Pr"], porosity=CASE["porosity"], steps=steps, ckpt_every=100, prec="f64", clamp_mode=1)
+    J = hot_wall_nusselt(Da, n, Ra, **kw)
+    (2.0 * J).backward()
+    with lbm.Cavity(nx, ny, CASE["n"], 1e-2, CASE["Ra"], CASE["Pr"], CASE["porosity"], prec="f64",
+                    clamp_mode=1) as cav:
+        cav.set_darcy_field(Da.detach().numpy())
+        J0, dDa, dn, dRa, _ = cav.adjoint_nu(steps, ckpt_every=100, from_rest=True)
+    assert float(J) == J0
+    assert np.array_equal(Da.grad.numpy(), 2.0 * dDa)
+    assert float(n.grad) == 2.0 * dn and float(Ra.grad) == 2.0 * dRa
+    # direction in log Da
+    rng = np.random.default_rng(5)
+    v = torch.tensor(rng.standard_normal((ny, nx)), dtype=torch.float64)
+    h = 1e-4
+    with torch.no_grad():
+        Jp = hot_wall_nusselt(Da * torch.exp(h * v), n, Ra, **kw)
+        Jm = hot_wall_nusselt(Da * torch.exp(-h * v), n, Ra, **kw)
+    fd = float(Jp - Jm) / (2 * h)
+    ad = float((Da.grad / 2.0 * Da.detach() * v).sum())
+    assert ad == pytest.approx(fd, rel=1e-5)
