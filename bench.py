@@ -130,7 +130,8 @@ def parse():
                     help="other storage precisions measured beside the headline ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", choices=["tables", "precision", "batch", "adjoint"], default=None,
+    ap.add_argument("--study", choices=["tables", "precision", "batch", "adjoint", "plain", "throughput"],
+                    default=None,
                     help="physics studies instead of the throughput bench (one JSON line per case)")
     ap.add_argument("--study-N", type=int, default=None)
     ap.add_argument("--study-max-steps", type=int, default=3_000_000)
@@ -347,7 +348,40 @@ def cpu_baseline(N_sample=1024, steps=150):
     dt = time.perf_counter() - t
     mlups = N_sample * N_sample * steps / dt / 1e6
     return {"value": mlups, "unit": "MLUPS", "cores": int(os.environ["OMP_NUM_THREADS"]), "kind": "oracle",
-            "sample": f"FP64 oracle, {N_sample}x{N_sample} cavity, {steps} steps, same (n, Da, Ra, Pr, porosity)"}
+            "sample": f"FP64 oracle, {N_sample}x{N_sample} cavity, {steps} steps, same (n, Da, Ra, Pr, porosity)",
+            "single_thread": oracle_single_thread(), "cpu_model": cpu_model()}
+
+
+def cpu_model():
+    """The host CPU's model string (x86 'model name', or the Arm implementer
+    and part numbers), for the CPU baseline's record."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return None
+    for key in ("model name", "Model"):
+        for ln in info:
+            if ln.startswith(key):
+                return ln.split(":", 1)[1].strip()
+    parts = sorted({ln.split(":", 1)[1].strip() for ln in info if ln.startswith(("CPU implementer", "CPU part"))})
+    return "arm " + " ".join(parts) if parts else None
+
+
+def oracle_single_thread(N=64, steps=2000):
+    """The oracle on one host core (a child process with OMP_NUM_THREADS=1),
+    on an N^2 cavity of the same parameters."""
+    import subprocess
+    code = ("import time, oracle; oracle.build(); "
+            f"c = oracle.Cavity.from_params({N}, {N}, {CASE['n']}, {CASE['Da']}, {CASE['Ra']}, {CASE['Pr']}, "
+            f"porosity={CASE['porosity']}); c.step(1); t = time.perf_counter(); c.step({steps}); "
+            "print(time.perf_counter() - t)")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, env=env, timeout=600)
+    if r.returncode != 0:
+        return None
+    dt = float(r.stdout.strip().splitlines()[-1])
+    return {"value": N * N * steps / dt / 1e6, "unit": "MLUPS", "cores": 1,
+            "sample": f"FP64 oracle, {N}x{N} cavity, {steps} steps"}
 
 
 def run_reference(args):
@@ -480,6 +514,58 @@ def study_precision(args):
                               "dnu_mean_rel": (r["nu_mean"] - ref["nu"]) / ref["nu"], "l2_rel": err,
                               "steps": r["steps"], "residual": r["resid"], "stop": r["stop"],
                               "seconds": r["sec"]}), flush=True)
+
+
+def study_plain(args):
+    """The plain method in FP64 on a 64^2 cavity (n = 1, Da = 0.1, Ra = 1e3,
+    porosity 0.6; Pr = 10 and 6.2): average hot-wall Nu after 20,000 steps,
+    on the GPU and from the FP64 oracle, and at convergence (r < 1e-10)."""
+    import oracle
+    from paper_2011_15073_gb300 import lbm
+    oracle.build()
+    for Pr in (10.0, 6.2):
+        case = dict(n=1.0, Da=1e-1, Ra=1e3, Pr=Pr, porosity=0.6)
+        ref = oracle.Cavity.from_params(64, 64, case["n"], case["Da"], case["Ra"], Pr, porosity=0.6)
+        t = time.perf_counter()
+        ref.step(20_000)
+        t_orc = time.perf_counter() - t
+        nu_orc = ref.nusselt()[0]
+        with lbm.Cavity(64, 64, prec="f64", **case) as cav:
+            cav.step(20_000)
+            nu_20k = cav.nusselt()[0]
+            steps, r, why = cav.run_to_steady(1e-10, 2_000_000)
+            nu_ss = cav.nusselt()[0]
+        print(json.dumps({"study": "plain", "N": 64, **case, "prec": "f64", "nu_hot_20000": nu_20k,
+                          "oracle_nu_hot_20000": nu_orc, "rel_diff_vs_oracle": (nu_20k - nu_orc) / nu_orc,
+                          "oracle_seconds": t_orc, "steady_steps": 20_000 + steps, "steady_residual": r,
+                          "nu_hot_steady": nu_ss}), flush=True)
+
+
+def study_throughput(args):
+    """Single cases at 1024^2 and 4096^2 (n = 0.6, Da = 1e-3, Ra = 1e5):
+    200 warm-up steps, then five timed runs of 2000 steps each (CUDA events
+    on the library's stream); best and median MLUPS per storage."""
+    import statistics
+    import torch
+    from paper_2011_15073_gb300 import lbm
+    stream = torch.cuda.Stream()
+    for N in (1024, 4096):
+        for prec in ("f64", "f32", "f32d"):
+            with lbm.Cavity(N, N, prec=prec, cuda_stream=stream, **CASE) as cav:
+                cav.step(200)
+                rates = []
+                for _ in range(5):
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    cav.step(2000)
+                    b.record(stream)
+                    b.synchronize()
+                    rates.append(N * N * 2000 / (a.elapsed_time(b) / 1e3) / 1e6)
+            print(json.dumps({"study": "throughput", "N": N, "prec": prec, "best_MLUPS": max(rates),
+                              "median_MLUPS": statistics.median(rates),
+                              "GBs_at_median": statistics.median(rates) * 1e6 * BYTES_PER_NODE[prec] / 1e9}),
+                  flush=True)
 
 
 def study_batch(args):
@@ -617,6 +703,12 @@ def main():
     if args.study == "precision":
         study_precision(args)
         return
+    if args.study == "plain":
+        study_plain(args)
+        return
+    if args.study == "throughput":
+        study_throughput(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -706,7 +798,9 @@ def main():
                      "peak_source": peak_src,
                      "kernel": ("step_kernel" if prec == "f64" else "step_tma_kernel" if args.staging == 2
                                 else "step2_kernel") + f"<{key_main}>",
-                     "bytes_per_node": bpn_main, "avg_launch_us": kern * 1e6},
+                     "bytes_per_node": bpn_main, "avg_launch_us": kern * 1e6,
+                     # the arithmetic side of the same kernel: FMA-pipe activity (ncu, 2048^2)
+                     "fma_pipe_active": recorded(key_main + "_fma_pipe_active")},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
