@@ -122,6 +122,8 @@ def parse():
     ap.add_argument("--variant-delta", type=int, default=200)
     ap.add_argument("--prec", default="f32d",
                     help="storage of the headline run (f32d: FP32 deviations from the rest state)")
+    ap.add_argument("--layout", type=int, default=0, choices=[0, 1],
+                    help="0: two buffers (pull); 1: one buffer, in-place AA-pattern streaming")
     ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2],
                     help="step-kernel inputs: 0 auto, 1 straight to registers, 2 bulk copies to shared memory")
     ap.add_argument("--tau-iters", type=int, default=0,
@@ -731,7 +733,7 @@ def main():
     barrier()
     with Clocks(local) as clk:
         total, kern, launches, nu = time_ours(lbm, torch, N, prec, args.steps, max(3, args.warmup), delta, stream,
-                                              tau_iters=args.tau_iters, staging=args.staging)
+                                              layout=args.layout, tau_iters=args.tau_iters, staging=args.staging)
     barrier()
     total = max_over_ranks(total, world, "cuda")
     units = whole_job_units(world, N, delta, args.steps)
@@ -740,7 +742,7 @@ def main():
     bpn_main = bytes_per_node(prec, args.tau_iters)
     achieved = bpn_main * N * N / kern / 1e9
     key_main = prec + (f"@tau{args.tau_iters}" if args.tau_iters else "") + \
-        {0: "", 1: "@reg", 2: "@tma"}[args.staging]
+        {0: "", 1: "@reg", 2: "@tma"}[args.staging] + ("@aa" if args.layout else "")
     variants = {}
     for v in [p for p in args.variants.split(",") if p and p != key_main]:
         vs, vd = 2, args.variant_delta

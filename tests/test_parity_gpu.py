@@ -380,37 +380,64 @@ def test_nonfinite_state_is_reported(mods):
         assert e.value.code == -3
 
 
-@pytest.mark.parametrize("prec,layout", [("f32", 0), ("f64", 0), ("f32", 1)])
+@pytest.mark.parametrize("prec,layout", [("f32", 0), ("f64", 0), ("f32", 1), ("f32d", 0), ("f16s", 0)])
 def test_full_size_sampled_parity(mods, prec, layout):
     """4096 x 4096, the benchmark's launch configuration: the state after k
     steps at a node depends only on the (2k+1)^2 nodes around it, so the
     oracle recomputes sampled nodes one window at a time.  A window that
     touches a real wall keeps it; its artificial edges stay more than k nodes
-    away from the sampled node."""
+    away from the sampled node.  The state goes in and out in the native
+    storage (values, FP32 deviations from rest, or FP16 deviations x 2^15)."""
     oracle, inputs, lbm = mods
     N, k, h = 4096, 3, 5
     c = CASES["thinning"]
-    dt = np.float64 if prec == "f64" else np.float32
     lat_full = oracle.map_params(N, N, c["n"], c["Da"], c["Ra"], c["Pr"], porosity=c["porosity"])
     rest = oracle.Cavity(oracle.map_params(4, 4, 1.0, 1e-2, 1e5, 6.2))
     f0, g0, t0 = rest.get_state()
+    wf, wg = f0[:, :1, :1], g0[:, :1, :1]          # rest values w_i and w_i T_m
     rng = np.random.default_rng(4096)
-    f = (f0[:, :1, :1] * (1 + rng.uniform(-1e-3, 1e-3, (9, N, N)))).astype(dt)
-    g = (g0[:, :1, :1] * (1 + rng.uniform(-1e-3, 1e-3, (5, N, N)))).astype(dt)
-    tau = np.full((N, N), lat_full.tau0, dtype=dt)
+    df_in = wf * rng.uniform(-1e-3, 1e-3, (9, N, N))
+    dg_in = wg * rng.uniform(-1e-3, 1e-3, (5, N, N))
+    if prec == "f16s":   # stored: FP16 of the deviation x 2^15 (exactly representable inputs)
+        sf, sg = (df_in * 32768).astype(np.float16), (dg_in * 32768).astype(np.float16)
+        f = wf + sf.astype(np.float64) / 32768
+        g = wg + sg.astype(np.float64) / 32768
+        host_fg = [sf.reshape(-1).view(np.uint8), sg.reshape(-1).view(np.uint8)]
+    else:
+        dt = np.float64 if prec == "f64" else np.float32
+        if prec == "f32d":
+            sf, sg = df_in.astype(dt), dg_in.astype(dt)
+            f, g = wf + sf.astype(np.float64), wg + sg.astype(np.float64)
+        else:
+            sf, sg = (wf + df_in).astype(dt), (wg + dg_in).astype(dt)
+            f, g = sf.astype(np.float64), sg.astype(np.float64)
+        host_fg = [sf.reshape(-1).view(np.uint8), sg.reshape(-1).view(np.uint8)]
+    tdt = np.float64 if prec == "f64" else np.float32
+    tau_s = np.full((N, N), lat_full.tau0, dtype=tdt)
+    tau = tau_s.astype(np.float64)
     with gpu_for(lbm, N, N, c, prec, layout) as cav:
-        host = np.concatenate([f.reshape(-1), g.reshape(-1), tau.reshape(-1)])
-        cav.set_state(host.view(np.uint8))
+        host = np.concatenate(host_fg + [tau_s.reshape(-1).view(np.uint8)])
+        cav.set_state(host)
         cav.step(k)
         out = np.empty_like(host)
-        cav.get_state(out.view(np.uint8))
+        cav.get_state(out)
     nn = N * N
-    fo = out[:9 * nn].reshape(9, N, N)
-    go = out[9 * nn:14 * nn].reshape(5, N, N)
-    to = out[14 * nn:].reshape(N, N)
+    nf, ng = len(host_fg[0]), len(host_fg[1])
+    if prec == "f16s":
+        fo = wf + out[:nf].view(np.float16).astype(np.float64).reshape(9, N, N) / 32768
+        go = wg + out[nf:nf + ng].view(np.float16).astype(np.float64).reshape(5, N, N) / 32768
+    else:
+        fo = out[:nf].view(tdt).astype(np.float64).reshape(9, N, N)
+        go = out[nf:nf + ng].view(tdt).astype(np.float64).reshape(5, N, N)
+        if prec == "f32d":
+            fo, go = wf + fo, wg + go
+    to = out[nf + ng:].view(tdt).astype(np.float64).reshape(N, N)
+    assert nf == 9 * nn * (2 if prec == "f16s" else tdt().itemsize)
     samples = [(0, 0), (N - 1, 0), (0, N - 1), (N - 1, N - 1), (N // 2, 0), (0, N // 2),
                (N - 1, N // 2), (N // 2, N - 1)] + [tuple(rng.integers(0, N, 2)) for _ in range(24)]
-    tol = 1e-12 if prec == "f64" else 2e-6
+    # FP16 x 2^15 stochastic: one spacing per store of deviations ~1e-3 w,
+    # 2^-11 of that, over three steps
+    tol = {"f64": 1e-12, "f16s": 1e-5}.get(prec, 2e-6)
     for (x, y) in samples:
         x0 = 0 if x < h + k else (N - (2 * h + 1) if x > N - 1 - h - k else x - h)
         y0 = 0 if y < h + k else (N - (2 * h + 1) if y > N - 1 - h - k else y - h)
