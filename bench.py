@@ -798,7 +798,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(key_main, N),
                      "peak_source": peak_src,
-                     "kernel": ("step_kernel" if prec == "f64" else "step_tma_kernel" if args.staging == 2
+                     "kernel": ("aa_even/aa_odd kernels (alternating)" if args.layout else
+                                "step_kernel" if prec == "f64" else "step_tma_kernel" if args.staging == 2
                                 else "step2_kernel") + f"<{key_main}>",
                      "bytes_per_node": bpn_main, "avg_launch_us": kern * 1e6,
                      # the arithmetic side of the same kernel: FMA-pipe activity (ncu, 2048^2)
