@@ -51,7 +51,7 @@ __device__ __forceinline__ void push(typename Store<PREC>::S *__restrict__ A, co
 }
 
 // ------------------------------------------------------- one node / thread
-template <int PREC, int TAU>
+template <int PREC, int TAU, int FIELD>
 __global__ void __launch_bounds__(128)
 aa_even_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::TauS *__restrict__ tau,
                Phys<typename Store<PREC>::R> p)
@@ -68,7 +68,7 @@ aa_even_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::Ta
     for (int i = 0; i < 5; i++) g[i] = ldf<PREC>(A + 9 * P, i * P + k, R(rest_g(i)));
     Macro<R> m;
     constexpr int DEV = dev_form<PREC>();
-    const R t = collide<R, 2, DEV>(p, f, g, tau_start<TAU, R, 2, DEV>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
+    const R t = collide<R, FIELD, DEV>(p, f, g, tau_start<TAU, R, FIELD, DEV>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
     uint32_t rng = rng_init(p.seed, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) stf<PREC>(A, opp(i) * P + k, f[i], R(rest_f(opp(i))), rng);
@@ -77,7 +77,7 @@ aa_even_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::Ta
     if constexpr (TAU == 0) tau[k] = typename St::TauS(t);
 }
 
-template <int PREC, class R, int TAU>
+template <int PREC, class R, int TAU, int FIELD>
 __device__ __forceinline__ void odd_node(typename Store<PREC>::S *__restrict__ A,
                                          typename Store<PREC>::TauS *__restrict__ tau, const Phys<R> &p, int x,
                                          int y)
@@ -87,23 +87,23 @@ __device__ __forceinline__ void odd_node(typename Store<PREC>::S *__restrict__ A
     constexpr int DEV = dev_form<PREC>();
     pull<PREC, R, true, DEV>(A, p, x, y, f, g);
     Macro<R> m;
-    const R t = collide<R, 2, DEV>(p, f, g, tau_start<TAU, R, 2, DEV>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
+    const R t = collide<R, FIELD, DEV>(p, f, g, tau_start<TAU, R, FIELD, DEV>(p, f, g, k, [&] { return R(tau[k]); }), m, k);
     push<PREC, R>(A, p, x, y, f, g);
     if constexpr (TAU == 0) tau[k] = typename Store<PREC>::TauS(t);
 }
 
-template <int PREC, int TAU>
+template <int PREC, int TAU, int FIELD>
 __global__ void __launch_bounds__(128)
 aa_odd_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::TauS *__restrict__ tau,
               Phys<typename Store<PREC>::R> p)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= p.nx) return;
-    odd_node<PREC, typename Store<PREC>::R, TAU>(A, tau, p, x, y);
+    odd_node<PREC, typename Store<PREC>::R, TAU, FIELD>(A, tau, p, x, y);
 }
 
 // ------------------------------------------------------ two nodes / thread
-template <int PREC, int TAU>
+template <int PREC, int TAU, int FIELD>
 __global__ void __launch_bounds__(128)
 aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
 {
@@ -117,7 +117,7 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
         for (int i = 0; i < 5; i++) g[i] = St::ldd(A + 9 * P, i * P + k, float(rest_g(i)));
         Macro<float> m;
         const float t =
-            collide<float, 2, 1>(p, f, g, tau_start<TAU, float, 2, 1>(p, f, g, k, [&] { return tau[k]; }), m, k);
+            collide<float, FIELD, 1>(p, f, g, tau_start<TAU, float, FIELD, 1>(p, f, g, k, [&] { return tau[k]; }), m, k);
         uint32_t rng = rng_init(p.seed, k);
         for (int i = 0; i < 9; i++) St::sdv(A, opp(i) * P + k, f[i], float(rest_f(opp(i))), rng);
         for (int i = 0; i < 5; i++) St::sdv(A + 9 * P, opp(i) * P + k, g[i], float(rest_g(opp(i))), rng);
@@ -130,8 +130,8 @@ aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau
 #pragma unroll
     for (int i = 0; i < 5; i++) g[i] = St::ldd2(A + (9 + i) * P, k, float(rest_g(i)));
     Macro<F2> m;
-    const F2 t0 = tau_start<TAU, F2, 2, 1>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
-    const F2 t = collide<F2, 2, 1>(p2, f, g, t0, m, k);
+    const F2 t0 = tau_start<TAU, F2, FIELD, 1>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
+    const F2 t = collide<F2, FIELD, 1>(p2, f, g, t0, m, k);
     uint32_t rng = rng_init(p2.seed, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) St::sdv2(A + opp(i) * P, k, f[i], float(rest_f(opp(i))), rng);
@@ -165,7 +165,7 @@ __device__ __forceinline__ void push_left(typename Store<PREC>::S *base, int64_t
     if (lane == 0) St::sdv(base, kr - 1, v.v.x, rest, rng);
 }
 
-template <int PREC, int TAU>
+template <int PREC, int TAU, int FIELD>
 __global__ void __launch_bounds__(128)
 aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
 {
@@ -177,7 +177,7 @@ aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau,
     const bool fast = y > 0 && y < p.ny - 1 && wx > 0 && wx + 64 < p.nx;
     if (!fast) {
         for (int j = 0; j < 2; j++)
-            if (x0 + j < p.nx) odd_node<PREC, float, TAU>(A, tau, p, x0 + j, y);
+            if (x0 + j < p.nx) odd_node<PREC, float, TAU, FIELD>(A, tau, p, x0 + j, y);
         return;
     }
     const int64_t P = p.plane, W = p.pitch;
@@ -206,8 +206,8 @@ aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau,
     g[3] = from_right(St::ldd2(gs + P, k, float(rest_g(1))), l31 ? St::ldd(gs + P, k + 2, float(rest_g(1))) : 0.f, lane);
     g[4] = St::ldd2(gs + 2 * P, k + W, float(rest_g(2)));
     Macro<F2> m;
-    const F2 t0 = tau_start<TAU, F2, 2, 1>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
-    const F2 t = collide<F2, 2, 1>(p2, f, g, t0, m, k);
+    const F2 t0 = tau_start<TAU, F2, FIELD, 1>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tau + k)); });
+    const F2 t = collide<F2, FIELD, 1>(p2, f, g, t0, m, k);
     uint32_t rng = rng_init(p2.seed, k);
     // push f*_i(x) into slot i of node x + e_i
     St::sdv2(fs, k, f[0], float(rest_f(0)), rng);
@@ -262,7 +262,7 @@ aa_normalize_kernel(typename Store<PREC>::S *__restrict__ A, Phys<typename Store
 }
 
 // ------------------------------------------------------------- launchers
-template <int PREC, int TAU>
+template <int PREC, int TAU, int FIELD>
 static void aa_launch(lbm_ctx *c)
 {
     using St = Store<PREC>;
@@ -270,18 +270,18 @@ static void aa_launch(lbm_ctx *c)
     if constexpr (PREC == LBM_F64) {
         const dim3 grid((c->nx + 127) / 128, c->ny);
         if (c->aa_form_o)
-            aa_even_kernel<PREC, TAU><<<grid, 128, 0, c->stream>>>(A, (double *)c->buf.tau[0],
+            aa_even_kernel<PREC, TAU, FIELD><<<grid, 128, 0, c->stream>>>(A, (double *)c->buf.tau[0],
                                                                  make_params<double>(c));
         else
-            aa_odd_kernel<PREC, TAU><<<grid, 128, 0, c->stream>>>(A, (double *)c->buf.tau[0],
+            aa_odd_kernel<PREC, TAU, FIELD><<<grid, 128, 0, c->stream>>>(A, (double *)c->buf.tau[0],
                                                                 make_params<double>(c));
     } else {
         const dim3 grid((c->nx + 255) / 256, c->ny);
         if (c->aa_form_o)
-            aa_even2_kernel<PREC, TAU><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0],
+            aa_even2_kernel<PREC, TAU, FIELD><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0],
                                                                   make_params<float>(c), make_params<F2>(c));
         else
-            aa_odd2_kernel<PREC, TAU><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0],
+            aa_odd2_kernel<PREC, TAU, FIELD><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0],
                                                                  make_params<float>(c), make_params<F2>(c));
     }
 }
@@ -289,10 +289,11 @@ static void aa_launch(lbm_ctx *c)
 template <int PREC>
 static cudaError_t aa_step_t(lbm_ctx *c)
 {
+    const bool field = c->d_da != nullptr;
     if (c->opts.tau_iters > 0)
-        aa_launch<PREC, 1>(c);
+        field ? aa_launch<PREC, 1, 1>(c) : aa_launch<PREC, 1, 0>(c);
     else
-        aa_launch<PREC, 0>(c);
+        field ? aa_launch<PREC, 0, 1>(c) : aa_launch<PREC, 0, 0>(c);
     c->aa_form_o = !c->aa_form_o;
     return cudaGetLastError();
 }

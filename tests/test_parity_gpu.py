@@ -435,9 +435,7 @@ def test_full_size_sampled_parity(mods, prec, layout):
     assert nf == 9 * nn * (2 if prec == "f16s" else tdt().itemsize)
     samples = [(0, 0), (N - 1, 0), (0, N - 1), (N - 1, N - 1), (N // 2, 0), (0, N // 2),
                (N - 1, N // 2), (N // 2, N - 1)] + [tuple(rng.integers(0, N, 2)) for _ in range(24)]
-    # FP16 x 2^15 stochastic: one spacing per store of deviations ~1e-3 w,
-    # 2^-11 of that, over three steps
-    tol = {"f64": 1e-12, "f16s": 1e-5}.get(prec, 2e-6)
+    tol = 1e-12 if prec == "f64" else 2e-6
     for (x, y) in samples:
         x0 = 0 if x < h + k else (N - (2 * h + 1) if x > N - 1 - h - k else x - h)
         y0 = 0 if y < h + k else (N - (2 * h + 1) if y > N - 1 - h - k else y - h)
@@ -453,7 +451,16 @@ def test_full_size_sampled_parity(mods, prec, layout):
         win.step(1)
         fw, gw, tw = win.get_state()
         lx, ly = x - x0, y - y0
-        assert np.max(np.abs(fo[:, y, x] - fw[:, ly, lx]) / W9[:, 0, 0]) < tol, (x, y)
-        assert np.max(np.abs(go[:, y, x] - gw[:, ly, lx]) / W5[:, 0, 0]) < tol, (x, y)
+        if prec == "f16s":
+            # each store rounds a deviation to one of its two FP16 neighbours
+            # (spacing at most 2^-10 of its size); after k steps the error stays
+            # within k spacings of the largest deviation in the window (at the
+            # isothermal walls the thermal ones reach 2w (T_w - T_m))
+            for a, b, w in ((fo, fw, wf), (go, gw, wg)):
+                dev = np.abs(b - w).max()
+                assert np.all(np.abs(a[:, y, x] - b[:, ly, lx]) <= k * 2.0 ** -10 * dev + 1e-9), (x, y)
+        else:
+            assert np.max(np.abs(fo[:, y, x] - fw[:, ly, lx]) / W9[:, 0, 0]) < tol, (x, y)
+            assert np.max(np.abs(go[:, y, x] - gw[:, ly, lx]) / W5[:, 0, 0]) < tol, (x, y)
         df = max(np.max(np.abs(fo[:, y, x] - fw[:, ly, lx])), np.max(np.abs(go[:, y, x] - gw[:, ly, lx])))
         check_tau(np.array([to[y, x]], float), tw[ly, lx:lx + 1], gam_w[ly, lx:lx + 1], lat, prec, df)
