@@ -132,7 +132,7 @@ def parse():
                     help="other storage precisions measured beside the headline ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", choices=["tables", "precision", "batch", "adjoint", "plain", "throughput"],
+    ap.add_argument("--study", choices=["tables", "precision", "batch", "adjoint", "plain", "throughput", "grid"],
                     default=None,
                     help="physics studies instead of the throughput bench (one JSON line per case)")
     ap.add_argument("--study-N", type=int, default=None)
@@ -461,6 +461,26 @@ def study_tables(args):
                           "seconds": time.perf_counter() - t}), flush=True)
 
 
+def study_grid(args):
+    """Grid independence of the average hot-wall Nu at 128^2, 160^2 and
+    192^2 (the paper reports choosing 160^2 without showing the study): three
+    of its cases (Table 1 n = 1; Table 2 Case 1 n = 1.0 and 1.4), its Darcy
+    model and literal law, FP64, each run until Nu settles."""
+    from paper_2011_15073_gb300 import lbm
+    cases = [PAPER_TABLES[1], PAPER_TABLES[4], PAPER_TABLES[5]]
+    for table, c, nu_paper in cases:
+        nus = {}
+        for N in (128, 160, 192):
+            Da = c["Da"] if c["Da"] is not None else 1e12
+            with lbm.Cavity(N, N, c["n"], Da, c["Ra"], c["Pr"], 1.0, prec="f64", porous_model=0) as cav:
+                steps, resid, why = run_until_nu_settles(cav, args.study_max_steps)
+                nus[N] = cav.nusselt()[0]
+        d1, d2 = nus[160] - nus[128], nus[192] - nus[160]
+        print(json.dumps({"study": "grid", "table": table, **c, "nu_hot": nus, "nu_paper_160": nu_paper,
+                          "rel_change_128_160": d1 / nus[160], "rel_change_160_192": d2 / nus[192],
+                          "rel_diff_160_vs_paper": (nus[160] - nu_paper) / nu_paper}), flush=True)
+
+
 DEFAULT_VARIANTS = "f64,f32,f32d@aa,f32d@tau2,f32d@tma,bf16d,f16d,f16s,bf16s,f16s@tau2"
 PRECISION_VARIANTS = ("f64", "f64@tau4", "f32", "f32@tau2", "f32d", "f16d", "bf16d", "f16s", "bf16s")
 
@@ -707,6 +727,9 @@ def main():
         return
     if args.study == "plain":
         study_plain(args)
+        return
+    if args.study == "grid":
+        study_grid(args)
         return
     if args.study == "throughput":
         study_throughput(args)

@@ -27,7 +27,7 @@ def test_bench_defines_every_leg():
     src = open(os.path.join(ROOT, "bench.py")).read()
     for fn in ("def time_ours", "def time_e2e", "def cpu_baseline", "def run_reference", "def hbm_peak",
                "def dist_env", "class Clocks", "def study_tables", "def study_precision", "def study_batch",
-               "def study_adjoint", "def main"):
+               "def study_adjoint", "def study_plain", "def study_throughput", "def study_grid", "def main"):
         assert fn in src, fn
 
 
