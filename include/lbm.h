@@ -85,8 +85,8 @@ typedef struct {
     double stag_floor; /* lbm_run_to_steady stops on stagnation only
                           below this residual (the storage's noise
                           floor); < 0: 0 for F64 (never), 1e-6 for
-                          F32 and F32D, 1e-2 for F16D, 1e-1 for
-                          BF16D                                      [-1]   */
+                          F32 and F32D, 1e-3 for F16S, 1e-2 for F16D
+                          and BF16S, 1e-1 for BF16D                  [-1]   */
     int tau_iters;     /* how the relaxation time of the strain rate and
                           the velocity solve is obtained (the paper
                           does not say: section "Power-law fluid"):
