@@ -38,10 +38,12 @@ STORAGE_NAMES = {"f64": "FP64", "f32": "FP32", "f32d": "FP32 deviation-from-rest
                  "f16d": "FP16 deviation", "f16s": "FP16 deviation (x2^15, stochastic rounding)",
                  "bf16s": "BF16 deviation (stochastic rounding)"}
 TAU_BYTES = {"f64": 16, "f32": 8, "f32d": 8, "bf16d": 8, "f16d": 8, "f16s": 8, "bf16s": 8}
+STAGING_NAMES = {1: "registers, two nodes per thread", 2: "bulk copies to shared memory",
+                 3: "registers, four nodes per thread"}
 
 
 def parse_variant(v):
-    """'prec[@aa][@tauK][@tma|@reg]' -> (prec, layout, tau_iters, staging)."""
+    """'prec[@aa][@tauK][@tma|@reg|@quad]' -> (prec, layout, tau_iters, staging)."""
     parts = v.split("@")
     layout, tau_iters, staging = 0, 0, 0
     for m in parts[1:]:
@@ -49,11 +51,28 @@ def parse_variant(v):
             layout = 1
         elif m.startswith("tau") and m[3:].isdigit():
             tau_iters = int(m[3:])
-        elif m in ("tma", "reg"):
-            staging = {"reg": 1, "tma": 2}[m]
+        elif m in ("tma", "reg", "quad"):
+            staging = {"reg": 1, "tma": 2, "quad": 3}[m]
         else:
             raise ValueError(f"unknown variant modifier {m!r} in {v!r}")
     return parts[0], layout, tau_iters, staging
+
+
+def resolved_staging(prec, tau_iters, staging, N):
+    """The step-kernel mode the library runs for lbm_opts.staging (0 = auto:
+    four nodes per thread for the 16-bit storages with lagged tau on grids of
+    at least 2048 x 2048, else two; the rule of lbm_opts.staging)."""
+    if staging:
+        return staging
+    return 3 if prec in ("bf16d", "f16d", "f16s", "bf16s") and not tau_iters and N >= 2048 else 1
+
+
+def step_kernel_name(prec, layout, tau_iters, staging, N):
+    if layout:
+        return "aa_even/aa_odd kernels (alternating)"
+    if prec == "f64":
+        return "step_kernel"
+    return {1: "step2_kernel", 2: "step_tma_kernel", 3: "step4_kernel"}[resolved_staging(prec, tau_iters, staging, N)]
 
 
 def bytes_per_node(prec, tau_iters=0):
@@ -124,8 +143,9 @@ def parse():
                     help="storage of the headline run (f32d: FP32 deviations from the rest state)")
     ap.add_argument("--layout", type=int, default=0, choices=[0, 1],
                     help="0: two buffers (pull); 1: one buffer, in-place AA-pattern streaming")
-    ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2],
-                    help="step-kernel inputs: 0 auto, 1 straight to registers, 2 bulk copies to shared memory")
+    ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="step-kernel inputs: 0 auto, 1 straight to registers (two nodes per thread), "
+                         "2 bulk copies to shared memory, 3 straight to registers (four nodes per thread)")
     ap.add_argument("--tau-iters", type=int, default=0,
                     help="0: lagged tau (stored per node); K > 0: node-local implicit tau, K Newton steps")
     ap.add_argument("--variants", default=DEFAULT_VARIANTS,
@@ -481,7 +501,7 @@ def study_grid(args):
                           "rel_diff_160_vs_paper": (nus[160] - nu_paper) / nu_paper}), flush=True)
 
 
-DEFAULT_VARIANTS = "f64,f32,f32d@aa,f32d@tau2,f32d@tma,bf16d,f16d,f16s,bf16s,f16s@tau2"
+DEFAULT_VARIANTS = "f64,f32,f32d@aa,f32d@tau2,f32d@tma,bf16d,f16d,f16s,f16s@reg,bf16s,f16s@tau2"
 PRECISION_VARIANTS = ("f64", "f64@tau4", "f32", "f32@tau2", "f32d", "f16d", "bf16d", "f16s", "bf16s")
 
 
@@ -765,7 +785,7 @@ def main():
     bpn_main = bytes_per_node(prec, args.tau_iters)
     achieved = bpn_main * N * N / kern / 1e9
     key_main = prec + (f"@tau{args.tau_iters}" if args.tau_iters else "") + \
-        {0: "", 1: "@reg", 2: "@tma"}[args.staging] + ("@aa" if args.layout else "")
+        {0: "", 1: "@reg", 2: "@tma", 3: "@quad"}[args.staging] + ("@aa" if args.layout else "")
     variants = {}
     for v in [p for p in args.variants.split(",") if p and p != key_main]:
         vs, vd = 2, args.variant_delta
@@ -779,7 +799,9 @@ def main():
                        "layout": "aa (in place)" if vl else "ab (two buffers)",
                        "tau": f"implicit, {vt} Newton steps" if vt else "lagged (stored)",
                        "dnu_rel_vs_f64_256": recorded_dnu(vp),
-                       "staging": {0: "auto", 1: "registers", 2: "bulk copies to shared memory"}[vg],
+                       "staging": ("auto: " if vg == 0 else "") +
+                                  STAGING_NAMES[resolved_staging(vp, vt, vg, N)],
+                       "kernel": step_kernel_name(vp, vl, vt, vg, N),
                        "nu_hot": nuv}
         if v == "f64":
             ipn = recorded("f64_fp64_inst_per_node")
@@ -821,9 +843,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(key_main, N),
                      "peak_source": peak_src,
-                     "kernel": ("aa_even/aa_odd kernels (alternating)" if args.layout else
-                                "step_kernel" if prec == "f64" else "step_tma_kernel" if args.staging == 2
-                                else "step2_kernel") + f"<{key_main}>",
+                     "kernel": step_kernel_name(prec, args.layout, args.tau_iters, args.staging, N) +
+                               f"<{key_main}>",
                      "bytes_per_node": bpn_main, "avg_launch_us": kern * 1e6,
                      # the arithmetic side of the same kernel: FMA-pipe activity (ncu, 2048^2)
                      "fma_pipe_active": recorded(key_main + "_fma_pipe_active")},

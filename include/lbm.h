@@ -103,11 +103,20 @@ typedef struct {
                           developed flows.  Not built with the batch
                           API or the adjoint                         [0]    */
     int staging;       /* how the step kernel of the two-buffer layout
-                          gets its inputs: 1 straight into registers;
-                          2 staged in shared memory by bulk
-                          asynchronous copies, a tile ahead (F64 gets
-                          LBM_ERR_UNSUPPORTED); 0 the faster of the
-                          two for the storage (today always 1)       [0]    */
+                          gets its inputs: 1 straight into registers,
+                          two nodes per thread; 2 staged in shared
+                          memory by bulk asynchronous copies, a tile
+                          ahead (F64 gets LBM_ERR_UNSUPPORTED); 3
+                          straight into registers, four nodes per
+                          thread (16-bit storages with tau_iters = 0
+                          only, else LBM_ERR_UNSUPPORTED); 0 the
+                          fastest measured: 3 for the 16-bit storages
+                          with lagged tau and a uniform Darcy number
+                          on grids of at least 2048 x 2048 nodes,
+                          else 1.  The update is the same; with
+                          stochastic rounding, the random bits of the
+                          nodes a mode updates one at a time (at the
+                          walls) differ between modes               [0]    */
     int graph_steps;   /* lbm_step replays a CUDA graph of this many
                           steps (rounded up to even) instead of one
                           launch per step, which pays on small,

@@ -92,10 +92,13 @@ int map_lattice(int nx, int ny, double n, double Da, double Ra, double Pr, doubl
         (o.clamp_mode != 0 && o.clamp_mode != 1) || (o.porous_model != 0 && o.porous_model != 1) ||
         !(o.s_e > 0) || !(o.s_e < 2) || !(o.s_p > 0) || !(o.s_p < 2) || o.resid_interval < 1 ||
         o.device < -1 || o.tau_iters < 0 || o.tau_iters > LBM_TAU_ITERS_MAX || o.staging < 0 ||
-        o.staging > 2 || o.graph_steps < -1)
+        o.staging > 3 || o.graph_steps < -1)
         return LBM_ERR_ARG;
     if (o.graph_steps > 0 && (o.prec == LBM_F16S || o.prec == LBM_BF16S)) return LBM_ERR_UNSUPPORTED;
     if (o.staging == 2 && o.prec == LBM_F64) return LBM_ERR_UNSUPPORTED;
+    if (o.staging == 3 && (o.tau_iters > 0 || !(o.prec == LBM_BF16D || o.prec == LBM_F16D || o.prec == LBM_F16S ||
+                                                o.prec == LBM_BF16S)))
+        return LBM_ERR_UNSUPPORTED;
     if (o.layout != 0 && o.layout != 1) return LBM_ERR_UNSUPPORTED;
     memset(L, 0, sizeof(*L));
     const double Uc = o.Ma / sqrt(3.0);

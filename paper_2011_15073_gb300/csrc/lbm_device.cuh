@@ -162,6 +162,30 @@ __host__ __device__ constexpr double rest_g(int i)  // w_i T_m with T_m = 1/2
 
 // ---------------------------------------------------------------- storage
 // ld/st move one node's value; ld2/st2 move the aligned pair (k, k+1) as F2.
+// The 16-bit storages also convert a pair held as one 32-bit word (the lower
+// node in the low half): unpack2 -> the two deviations, pack2 <- them (the
+// stochastic-rounding ones draw their random bits from rng).  ldd2/sdv2 are
+// written with them, so every path converts a pair the same way.
+__device__ __forceinline__ __half2 as_h2(uint32_t u)
+{
+    __half2 h;
+    memcpy(&h, &u, 4);
+    return h;
+}
+__device__ __forceinline__ __nv_bfloat162 as_bf162(uint32_t u)
+{
+    __nv_bfloat162 h;
+    memcpy(&h, &u, 4);
+    return h;
+}
+template <class H2>
+__device__ __forceinline__ uint32_t as_u32(H2 h)
+{
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+
 template <int PREC>
 struct Store;
 
@@ -251,13 +275,15 @@ struct Store<LBM_BF16D> {
     }
     static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __bfloat162float(p[k]); }
     static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t &) { p[k] = __float2bfloat16_rn(d); }
+    static __device__ __forceinline__ F2 unpack2(uint32_t u) { return F2(__bfloat1622float2(as_bf162(u))); }
+    static __device__ __forceinline__ uint32_t pack2(F2 d, uint32_t &) { return as_u32(__float22bfloat162_rn(d.v)); }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
     {
-        return F2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p + k)));
+        return unpack2(*reinterpret_cast<const uint32_t *>(p + k));
     }
-    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &)
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &rng)
     {
-        *reinterpret_cast<__nv_bfloat162 *>(p + k) = __float22bfloat162_rn(d.v);
+        *reinterpret_cast<uint32_t *>(p + k) = pack2(d, rng);
     }
 };
 template <>
@@ -284,13 +310,15 @@ struct Store<LBM_F16D> {
     }
     static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __half2float(p[k]); }
     static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t &) { p[k] = __float2half_rn(d); }
+    static __device__ __forceinline__ F2 unpack2(uint32_t u) { return F2(__half22float2(as_h2(u))); }
+    static __device__ __forceinline__ uint32_t pack2(F2 d, uint32_t &) { return as_u32(__float22half2_rn(d.v)); }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
     {
-        return F2(__half22float2(*reinterpret_cast<const __half2 *>(p + k)));
+        return unpack2(*reinterpret_cast<const uint32_t *>(p + k));
     }
-    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &)
+    static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &rng)
     {
-        *reinterpret_cast<__half2 *>(p + k) = __float22half2_rn(d.v);
+        *reinterpret_cast<uint32_t *>(p + k) = pack2(d, rng);
     }
 };
 
@@ -317,9 +345,16 @@ struct Store<LBM_F16S> {
     {
         p[k] = sr_half_normal((v - rest) * F16S_SCALE, sr_bits(seed, p + k) >> 16);
     }
+    static __device__ __forceinline__ F2 unpack2(uint32_t u) { return F2(__half22float2(as_h2(u))) * F2(F16S_ISCALE); }
+    static __device__ __forceinline__ uint32_t pack2(F2 d, uint32_t &rng)
+    {
+        rng = rng_next(rng);
+        const F2 ds = d * F2(F16S_SCALE);
+        return sr_half2_normal(ds.v.x, ds.v.y, rng);
+    }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
     {
-        return F2(__half22float2(*reinterpret_cast<const __half2 *>(p + k))) * F2(F16S_ISCALE);
+        return unpack2(*reinterpret_cast<const uint32_t *>(p + k));
     }
     static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float rest) { return ldd2(p, k, rest) + F2(rest); }
     static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest, uint32_t seed = 0)
@@ -335,9 +370,7 @@ struct Store<LBM_F16S> {
     }
     static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &rng)
     {
-        rng = rng_next(rng);
-        const F2 ds = d * F2(F16S_SCALE);
-        *reinterpret_cast<uint32_t *>(p + k) = sr_half2_normal(ds.v.x, ds.v.y, rng);
+        *reinterpret_cast<uint32_t *>(p + k) = pack2(d, rng);
     }
 };
 template <>
@@ -371,14 +404,19 @@ struct Store<LBM_BF16S> {
         rng = rng_next(rng);
         p[k] = sr_bf16(d, rng >> 16);
     }
+    static __device__ __forceinline__ F2 unpack2(uint32_t u) { return F2(__bfloat1622float2(as_bf162(u))); }
+    static __device__ __forceinline__ uint32_t pack2(F2 d, uint32_t &rng)
+    {
+        rng = rng_next(rng);
+        return sr_bf16x2(d.v.x, d.v.y, rng);
+    }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
     {
-        return F2(__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p + k)));
+        return unpack2(*reinterpret_cast<const uint32_t *>(p + k));
     }
     static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &rng)
     {
-        rng = rng_next(rng);
-        *reinterpret_cast<uint32_t *>(p + k) = sr_bf16x2(d.v.x, d.v.y, rng);
+        *reinterpret_cast<uint32_t *>(p + k) = pack2(d, rng);
     }
 };
 
@@ -391,6 +429,12 @@ template <int PREC>
 constexpr int dev_form()
 {
     return PREC == LBM_F64 ? 0 : 1;
+}
+// The 16-bit storages (two nodes' values per 32-bit word).
+template <int PREC>
+constexpr bool is16()
+{
+    return PREC == LBM_BF16D || PREC == LBM_F16D || PREC == LBM_F16S || PREC == LBM_BF16S;
 }
 template <int PREC, class R>
 __device__ __forceinline__ R ldf(const typename Store<PREC>::S *p, int64_t k, R rest)

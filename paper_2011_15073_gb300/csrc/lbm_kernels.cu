@@ -49,6 +49,17 @@ step2_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PRE
     step2_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
 }
 
+// Four nodes per thread (16-bit storages, lagged tau).  At most 96
+// registers, so that five 128-thread blocks fit on an SM: more bytes in
+// flight per SM than 64-register blocks of step2_kernel at eight per SM.
+template <int PREC, int FIELD>
+__global__ void __launch_bounds__(128, 5)
+step4_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
+             const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
+{
+    step4_tile<PREC, FIELD, 0>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 512, blockIdx.y);
+}
+
 // tau the next collision of every node starts from, in implicit mode (the
 // solve of implicit_tau on the streamed populations) -> out[ny][nx].
 template <int PREC, bool REV>
@@ -291,14 +302,36 @@ static cudaError_t step_buffers_tau(lbm_ctx *c, const void *src, void *dst, cons
     return cudaGetLastError();
 }
 
-// How the step kernel gets its inputs: 1 straight into registers, 2 staged
-// by bulk copies (lbm_tma.cu); 0 picks per storage (the register path, the
-// faster one measured for every storage).
+// How the step kernel gets its inputs (lbm_opts.staging, resolved): 1
+// straight into registers, two nodes per thread; 2 staged by bulk copies
+// (lbm_tma.cu); 3 straight into registers, four nodes per thread (16-bit
+// storages with lagged tau; lbm_init refuses it elsewhere).  0 picks 3 for
+// those storages on grids of at least 2048 x 2048 nodes with a uniform
+// Darcy number (measured 8-16 % faster there, and slower on 1024^2, where
+// the 128-node warps at the side walls run a larger share of the row one
+// node at a time), else 1.
 static int staging_of(const lbm_ctx *c)
 {
     if (c->opts.prec == LBM_F64) return 1;
     if (c->opts.staging != 0) return c->opts.staging;
+    const bool p16 = c->opts.prec == LBM_BF16D || c->opts.prec == LBM_F16D || c->opts.prec == LBM_F16S ||
+                     c->opts.prec == LBM_BF16S;
+    if (p16 && c->opts.tau_iters == 0 && !c->d_da && c->nx >= 2048 && c->ny >= 2048) return 3;
     return 1;
+}
+
+template <int PREC>
+static cudaError_t step4_buffers(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
+{
+    if constexpr (is16<PREC>()) {
+        using St = Store<PREC>;
+        auto *kern = c->d_da ? step4_kernel<PREC, 1> : step4_kernel<PREC, 0>;
+        kern<<<node_grid(c, 512), 128, 0, c->stream>>>((const typename St::S *)src, (typename St::S *)dst,
+                                                      (const float *)tsrc, (float *)tdst, make_params<float>(c),
+                                                      make_params<F2>(c));
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int PREC>
@@ -306,6 +339,7 @@ static cudaError_t step_buffers_t(lbm_ctx *c, const void *src, void *dst, const 
 {
     const int how = staging_of(c);
     if (how == 2) return launch_step_tma(c, src, dst, tsrc, tdst);
+    if (how == 3) return step4_buffers<PREC>(c, src, dst, tsrc, tdst);
     return c->opts.tau_iters > 0 ? step_buffers_tau<PREC, 1>(c, src, dst, tsrc, tdst)
                                  : step_buffers_tau<PREC, 0>(c, src, dst, tsrc, tdst);
 }

@@ -1,6 +1,7 @@
 // lbm_step.cuh -- bodies of the fused pull-scheme step: one node at a time
-// (any precision) and a tile of two nodes per thread (FP32 arithmetic), used
-// by the single-cavity kernels and by the batched sweep.
+// (any precision), a tile of two nodes per thread (FP32 arithmetic), used by
+// the single-cavity kernels and by the batched sweep, and a tile of four
+// nodes per thread for the 16-bit storages.
 #pragma once
 
 #include "lbm_device.cuh"
@@ -94,6 +95,104 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
 #pragma unroll
     for (int i = 0; i < 5; i++) St::sdv2(dst + (9 + i) * P, k, g[i], float(rest_g(i)), rng);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tdst + k) = tau.v;
+}
+
+// One pair of nodes of a four-node tile: the 14 stored words of the pair
+// (deviation form, already shifted to this pair's sources) -> the 14 words
+// to store and the new tau.  The same arithmetic, and the same random bits
+// (rng_init at the pair's first node), as step2_tile's pair.
+template <int PREC, int FIELD, int TAU>
+__device__ __forceinline__ F2 pair_words(const Phys<F2> &p2, const uint32_t (&in)[14], F2 tau_lag, int64_t k,
+                                         uint32_t seed, uint32_t (&out)[14])
+{
+    using St = Store<PREC>;
+    F2 f[9], g[5];
+#pragma unroll
+    for (int i = 0; i < 9; i++) f[i] = St::unpack2(in[i]);
+#pragma unroll
+    for (int i = 0; i < 5; i++) g[i] = St::unpack2(in[9 + i]);
+    const F2 t0 = tau_start<TAU, F2, FIELD, 1>(p2, f, g, k, [&] { return tau_lag; });
+    Macro<F2> m;
+    const F2 tau = collide<F2, FIELD, 1>(p2, f, g, t0, m, k);
+    uint32_t rng = rng_init(seed, k);
+#pragma unroll
+    for (int i = 0; i < 9; i++) out[i] = St::pack2(f[i], rng);
+#pragma unroll
+    for (int i = 0; i < 5; i++) out[9 + i] = St::pack2(g[i], rng);
+    return tau;
+}
+
+// Four nodes per thread for the 16-bit storages: thread t of the block
+// updates nodes xbase + 4t .. xbase + 4t + 3 of row y.  Each population row
+// is one 8-byte load per thread (twice the bytes in flight per load of
+// step2_tile, which the 16-bit storages need to keep HBM busy); the
+// x-shifted sources are assembled from the raw 16-bit words by byte
+// permutes and one warp shuffle (lane 0 / 31 load their halo word), the two
+// pairs are collided one after the other, and each population row is
+// stored as one 8-byte word.  A warp whose 128 nodes and their neighbours
+// are not all interior updates its nodes one at a time with the wall rules.
+// Results equal step2_tile's wherever both take the fast path.
+template <int PREC, int FIELD, int TAU>
+__device__ __forceinline__ void step4_tile(const typename Store<PREC>::S *__restrict__ src,
+                                           typename Store<PREC>::S *__restrict__ dst,
+                                           const float *__restrict__ tsrc, float *__restrict__ tdst,
+                                           const Phys<float> &p, const Phys<F2> &p2, int xbase, int y)
+{
+    static_assert(is16<PREC>(), "four-node tiles are built for the 16-bit storages");
+    using S = typename Store<PREC>::S;
+    const int lane = threadIdx.x & 31;
+    const int x0 = xbase + 4 * threadIdx.x;
+    const int wx = xbase + 4 * (threadIdx.x & ~31);
+    const bool fast = y > 0 && y < p.ny - 1 && wx > 0 && wx + 128 < p.nx;
+    if (!fast) {
+        for (int j = 0; j < 4; j++)
+            if (x0 + j < p.nx) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, x0 + j, y);
+        return;
+    }
+    const int64_t P = p.plane, W = p.pitch;
+    const int64_t k = (int64_t)y * W + x0;
+    // Source row offset and x-direction of population q (f0..f8, g0..g4):
+    // -1 from x - 1, +1 from x + 1.
+    const int64_t row[14] = {0, 0, -W, 0, W, -W, -W, W, W, 0, 0, -W, 0, W};
+    constexpr int side[14] = {0, -1, 0, 1, 0, -1, 1, 1, -1, 0, -1, 0, 1, 0};
+    uint2 c[14];
+    uint32_t halo[14];
+#pragma unroll
+    for (int q = 0; q < 14; q++) {
+        const S *b = src + q * P + k + row[q];
+        c[q] = *reinterpret_cast<const uint2 *>(b);
+        halo[q] = 0;
+        if (side[q] < 0 && lane == 0) halo[q] = *reinterpret_cast<const uint32_t *>(b - 2);   // [x0-2, x0-1]
+        if (side[q] > 0 && lane == 31) halo[q] = *reinterpret_cast<const uint32_t *>(b + 4);  // [x0+4, x0+5]
+    }
+    float4 lag = make_float4(0.f, 0.f, 0.f, 0.f);
+    if constexpr (TAU == 0) lag = *reinterpret_cast<const float4 *>(tsrc + k);
+    // ra: sources of nodes x0, x0+1; rb: of x0+2, x0+3.  __byte_perm(a, b,
+    // 0x5432) = (high half of a, low half of b): the pair one node earlier.
+    uint32_t ra[14], rb[14];
+#pragma unroll
+    for (int q = 0; q < 14; q++) {
+        if (side[q] < 0) {
+            uint32_t prev = __shfl_up_sync(0xffffffffu, c[q].y, 1);
+            if (lane == 0) prev = halo[q];
+            ra[q] = __byte_perm(prev, c[q].x, 0x5432);
+            rb[q] = __byte_perm(c[q].x, c[q].y, 0x5432);
+        } else if (side[q] > 0) {
+            uint32_t next = __shfl_down_sync(0xffffffffu, c[q].x, 1);
+            if (lane == 31) next = halo[q];
+            ra[q] = __byte_perm(c[q].x, c[q].y, 0x5432);
+            rb[q] = __byte_perm(c[q].y, next, 0x5432);
+        } else {
+            ra[q] = c[q].x;
+            rb[q] = c[q].y;
+        }
+    }
+    uint32_t oa[14], ob[14];
+    const F2 ta = pair_words<PREC, FIELD, TAU>(p2, ra, F2(lag.x, lag.y), k, p.seed, oa);
+    const F2 tb = pair_words<PREC, FIELD, TAU>(p2, rb, F2(lag.z, lag.w), k + 2, p.seed, ob);
+#pragma unroll
+    for (int q = 0; q < 14; q++) *reinterpret_cast<uint2 *>(dst + q * P + k) = make_uint2(oa[q], ob[q]);
+    if constexpr (TAU == 0) *reinterpret_cast<float4 *>(tdst + k) = make_float4(ta.v.x, ta.v.y, tb.v.x, tb.v.y);
 }
 
 }  // namespace lbm

@@ -76,8 +76,8 @@ def test_init_rejects_bad_arguments(L, args, code):
     ("prec", 7, -1), ("prec", -1, -1), ("Ma", 0.0, -1), ("clamp_mode", 2, -1), ("porous_model", 3, -1),
     ("s_e", 2.5, -1), ("s_p", 0.0, -1), ("resid_interval", 0, -1), ("layout", 2, -7),
     ("device", -2, -1), ("tau_iters", -1, -1), ("tau_iters", 17, -1),
-    ("staging", -1, -1), ("staging", 2, -7), ("staging", 3, -1), ("graph_steps", -2, -1),
-    # (the default storage is F64: the staged kernel is not built for it)
+    ("staging", -1, -1), ("staging", 2, -7), ("staging", 3, -7), ("staging", 4, -1), ("graph_steps", -2, -1),
+    # (the default storage is F64: neither the staged nor the four-node kernel is built for it)
 ])
 def test_init_rejects_bad_options(L, field, value, code):
     from paper_2011_15073_gb300 import lbm
@@ -85,6 +85,17 @@ def test_init_rejects_bad_options(L, field, value, code):
     o = lbm.default_opts()
     setattr(o, field, value)
     assert L.lbm_init(ctypes.byref(h), 8, 8, 0.6, 1e-2, 1e5, 6.2, 0.6, ctypes.byref(o)) == code
+
+
+@pytest.mark.parametrize("prec,tau_iters", [(0, 0), (1, 0), (4, 0), (5, 2), (6, 1), (2, 3)])
+def test_four_node_mode_is_refused_where_not_built(L, prec, tau_iters):
+    """staging = 3 (four nodes per thread) exists for the 16-bit storages
+    (2, 3, 5, 6) with lagged tau only."""
+    from paper_2011_15073_gb300 import lbm
+    h = ctypes.c_void_p()
+    o = lbm.default_opts()
+    o.prec, o.staging, o.tau_iters = prec, 3, tau_iters
+    assert L.lbm_init(ctypes.byref(h), 8, 8, 0.6, 1e-2, 1e5, 6.2, 0.6, ctypes.byref(o)) == -7
 
 
 def test_darcy_field_rejects_bad_values(L):
