@@ -67,6 +67,14 @@ def resolved_staging(prec, tau_iters, staging, N):
     return 3 if prec in ("bf16d", "f16d", "f16s", "bf16s") and not tau_iters and N >= 2048 else 1
 
 
+def staging_label(prec, layout, tau_iters, staging, N):
+    if layout:
+        return "in-place kernels (no staging choice)"
+    if prec == "f64":
+        return "registers, one node per thread"
+    return ("auto: " if staging == 0 else "") + STAGING_NAMES[resolved_staging(prec, tau_iters, staging, N)]
+
+
 def step_kernel_name(prec, layout, tau_iters, staging, N):
     if layout:
         return "aa_even/aa_odd kernels (alternating)"
@@ -799,8 +807,7 @@ def main():
                        "layout": "aa (in place)" if vl else "ab (two buffers)",
                        "tau": f"implicit, {vt} Newton steps" if vt else "lagged (stored)",
                        "dnu_rel_vs_f64_256": recorded_dnu(vp),
-                       "staging": ("auto: " if vg == 0 else "") +
-                                  STAGING_NAMES[resolved_staging(vp, vt, vg, N)],
+                       "staging": staging_label(vp, vl, vt, vg, N),
                        "kernel": step_kernel_name(vp, vl, vt, vg, N),
                        "nu_hot": nuv}
         if v == "f64":
