@@ -60,11 +60,12 @@ def parse_variant(v):
 
 def resolved_staging(prec, tau_iters, staging, N):
     """The step-kernel mode the library runs for lbm_opts.staging (0 = auto:
-    four nodes per thread for the 16-bit storages with lagged tau on grids of
-    at least 2048 x 2048, else two; the rule of lbm_opts.staging)."""
+    four nodes per thread for the 16-bit storages on grids of at least
+    2048 x 2048, 4096 x 4096 with the implicit tau, else two; the rule of
+    lbm_opts.staging)."""
     if staging:
         return staging
-    return 3 if prec in ("bf16d", "f16d", "f16s", "bf16s") and not tau_iters and N >= 2048 else 1
+    return 3 if prec in ("bf16d", "f16d", "f16s", "bf16s") and N >= (4096 if tau_iters else 2048) else 1
 
 
 def staging_label(prec, layout, tau_iters, staging, N):

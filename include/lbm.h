@@ -108,12 +108,12 @@ typedef struct {
                           memory by bulk asynchronous copies, a tile
                           ahead (F64 gets LBM_ERR_UNSUPPORTED); 3
                           straight into registers, four nodes per
-                          thread (16-bit storages with tau_iters = 0
-                          only, else LBM_ERR_UNSUPPORTED); 0 the
-                          fastest measured: 3 for the 16-bit storages
-                          with lagged tau and a uniform Darcy number
-                          on grids of at least 2048 x 2048 nodes,
-                          else 1.  The update is the same; with
+                          thread (16-bit storages only, else
+                          LBM_ERR_UNSUPPORTED); 0 the fastest
+                          measured: 3 for the 16-bit storages on grids
+                          of at least 2048 x 2048 nodes (4096 x 4096
+                          with tau_iters > 0), else 1.  The update is
+                          the same; with
                           stochastic rounding, the random bits of the
                           nodes a mode updates one at a time (at the
                           walls) differ between modes               [0]    */

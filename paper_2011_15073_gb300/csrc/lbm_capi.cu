@@ -96,8 +96,7 @@ int map_lattice(int nx, int ny, double n, double Da, double Ra, double Pr, doubl
         return LBM_ERR_ARG;
     if (o.graph_steps > 0 && (o.prec == LBM_F16S || o.prec == LBM_BF16S)) return LBM_ERR_UNSUPPORTED;
     if (o.staging == 2 && o.prec == LBM_F64) return LBM_ERR_UNSUPPORTED;
-    if (o.staging == 3 && (o.tau_iters > 0 || !(o.prec == LBM_BF16D || o.prec == LBM_F16D || o.prec == LBM_F16S ||
-                                                o.prec == LBM_BF16S)))
+    if (o.staging == 3 && !(o.prec == LBM_BF16D || o.prec == LBM_F16D || o.prec == LBM_F16S || o.prec == LBM_BF16S))
         return LBM_ERR_UNSUPPORTED;
     if (o.layout != 0 && o.layout != 1) return LBM_ERR_UNSUPPORTED;
     memset(L, 0, sizeof(*L));

@@ -49,15 +49,16 @@ step2_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PRE
     step2_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
 }
 
-// Four nodes per thread (16-bit storages, lagged tau).  At most 96
-// registers, so that five 128-thread blocks fit on an SM: more bytes in
-// flight per SM than 64-register blocks of step2_kernel at eight per SM.
-template <int PREC, int FIELD>
+// Four nodes per thread (16-bit storages).  At most 96 registers, so that
+// five 128-thread blocks fit on an SM: more bytes in flight per SM than the
+// 64-80-register blocks of step2_kernel (measured against caps of 80 and
+// 128 registers: both slower).
+template <int PREC, int FIELD, int TAU>
 __global__ void __launch_bounds__(128, 5)
 step4_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
              const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
 {
-    step4_tile<PREC, FIELD, 0>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 512, blockIdx.y);
+    step4_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 512, blockIdx.y);
 }
 
 // tau the next collision of every node starts from, in implicit mode (the
@@ -305,32 +306,41 @@ static cudaError_t step_buffers_tau(lbm_ctx *c, const void *src, void *dst, cons
 // How the step kernel gets its inputs (lbm_opts.staging, resolved): 1
 // straight into registers, two nodes per thread; 2 staged by bulk copies
 // (lbm_tma.cu); 3 straight into registers, four nodes per thread (16-bit
-// storages with lagged tau; lbm_init refuses it elsewhere).  0 picks 3 for
-// those storages on grids of at least 2048 x 2048 nodes with a uniform
-// Darcy number (measured 8-16 % faster there, and slower on 1024^2, where
-// the 128-node warps at the side walls run a larger share of the row one
-// node at a time), else 1.
+// storages only; lbm_init refuses it elsewhere).  0 picks 3 for those
+// storages on grids of at least 2048 x 2048 nodes with lagged tau, or
+// 4096 x 4096 with the implicit tau, else 1.  Measured: 8-21 % faster at
+// 4096^2 (the Darcy-field form gains most), 8 % at 2048^2 with lagged tau
+// but 2 % slower with the implicit one, and slower at 1024^2, where the
+// 128-node warps at the side walls update a larger share of each row one
+// node at a time.
 static int staging_of(const lbm_ctx *c)
 {
     if (c->opts.prec == LBM_F64) return 1;
     if (c->opts.staging != 0) return c->opts.staging;
     const bool p16 = c->opts.prec == LBM_BF16D || c->opts.prec == LBM_F16D || c->opts.prec == LBM_F16S ||
                      c->opts.prec == LBM_BF16S;
-    if (p16 && c->opts.tau_iters == 0 && !c->d_da && c->nx >= 2048 && c->ny >= 2048) return 3;
+    const int min_side = c->opts.tau_iters > 0 ? 4096 : 2048;
+    if (p16 && c->nx >= min_side && c->ny >= min_side) return 3;
     return 1;
+}
+
+template <int PREC, int TAU>
+static cudaError_t step4_buffers_tau(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
+{
+    using St = Store<PREC>;
+    auto *kern = c->d_da ? step4_kernel<PREC, 1, TAU> : step4_kernel<PREC, 0, TAU>;
+    kern<<<node_grid(c, 512), 128, 0, c->stream>>>((const typename St::S *)src, (typename St::S *)dst,
+                                                  (const float *)tsrc, (float *)tdst, make_params<float>(c),
+                                                  make_params<F2>(c));
+    return cudaGetLastError();
 }
 
 template <int PREC>
 static cudaError_t step4_buffers(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
 {
-    if constexpr (is16<PREC>()) {
-        using St = Store<PREC>;
-        auto *kern = c->d_da ? step4_kernel<PREC, 1> : step4_kernel<PREC, 0>;
-        kern<<<node_grid(c, 512), 128, 0, c->stream>>>((const typename St::S *)src, (typename St::S *)dst,
-                                                      (const float *)tsrc, (float *)tdst, make_params<float>(c),
-                                                      make_params<F2>(c));
-        return cudaGetLastError();
-    }
+    if constexpr (is16<PREC>())
+        return c->opts.tau_iters > 0 ? step4_buffers_tau<PREC, 1>(c, src, dst, tsrc, tdst)
+                                     : step4_buffers_tau<PREC, 0>(c, src, dst, tsrc, tdst);
     return cudaErrorInvalidValue;
 }
 

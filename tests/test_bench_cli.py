@@ -40,10 +40,12 @@ def test_variant_names():
     assert bench.parse_variant("bf16d@tau2@tma") == ("bf16d", 0, 2, 2)
     assert bench.parse_variant("f16s@quad") == ("f16s", 0, 0, 3)
     # the auto rule of lbm_opts.staging: four nodes per thread for the 16-bit
-    # storages with lagged tau from 2048^2 on
+    # storages from 2048^2 on (4096^2 with the implicit tau)
     assert bench.step_kernel_name("f16s", 0, 0, 0, 4096) == "step4_kernel"
+    assert bench.step_kernel_name("f16s", 0, 0, 0, 2048) == "step4_kernel"
     assert bench.step_kernel_name("f16s", 0, 0, 0, 1024) == "step2_kernel"
-    assert bench.step_kernel_name("f16s", 0, 2, 0, 4096) == "step2_kernel"
+    assert bench.step_kernel_name("f16s", 0, 2, 0, 4096) == "step4_kernel"
+    assert bench.step_kernel_name("f16s", 0, 2, 0, 2048) == "step2_kernel"
     assert bench.step_kernel_name("f16s", 0, 0, 1, 4096) == "step2_kernel"
     assert bench.step_kernel_name("f32d", 0, 0, 0, 4096) == "step2_kernel"
     assert bench.step_kernel_name("f64", 0, 0, 0, 4096) == "step_kernel"

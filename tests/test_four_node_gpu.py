@@ -40,9 +40,10 @@ def mods():
     return oracle, inputs, lbm
 
 
-def cavity(lbm, nx, ny, c, prec, staging):
+def cavity(lbm, nx, ny, c, prec, staging, tau_iters=0):
     return lbm.Cavity(nx, ny, c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec=prec,
-                      clamp_mode=c["clamp_mode"], porous_model=c["porous_model"], staging=staging)
+                      clamp_mode=c["clamp_mode"], porous_model=c["porous_model"], staging=staging,
+                      tau_iters=tau_iters)
 
 
 def fast_path(nx, ny, span):
@@ -73,15 +74,16 @@ def ordinal(codes):
 
 
 @pytest.mark.parametrize("prec", ["bf16d", "f16d", "f16s", "bf16s"])
+@pytest.mark.parametrize("tau_iters", [0, 2])
 @pytest.mark.parametrize("field", [False, True], ids=["uniform", "field"])
 @pytest.mark.parametrize("size", SIZES, ids=lambda s: f"{s[0]}x{s[1]}")
-def test_four_node_one_step_equals_two_node(mods, prec, field, size):
+def test_four_node_one_step_equals_two_node(mods, prec, tau_iters, field, size):
     oracle, inputs, lbm = mods
     nx, ny = size
     c = dict(CASES["thinning"], clamp_mode=1)
     state = inputs.perturbed_state(oracle_for(oracle, nx, ny, c).get_state(), seed=nx + 3 * ny, amp=1e-2)
     Da = inputs.darcy_field(3, nx, ny) if field else None
-    with cavity(lbm, nx, ny, c, prec, 1) as a, cavity(lbm, nx, ny, c, prec, 3) as b:
+    with cavity(lbm, nx, ny, c, prec, 1, tau_iters) as a, cavity(lbm, nx, ny, c, prec, 3, tau_iters) as b:
         if Da is not None:
             a.set_darcy_field(Da)
             b.set_darcy_field(Da)
@@ -103,13 +105,15 @@ def test_four_node_one_step_equals_two_node(mods, prec, field, size):
         assert d[:, ~same].any()
 
 
+@pytest.mark.parametrize("tau_iters", [0, 2])
 @pytest.mark.parametrize("prec,tol_f,tol_g", [("bf16d", 2e-3, 2e-2), ("f16d", 2e-4, 2.5e-3),
                                               ("bf16s", 4e-3, 4e-2), ("f16s", 4e-4, 5e-3)])
-def test_four_node_oracle_parity(mods, prec, tol_f, tol_g):
+def test_four_node_oracle_parity(mods, prec, tol_f, tol_g, tau_iters):
     oracle, inputs, lbm = mods
     nx, ny = 520, 67
     c = dict(CASES["thinning"], clamp_mode=1)
-    ref = oracle_for(oracle, nx, ny, c)
+    ref = oracle.Cavity.from_params(nx, ny, c["n"], c["Da"], c["Ra"], c["Pr"], porosity=c["porosity"],
+                                    porous_model=c["porous_model"], clamp_mode=1, tau_iters=tau_iters)
     state = inputs.perturbed_state(ref.get_state(), seed=12)
     ref.set_state(*state)
     ref.step(99)
@@ -117,22 +121,28 @@ def test_four_node_oracle_parity(mods, prec, tol_f, tol_g):
     gam_r = ref.fields()["gamma"]
     ref.step(1)
     f_r, g_r, t_r = ref.get_state()
-    with cavity(lbm, nx, ny, c, prec, 3) as cav:
+    with cavity(lbm, nx, ny, c, prec, 3, tau_iters) as cav:
         cav.set_state_f64(*state)
         cav.step(99)
         f99, g99, _ = cav.get_state_f64()
         cav.step(1)
         f, g, tau = cav.get_state_f64()
+        nu = cav.fields()["nu"]
     assert rel_err(f, f_r, W9) < tol_f
     assert rel_err(g, g_r, W5) < tol_g
     df = max(np.abs(f99 - f99_r).max(), np.abs(g99 - g99_r).max())
-    check_tau(tau, t_r, gam_r, ref.lat, prec, df)
+    if tau_iters == 0:
+        check_tau(tau, t_r, gam_r, ref.lat, prec, df)
+    else:   # no stored tau: the viscosity of the last collision, node by node
+        fr = ref.fields()
+        check_tau(3 * nu + 0.5, 3 * fr["nu"] + 0.5, fr["gamma"], ref.lat, prec,
+                  max(np.abs(f - f_r).max(), np.abs(g - g_r).max()))
 
 
 def test_four_node_mode_is_refused_where_not_built(mods):
     _, _, lbm = mods
     c = dict(CASES["thinning"], clamp_mode=1)
-    for prec, kw in [("f32d", {}), ("f32", {}), ("f16s", {"tau_iters": 2})]:
+    for prec, kw in [("f32d", {}), ("f32", {}), ("f64", {}), ("f32d", {"tau_iters": 2})]:
         with pytest.raises(lbm.LBMError) as e:
             lbm.Cavity(64, 64, c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec=prec, staging=3, **kw)
         assert e.value.code == -7   # LBM_ERR_UNSUPPORTED
