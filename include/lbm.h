@@ -100,8 +100,8 @@ typedef struct {
                           from tau0; no tau is stored, so a step moves
                           8 bytes per node less in FP32 storage.  2
                           reach FP32 rounding, 4 FP64 rounding on
-                          developed flows.  Not built with the batch
-                          API or the adjoint                         [0]    */
+                          developed flows.  Not built with the
+                          adjoint                                    [0]    */
     int staging;       /* how the step kernel of the two-buffer layout
                           gets its inputs: 1 straight into registers,
                           two nodes per thread; 2 staged in shared
@@ -274,7 +274,9 @@ int lbm_adjoint_nu(lbm_ctx *ctx, int64_t steps, int ckpt_every, int from_rest,
  * every active case (grids may differ), every resid_interval steps each
  * case's residual is checked on the device and converged cases stop being
  * stepped.  All cases share the storage precision and the options of
- * lbm_batch_create (the two-buffer layout; resid_interval must be even). */
+ * lbm_batch_create (the two-buffer layout; resid_interval must be even; the
+ * lagged or the implicit tau; not the stochastic-rounding storages, whose
+ * per-step seeds a replayed graph would repeat). */
 typedef struct {
     int nx, ny;
     double n, Da, Ra, Pr, porosity;
@@ -283,7 +285,8 @@ typedef struct {
 typedef struct lbm_batch lbm_batch;
 
 /* Create one context per case (validated as by lbm_init) on one stream.
- * Errors as lbm_init; LBM_ERR_ARG also for an odd resid_interval. */
+ * Errors as lbm_init; LBM_ERR_ARG also for an odd resid_interval;
+ * LBM_ERR_UNSUPPORTED for layout 1 and for F16S / BF16S. */
 int lbm_batch_create(lbm_batch **out, const lbm_case *cases, int ncases,
                      const lbm_opts *opts);
 void lbm_batch_destroy(lbm_batch *batch);

@@ -37,7 +37,9 @@ struct Conv {
     int since, active, reason, pad;
 };
 
-template <int PREC>
+// TAU as for step_node: 0 lagged tau (stored per node), 1 node-local
+// implicit tau (every case of a batch shares lbm_opts.tau_iters).
+template <int PREC, int TAU>
 __global__ void __launch_bounds__(256)
 batch_step_kernel(const CaseDev *__restrict__ cases, int ncases, const int *__restrict__ active, int parity)
 {
@@ -58,10 +60,11 @@ batch_step_kernel(const CaseDev *__restrict__ cases, int ncases, const int *__re
     if constexpr (PREC == LBM_F64) {
         const int x = xb * blockDim.x + threadIdx.x;
         if (x < cd.pd.nx)
-            step_node<PREC, double>(src, dst, (const double *)cd.tau[s], (double *)cd.tau[s ^ 1], cd.pd, x, y);
+            step_node<PREC, double, 2, TAU>(src, dst, (const double *)cd.tau[s], (double *)cd.tau[s ^ 1], cd.pd,
+                                            x, y);
     } else {
-        step2_tile<PREC>(src, dst, (const float *)cd.tau[s], (float *)cd.tau[s ^ 1], cd.pf, cd.p2,
-                         xb * 2 * (int)blockDim.x, y);
+        step2_tile<PREC, 2, TAU>(src, dst, (const float *)cd.tau[s], (float *)cd.tau[s ^ 1], cd.pf, cd.p2,
+                                 xb * 2 * (int)blockDim.x, y);
     }
 }
 
@@ -175,17 +178,23 @@ int upload_cases(lbm_batch *b)
     return LBM_OK;
 }
 
-cudaError_t launch_batch_step(lbm_batch *b, int parity)
+template <int TAU>
+cudaError_t launch_batch_step_tau(lbm_batch *b, int parity)
 {
     const int n = (int)b->sub.size();
     switch (b->opts.prec) {
-    case LBM_F64: batch_step_kernel<LBM_F64><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
-    case LBM_F32: batch_step_kernel<LBM_F32><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
-    case LBM_BF16D: batch_step_kernel<LBM_BF16D><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
-    case LBM_F16D: batch_step_kernel<LBM_F16D><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
-    default: batch_step_kernel<LBM_F32D><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
+    case LBM_F64: batch_step_kernel<LBM_F64, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
+    case LBM_F32: batch_step_kernel<LBM_F32, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
+    case LBM_BF16D: batch_step_kernel<LBM_BF16D, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
+    case LBM_F16D: batch_step_kernel<LBM_F16D, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
+    default: batch_step_kernel<LBM_F32D, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_step(lbm_batch *b, int parity)
+{
+    return b->opts.tau_iters > 0 ? launch_batch_step_tau<1>(b, parity) : launch_batch_step_tau<0>(b, parity);
 }
 
 double default_floor(const lbm_opts &o)
@@ -246,7 +255,7 @@ int lbm_batch_create(lbm_batch **out, const lbm_case *cases, int ncases, const l
     if (opts) o = *opts; else lbm_default_opts(&o);
     // the batched sweep replays a CUDA graph, which would replay the
     // stochastic rounding's seed too: those storages are not built here
-    if (o.layout != 0 || o.tau_iters != 0 || o.prec == LBM_F16S || o.prec == LBM_BF16S) return LBM_ERR_UNSUPPORTED;
+    if (o.layout != 0 || o.prec == LBM_F16S || o.prec == LBM_BF16S) return LBM_ERR_UNSUPPORTED;
     if (o.resid_interval < 2 || (o.resid_interval & 1)) return LBM_ERR_ARG;
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_ERR_OOM;

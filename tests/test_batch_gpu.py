@@ -3,7 +3,8 @@
 A batch steps many cavities of different sizes in one launch per step, one
 row tile per block; each case must evolve exactly as it would alone:
 * FP32: bit-for-bit equal to the same case stepped as a single context
-  (the batched kernel runs the same tile code on the same numbers);
+  (the batched kernel runs the same tile code on the same numbers), with
+  the lagged and with the node-local implicit tau;
 * FP64: within the parity bounds of test_parity_gpu against the oracle;
 * run-to-steady (host-looped graph and single device-looped graph): the same
   per-case stopping step and Nusselt numbers as lbm_run_to_steady alone.
@@ -58,6 +59,49 @@ def test_batch_fp32_equals_single_contexts(mods, tuned):
             want = cav.get_state_f64()
         for a, w in zip(got[i], want):
             assert np.array_equal(a, w), i
+
+
+@pytest.mark.parametrize("prec", ["f32", "f32d", "f64", "bf16d"])
+def test_batch_implicit_tau_equals_single_contexts(mods, prec):
+    """With the node-local implicit tau the batched kernel runs the same tile
+    (and, in FP64, node) code as a single context: bit for bit."""
+    oracle, inputs, lbm = mods
+    st = start_states(oracle, inputs, CASES)
+    with lbm.Batch(CASES, prec=prec, clamp_mode=1, tau_iters=2) as b:
+        for i, (_, s) in enumerate(st):
+            lbm.set_state_f64(b.case_ctx(i), *s)
+        b.step(37)
+        got = [lbm.get_state_f64(b.case_ctx(i), c["nx"], c["ny"]) for i, c in enumerate(CASES)]
+    for i, c in enumerate(CASES):
+        with lbm.Cavity(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec=prec,
+                        clamp_mode=1, tau_iters=2) as cav:
+            cav.set_state_f64(*st[i][1])
+            cav.step(37)
+            want = cav.get_state_f64()
+        for a, w in zip(got[i], want):
+            assert np.array_equal(a, w), i
+
+
+def test_batch_implicit_tau_fp64_parity_with_oracle(mods):
+    oracle, inputs, lbm = mods
+    cases = CASES[:3]
+    st = []
+    for i, c in enumerate(cases):
+        ref = oracle.Cavity.from_params(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"],
+                                        porosity=c["porosity"], clamp_mode=1, tau_iters=4)
+        st.append((ref, inputs.perturbed_state(ref.get_state(), seed=200 + i)))
+    with lbm.Batch(cases, prec="f64", clamp_mode=1, tau_iters=4) as b:
+        for i, (_, s) in enumerate(st):
+            lbm.set_state_f64(b.case_ctx(i), *s)
+        b.step(60)
+        got = [lbm.get_state_f64(b.case_ctx(i), c["nx"], c["ny"]) for i, c in enumerate(cases)]
+    for i, (ref, s) in enumerate(st):
+        ref.set_state(*s)
+        ref.step(60)
+        f_r, g_r, _ = ref.get_state()
+        f, g, _ = got[i]
+        assert np.max(np.abs(f - f_r) / np.abs(f_r)) < 1e-12
+        assert np.max(np.abs(g - g_r) / np.abs(g_r)) < 1e-12
 
 
 def test_batch_fp64_parity_with_oracle(mods):

@@ -137,11 +137,13 @@ def test_header_struct_matches_binding():
     assert flat == [f[0] for f in lbm.Opts._fields_]
 
 
-def test_batch_refuses_implicit_tau(L):
-    """The batched sweep is built for the lagged tau only (checked before any
-    device work)."""
+@pytest.mark.parametrize("opts", [dict(prec=5), dict(prec=6), dict(prec=6, tau_iters=2), dict(layout=1)])
+def test_batch_refuses_what_is_not_built(L, opts):
+    """The batched sweep is not built for the stochastic-rounding storages
+    (a replayed graph would repeat their seeds) or the in-place layout
+    (checked before any device work)."""
     from paper_2011_15073_gb300 import lbm
-    o = lbm.default_opts(tau_iters=2, resid_interval=1000)
+    o = lbm.default_opts(resid_interval=1000, **opts)
     case = lbm.Case(16, 16, 0.6, 1e-2, 1e5, 6.2, 0.6)
     h = ctypes.c_void_p()
     assert L.lbm_batch_create(ctypes.byref(h), ctypes.byref(case), 1, ctypes.byref(o)) == -7
