@@ -228,20 +228,22 @@ __device__ __forceinline__ void aa_odd2_body(typename Store<PREC>::S *__restrict
 }
 
 // The two-node kernels: the stochastic-rounding storages take the seed of
-// the launch from the device step count (launch_seed).
+// the launch from the device step count (launch_seed / launch_done).
 template <int PREC, int TAU, int FIELD>
 __global__ void __launch_bounds__(128)
 aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
 {
-    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p, p.slot);
+    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p);
     aa_even2_body<PREC, TAU, FIELD>(A, tau, p, p2);
+    launch_done<PREC>(p, gridDim.x * gridDim.y);
 }
 template <int PREC, int TAU, int FIELD>
 __global__ void __launch_bounds__(128)
 aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
 {
-    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p, p.slot);
+    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p);
     aa_odd2_body<PREC, TAU, FIELD>(A, tau, p, p2);
+    launch_done<PREC>(p, gridDim.x * gridDim.y);
 }
 
 // Form O -> form E in place, without a collision: each interior link
@@ -323,14 +325,8 @@ static cudaError_t aa_normalize_t(lbm_ctx *c)
     const dim3 grid((c->nx + 127) / 128, c->ny);
     aa_normalize_kernel<PREC><<<grid, 128, 0, c->stream>>>((typename St::S *)c->buf.dist[0],
                                                           make_params<typename St::R>(c));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // the form goes back to E without a step: carry the device step count
-    // to the slot the next (even) step reads
-    e = cudaMemcpyAsync(c->d_stepc, c->d_stepc + 1, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
-                        c->stream);
     c->aa_form_o = false;
-    return e;
+    return cudaGetLastError();
 }
 
 #define LBM_DISPATCH(fn, ...)                                      \

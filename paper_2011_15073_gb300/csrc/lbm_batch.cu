@@ -65,9 +65,10 @@ batch_step_kernel(const CaseDev *__restrict__ cases, int ncases, const int *__re
     } else if constexpr (is_sr<PREC>()) {   // the seed from the case's device step count
         Phys<float> pf = cd.pf;
         Phys<F2> p2 = cd.p2;
-        pf.seed = p2.seed = launch_seed<PREC>(pf, s);   // s: the case's source buffer
+        pf.seed = p2.seed = launch_seed<PREC>(pf);
         step2_tile<PREC, 2, TAU>(src, dst, (const float *)cd.tau[s], (float *)cd.tau[s ^ 1], pf, p2,
                                  xb * 2 * (int)blockDim.x, y);
+        launch_done<PREC>(pf, (unsigned)(cd.tiles_per_row * cd.pf.ny));
     } else {
         step2_tile<PREC, 2, TAU>(src, dst, (const float *)cd.tau[s], (float *)cd.tau[s ^ 1], cd.pf, cd.p2,
                                  xb * 2 * (int)blockDim.x, y);

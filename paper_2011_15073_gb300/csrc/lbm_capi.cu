@@ -250,7 +250,8 @@ int init_ctx(lbm_ctx *c)
     CK(cudaMallocHost(&c->h_err, sizeof(unsigned)));
     *c->h_err = 0;
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
-    CK(cudaMalloc(&c->d_stepc, 2 * sizeof(unsigned long long)));
+    CK(cudaMalloc(&c->d_stepc, 2 * sizeof(unsigned long long)));   // count, then the block counter
+    c->d_stepd = reinterpret_cast<unsigned *>(c->d_stepc + 1);
     CK(cudaMemsetAsync(c->d_stepc, 0, 2 * sizeof(unsigned long long), c->stream));
     CK(cudaMalloc(&c->d_nuloc, sizeof(double) * (size_t)c->ny));
     c->n_part = lbm::residual_blocks(c);
@@ -520,9 +521,6 @@ int lbm_set_state(lbm_ctx *c, const void *host, size_t bytes)
     if (!c || !host || bytes != lbm_state_bytes(c)) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
     const size_t es = c->dist_elem, ts = c->tau_elem, n = (size_t)c->nx * c->ny;
-    if (c->aa_form_o)   // back to form E without a step: carry the step count (as normalisation does)
-        CK(cudaMemcpyAsync(c->d_stepc, c->d_stepc + 1, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
-                           c->stream));
     c->aa_form_o = false;   // the whole state is replaced by a canonical one
     if (int rc0 = copy_planes(c, const_cast<void *>(host), false)) return rc0;
     CK(cudaMemcpy2DAsync(c->buf.tau[c->cur], c->pitch * ts, (const char *)host + 14 * n * es, c->nx * ts,

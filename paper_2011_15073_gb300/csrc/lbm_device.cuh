@@ -108,8 +108,8 @@ struct Phys {
     // it from the context's device step count instead (launch_seed below),
     // which replayed graphs and batched sweeps advance too.
     uint32_t seed;
-    unsigned long long *stepc;   // device step count of the context, two slots
-    int slot;                    // the slot this launch reads (its buffer parity)
+    unsigned long long *stepc;   // device step count of the context
+    unsigned *stepd;             // blocks of the current launch that are done
 };
 
 // Seed of the stochastic rounding for the step that follows `steps` steps.
@@ -159,40 +159,56 @@ inline Phys<V> make_params(const lbm_ctx *c)
     p.nu3 = V(3.0 * L.nu_ref);
     p.seed = step_seed((uint64_t)c->steps);
     p.stepc = c->d_stepc;
-    p.slot = c->opts.layout == 1 ? (c->aa_form_o ? 1 : 0) : c->cur;
+    p.stepd = c->d_stepd;
     return p;
 }
 
 // ------------------------------------------------- per-launch random seed
 // The stochastic-rounding storages (F16S, BF16S) draw new random bits every
-// step from the seed step_seed(step count).  The count lives on the device,
-// so that a replayed CUDA graph of step launches, or a batched sweep, gets a
-// new seed every step.  It has two slots, one per parity of the buffer
-// state (Phys::slot: the source buffer of the two-buffer layout, the form of
-// the in-place one): a step launch reads its slot and one thread writes the
-// next count into the other slot, which no thread of the launch reads.
-// Every step flips the parity, so the next launch reads what this one wrote;
-// where the parity changes without a step (the in-place layout's return to
-// form E), the host copies the count to the other slot.  The host's own
-// count (Phys::seed) stays in step with it for single contexts, so both give
-// the same seeds.
+// step from the seed step_seed(step count).  The count lives on the device
+// (Phys::stepc), so that a replayed CUDA graph of step launches, or a batched
+// sweep, gets a new seed every step: every block of a step launch reads the
+// count once when it starts, and the last block to finish advances it
+// (Phys::stepd counts the finished blocks; a block's read comes before its
+// own count in thread 0's program order, and the last block sees every other
+// block's count before it writes).  The host's own count (Phys::seed) stays
+// in step with it for single contexts, so both give the same seeds.
 template <int PREC>
 constexpr bool is_sr()
 {
     return PREC == LBM_F16S || PREC == LBM_BF16S;
 }
 
-// Seed of this step launch (slot: the launch's parity); other storages get
-// p.seed.
+// Seed of this launch, shared by the block.  Every thread of the block must
+// call it (it holds a barrier); other storages get p.seed without one.
 template <int PREC, class V>
-__device__ __forceinline__ uint32_t launch_seed(const Phys<V> &p, int slot)
+__device__ __forceinline__ uint32_t launch_seed(const Phys<V> &p)
 {
     if constexpr (is_sr<PREC>()) {
-        const unsigned long long s = __ldcg(p.stepc + slot);
-        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) p.stepc[slot ^ 1] = s + 1ull;
-        return step_seed(s);
+        __shared__ uint32_t block_seed;
+        if (threadIdx.x == 0) block_seed = step_seed(*(volatile unsigned long long *)p.stepc);
+        __syncthreads();
+        return block_seed;
     } else {
         return p.seed;
+    }
+}
+
+// Thread 0 of every block of a step launch, after the block's reads of the
+// count: the last of the launch's nblocks blocks advances the count and
+// resets the block counter for the next launch.
+template <int PREC, class V>
+__device__ __forceinline__ void launch_done(const Phys<V> &p, unsigned nblocks)
+{
+    if constexpr (is_sr<PREC>()) {
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(p.stepd, 1u) == nblocks - 1) {
+                *p.stepc += 1ull;
+                *p.stepd = 0u;
+                __threadfence();
+            }
+        }
     }
 }
 

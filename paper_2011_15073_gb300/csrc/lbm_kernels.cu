@@ -46,8 +46,9 @@ __global__ void __launch_bounds__(128)
 step2_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
              const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
 {
-    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p, p.slot);
+    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p);
     step2_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
+    launch_done<PREC>(p, gridDim.x * gridDim.y);
 }
 // The same for the stochastic-rounding storages with lagged tau and a
 // uniform Darcy number, held to 64 registers (eight blocks per SM, as the
@@ -58,8 +59,9 @@ __global__ void __launch_bounds__(128, 8)
 step2_sr_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
                 const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
 {
-    p.seed = p2.seed = launch_seed<PREC>(p, p.slot);
+    p.seed = p2.seed = launch_seed<PREC>(p);
     step2_tile<PREC, 0, 0>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
+    launch_done<PREC>(p, gridDim.x * gridDim.y);
 }
 
 // Four nodes per thread (16-bit storages).  At most 96 registers, so that
@@ -71,8 +73,9 @@ __global__ void __launch_bounds__(128, 5)
 step4_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
              const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
 {
-    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p, p.slot);
+    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p);
     step4_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 512, blockIdx.y);
+    launch_done<PREC>(p, gridDim.x * gridDim.y);
 }
 
 // tau the next collision of every node starts from, in implicit mode (the
