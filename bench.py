@@ -81,10 +81,7 @@ def step_kernel_name(prec, layout, tau_iters, staging, N):
         return "aa_even/aa_odd kernels (alternating)"
     if prec == "f64":
         return "step_kernel"
-    name = {1: "step2_kernel", 2: "step_tma_kernel", 3: "step4_kernel"}[resolved_staging(prec, tau_iters, staging, N)]
-    if name == "step2_kernel" and prec in ("f16s", "bf16s") and not tau_iters:
-        name = "step2_sr_kernel"   # the 64-register copy for stochastic rounding with lagged tau
-    return name
+    return {1: "step2_kernel", 2: "step_tma_kernel", 3: "step4_kernel"}[resolved_staging(prec, tau_iters, staging, N)]
 
 
 def bytes_per_node(prec, tau_iters=0):

@@ -56,12 +56,10 @@ enum {
  * bits for BF16D and F16D, in 32 bits for F32D; the per-node relaxation time
  * is then stored as FP32.  F16S and BF16S store the same 16-bit deviations
  * rounded stochastically (up or down with probability given by the distance
- * to the two neighbours; in a step, random bits hashed from the step's seed
- * and the node, the seed a hash of the context's step count, which the
- * kernels keep on the device; on import, hashed from the element's
- * address), so that updates below the 16-bit spacing are not lost on
- * average near a steady state; the paper has no counterpart (its storage is
- * not stated).  Not built with the adjoint. */
+ * to the two neighbours, random bits hashed from a per-step seed and the
+ * element's address), so that updates below the 16-bit spacing are not
+ * lost on average near a steady state; the paper has no counterpart (its
+ * storage is not stated).  Not built with the batch API or the adjoint. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_BF16D = 2, LBM_F16D = 3, LBM_F32D = 4,
                LBM_F16S = 5, LBM_BF16S = 6 } lbm_prec;
 
@@ -123,11 +121,12 @@ typedef struct {
                           steps (rounded up to even) instead of one
                           launch per step, which pays on small,
                           launch-bound grids: 0 auto (64 steps for
-                          grids of at most 512 x 512 nodes, else
-                          none); -1 never; G > 0 always.  Results are
-                          identical either way (the stochastic
-                          rounding's seeds come from the device step
-                          count, which a replay advances too).  The graph
+                          grids of at most 512 x 512 nodes whose
+                          storage is not F16S / BF16S, else none);
+                          -1 never; G > 0 always (F16S / BF16S get
+                          LBM_ERR_UNSUPPORTED: a replayed graph would
+                          repeat the stochastic rounding's seeds).
+                          Results are identical either way.  The graph
                           is captured on the context's stream at the
                           first use (and again after
                           lbm_set_darcy_field); none is used while the
@@ -276,7 +275,8 @@ int lbm_adjoint_nu(lbm_ctx *ctx, int64_t steps, int ckpt_every, int from_rest,
  * case's residual is checked on the device and converged cases stop being
  * stepped.  All cases share the storage precision and the options of
  * lbm_batch_create (the two-buffer layout; resid_interval must be even; the
- * lagged or the implicit tau; every storage). */
+ * lagged or the implicit tau; not the stochastic-rounding storages, whose
+ * per-step seeds a replayed graph would repeat). */
 typedef struct {
     int nx, ny;
     double n, Da, Ra, Pr, porosity;
@@ -286,7 +286,7 @@ typedef struct lbm_batch lbm_batch;
 
 /* Create one context per case (validated as by lbm_init) on one stream.
  * Errors as lbm_init; LBM_ERR_ARG also for an odd resid_interval;
- * LBM_ERR_UNSUPPORTED for layout 1. */
+ * LBM_ERR_UNSUPPORTED for layout 1 and for F16S / BF16S. */
 int lbm_batch_create(lbm_batch **out, const lbm_case *cases, int ncases,
                      const lbm_opts *opts);
 void lbm_batch_destroy(lbm_batch *batch);
@@ -315,8 +315,7 @@ int lbm_batch_nusselt(lbm_batch *batch, double *nu_hot, double *nu_cold);
 
 /* Autotune the batched kernel's block size (tile width) by timing `steps`
  * batched steps for each candidate on copies of the current states (the
- * states and the step counts are restored); *threads_out receives the block
- * size chosen. */
+ * states are restored); *threads_out receives the block size chosen. */
 int lbm_batch_tune(lbm_batch *batch, int steps, int *threads_out);
 
 /* Allocation-free form of lbm_residual, for callers that cannot call

@@ -104,8 +104,8 @@ aa_odd_kernel(typename Store<PREC>::S *__restrict__ A, typename Store<PREC>::Tau
 
 // ------------------------------------------------------ two nodes / thread
 template <int PREC, int TAU, int FIELD>
-__device__ __forceinline__ void aa_even2_body(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau,
-                                              const Phys<float> &p, const Phys<F2> &p2)
+__global__ void __launch_bounds__(128)
+aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
 {
     using St = Store<PREC>;
     const int x0 = (blockIdx.x * 128 + threadIdx.x) * 2, y = blockIdx.y;
@@ -166,8 +166,8 @@ __device__ __forceinline__ void push_left(typename Store<PREC>::S *base, int64_t
 }
 
 template <int PREC, int TAU, int FIELD>
-__device__ __forceinline__ void aa_odd2_body(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau,
-                                             const Phys<float> &p, const Phys<F2> &p2)
+__global__ void __launch_bounds__(128)
+aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
 {
     using St = Store<PREC>;
     using S = typename St::S;
@@ -225,25 +225,6 @@ __device__ __forceinline__ void aa_odd2_body(typename Store<PREC>::S *__restrict
     push_left<PREC>(gs + 3 * P, k, g[3], float(rest_g(3)), lane, rng);
     St::sdv2(gs + 4 * P, k - W, g[4], float(rest_g(4)), rng);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tau + k) = t.v;
-}
-
-// The two-node kernels: the stochastic-rounding storages take the seed of
-// the launch from the device step count (launch_seed / launch_done).
-template <int PREC, int TAU, int FIELD>
-__global__ void __launch_bounds__(128)
-aa_even2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
-{
-    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p);
-    aa_even2_body<PREC, TAU, FIELD>(A, tau, p, p2);
-    launch_done<PREC>(p, gridDim.x * gridDim.y);
-}
-template <int PREC, int TAU, int FIELD>
-__global__ void __launch_bounds__(128)
-aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
-{
-    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p);
-    aa_odd2_body<PREC, TAU, FIELD>(A, tau, p, p2);
-    launch_done<PREC>(p, gridDim.x * gridDim.y);
 }
 
 // Form O -> form E in place, without a collision: each interior link

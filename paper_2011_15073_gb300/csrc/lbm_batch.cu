@@ -62,13 +62,6 @@ batch_step_kernel(const CaseDev *__restrict__ cases, int ncases, const int *__re
         if (x < cd.pd.nx)
             step_node<PREC, double, 2, TAU>(src, dst, (const double *)cd.tau[s], (double *)cd.tau[s ^ 1], cd.pd,
                                             x, y);
-    } else if constexpr (is_sr<PREC>()) {   // the seed from the case's device step count
-        Phys<float> pf = cd.pf;
-        Phys<F2> p2 = cd.p2;
-        pf.seed = p2.seed = launch_seed<PREC>(pf);
-        step2_tile<PREC, 2, TAU>(src, dst, (const float *)cd.tau[s], (float *)cd.tau[s ^ 1], pf, p2,
-                                 xb * 2 * (int)blockDim.x, y);
-        launch_done<PREC>(pf, (unsigned)(cd.tiles_per_row * cd.pf.ny));
     } else {
         step2_tile<PREC, 2, TAU>(src, dst, (const float *)cd.tau[s], (float *)cd.tau[s ^ 1], cd.pf, cd.p2,
                                  xb * 2 * (int)blockDim.x, y);
@@ -194,8 +187,6 @@ cudaError_t launch_batch_step_tau(lbm_batch *b, int parity)
     case LBM_F32: batch_step_kernel<LBM_F32, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
     case LBM_BF16D: batch_step_kernel<LBM_BF16D, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
     case LBM_F16D: batch_step_kernel<LBM_F16D, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
-    case LBM_F16S: batch_step_kernel<LBM_F16S, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
-    case LBM_BF16S: batch_step_kernel<LBM_BF16S, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
     default: batch_step_kernel<LBM_F32D, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
     }
     return cudaGetLastError();
@@ -209,15 +200,7 @@ cudaError_t launch_batch_step(lbm_batch *b, int parity)
 double default_floor(const lbm_opts &o)
 {
     if (o.stag_floor >= 0) return o.stag_floor;
-    switch (o.prec) {   // as lbm_run_to_steady
-    case LBM_F64: return 0.0;
-    case LBM_F32:
-    case LBM_F32D: return 1e-6;
-    case LBM_F16S: return 1e-3;
-    case LBM_F16D:
-    case LBM_BF16S: return 1e-2;
-    default: return 1e-1;
-    }
+    return o.prec == LBM_F64 ? 0.0 : ((o.prec == LBM_F32 || o.prec == LBM_F32D) ? 1e-6 : (o.prec == LBM_F16D ? 1e-2 : 1e-1));
 }
 
 // Enqueue one chunk: `delta` steps of every active case, their residuals and
@@ -270,7 +253,9 @@ int lbm_batch_create(lbm_batch **out, const lbm_case *cases, int ncases, const l
     if (!cases || ncases < 1) return LBM_ERR_ARG;
     lbm_opts o;
     if (opts) o = *opts; else lbm_default_opts(&o);
-    if (o.layout != 0) return LBM_ERR_UNSUPPORTED;
+    // the batched sweep replays a CUDA graph, which would replay the
+    // stochastic rounding's seed too: those storages are not built here
+    if (o.layout != 0 || o.prec == LBM_F16S || o.prec == LBM_BF16S) return LBM_ERR_UNSUPPORTED;
     if (o.resid_interval < 2 || (o.resid_interval & 1)) return LBM_ERR_ARG;
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_ERR_OOM;
@@ -470,22 +455,17 @@ int lbm_batch_tune(lbm_batch *b, int steps, int *threads_out)
     if (!b || steps < 2) return LBM_ERR_ARG;
     BK(cudaSetDevice(b->device));
     steps &= ~1;  // even: every case ends in the buffer it started in
-    // keep the states (and the device step counts that seed the stochastic
-    // rounding): time on copies, restore afterwards
+    // keep the states: time on copies, restore afterwards
     std::vector<void *> save_d(b->sub.size(), nullptr), save_t(b->sub.size(), nullptr);
-    std::vector<unsigned long long> save_c(2 * b->sub.size(), 0ull);
     int rc = LBM_OK;
     for (size_t i = 0; i < b->sub.size() && rc == LBM_OK; i++) {
         lbm_ctx *c = b->sub[i];
         const size_t db = c->dist_elem * 14 * (size_t)c->plane, tb = c->tau_elem * (size_t)c->plane;
         if (cudaMalloc(&save_d[i], db) != cudaSuccess || cudaMalloc(&save_t[i], tb) != cudaSuccess ||
             cudaMemcpyAsync(save_d[i], c->buf.dist[c->cur], db, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
-            cudaMemcpyAsync(save_t[i], c->buf.tau[c->cur], tb, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess ||
-            cudaMemcpyAsync(&save_c[2 * i], c->d_stepc, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                            b->stream) != cudaSuccess)
+            cudaMemcpyAsync(save_t[i], c->buf.tau[c->cur], tb, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
             rc = LBM_ERR_CUDA;
     }
-    if (rc == LBM_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
     const int cand[3] = {64, 128, 256};
     float best_ms = 1e30f;
     int best = b->threads;
@@ -516,8 +496,6 @@ int lbm_batch_tune(lbm_batch *b, int steps, int *threads_out)
             cudaMemcpyAsync(c->buf.dist[c->cur], save_d[i], c->dist_elem * 14 * (size_t)c->plane,
                             cudaMemcpyDeviceToDevice, b->stream);
             cudaMemcpyAsync(c->buf.tau[c->cur], save_t[i], c->tau_elem * (size_t)c->plane, cudaMemcpyDeviceToDevice,
-                            b->stream);
-            cudaMemcpyAsync(c->d_stepc, &save_c[2 * i], 2 * sizeof(unsigned long long), cudaMemcpyHostToDevice,
                             b->stream);
         }
     }

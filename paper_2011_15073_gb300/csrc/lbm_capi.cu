@@ -38,7 +38,8 @@ int graph_len_for(const lbm_ctx *c)
     const int g = c->opts.graph_steps;
     if (g < 0) return 0;
     if (g > 0) return (g + 1) & ~1;
-    return (int64_t)c->nx * c->ny <= 512 * 512 ? 64 : 0;
+    const bool sr = c->opts.prec == LBM_F16S || c->opts.prec == LBM_BF16S;
+    return (!sr && (int64_t)c->nx * c->ny <= 512 * 512) ? 64 : 0;
 }
 
 int graph_parity(const lbm_ctx *c) { return c->opts.layout == 1 ? (c->aa_form_o ? 1 : 0) : c->cur; }
@@ -93,6 +94,7 @@ int map_lattice(int nx, int ny, double n, double Da, double Ra, double Pr, doubl
         o.device < -1 || o.tau_iters < 0 || o.tau_iters > LBM_TAU_ITERS_MAX || o.staging < 0 ||
         o.staging > 3 || o.graph_steps < -1)
         return LBM_ERR_ARG;
+    if (o.graph_steps > 0 && (o.prec == LBM_F16S || o.prec == LBM_BF16S)) return LBM_ERR_UNSUPPORTED;
     if (o.staging == 2 && o.prec == LBM_F64) return LBM_ERR_UNSUPPORTED;
     if (o.staging == 3 && !(o.prec == LBM_BF16D || o.prec == LBM_F16D || o.prec == LBM_F16S || o.prec == LBM_BF16S))
         return LBM_ERR_UNSUPPORTED;
@@ -144,7 +146,6 @@ void free_ctx(lbm_ctx *c)
     cudaFree(c->d_da);
     cudaFree(c->d_err);
     cudaFreeHost(c->h_err);
-    cudaFree(c->d_stepc);
     drop_graphs(c);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -250,9 +251,6 @@ int init_ctx(lbm_ctx *c)
     CK(cudaMallocHost(&c->h_err, sizeof(unsigned)));
     *c->h_err = 0;
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
-    CK(cudaMalloc(&c->d_stepc, 2 * sizeof(unsigned long long)));   // count, then the block counter
-    c->d_stepd = reinterpret_cast<unsigned *>(c->d_stepc + 1);
-    CK(cudaMemsetAsync(c->d_stepc, 0, 2 * sizeof(unsigned long long), c->stream));
     CK(cudaMalloc(&c->d_nuloc, sizeof(double) * (size_t)c->ny));
     c->n_part = lbm::residual_blocks(c);
     CK(cudaMalloc(&c->d_part, sizeof(double) * 8 * (size_t)c->n_part));

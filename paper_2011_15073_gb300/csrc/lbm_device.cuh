@@ -103,20 +103,9 @@ struct Phys {
     // collision, their start tau0 and 3 nu_ref.
     int tau_iters;
     V tau0, nu3;
-    // Seed of the stochastic rounding of this launch (a new one every step),
-    // as the host counts steps.  The stochastic-rounding step kernels take
-    // it from the context's device step count instead (launch_seed below),
-    // which replayed graphs and batched sweeps advance too.
+    // Seed of the stochastic rounding of this launch (a new one every step).
     uint32_t seed;
-    unsigned long long *stepc;   // device step count of the context
-    unsigned *stepd;             // blocks of the current launch that are done
 };
-
-// Seed of the stochastic rounding for the step that follows `steps` steps.
-__host__ __device__ __forceinline__ uint32_t step_seed(uint64_t steps)
-{
-    return mix32(0x9e3779b9u * (uint32_t)(steps + 1) ^ (uint32_t)(steps >> 32));
-}
 
 // ------------------------------------------------------------ parameters
 template <class V>
@@ -157,59 +146,8 @@ inline Phys<V> make_params(const lbm_ctx *c)
     p.tau_iters = c->opts.tau_iters;
     p.tau0 = V(L.tau0);
     p.nu3 = V(3.0 * L.nu_ref);
-    p.seed = step_seed((uint64_t)c->steps);
-    p.stepc = c->d_stepc;
-    p.stepd = c->d_stepd;
+    p.seed = mix32(0x9e3779b9u * (uint32_t)(c->steps + 1) ^ (uint32_t)((uint64_t)c->steps >> 32));
     return p;
-}
-
-// ------------------------------------------------- per-launch random seed
-// The stochastic-rounding storages (F16S, BF16S) draw new random bits every
-// step from the seed step_seed(step count).  The count lives on the device
-// (Phys::stepc), so that a replayed CUDA graph of step launches, or a batched
-// sweep, gets a new seed every step: every block of a step launch reads the
-// count once when it starts, and the last block to finish advances it
-// (Phys::stepd counts the finished blocks; a block's read comes before its
-// own count in thread 0's program order, and the last block sees every other
-// block's count before it writes).  The host's own count (Phys::seed) stays
-// in step with it for single contexts, so both give the same seeds.
-template <int PREC>
-constexpr bool is_sr()
-{
-    return PREC == LBM_F16S || PREC == LBM_BF16S;
-}
-
-// Seed of this launch, shared by the block.  Every thread of the block must
-// call it (it holds a barrier); other storages get p.seed without one.
-template <int PREC, class V>
-__device__ __forceinline__ uint32_t launch_seed(const Phys<V> &p)
-{
-    if constexpr (is_sr<PREC>()) {
-        __shared__ uint32_t block_seed;
-        if (threadIdx.x == 0) block_seed = step_seed(*(volatile unsigned long long *)p.stepc);
-        __syncthreads();
-        return block_seed;
-    } else {
-        return p.seed;
-    }
-}
-
-// Thread 0 of every block of a step launch, after the block's reads of the
-// count: the last of the launch's nblocks blocks advances the count and
-// resets the block counter for the next launch.
-template <int PREC, class V>
-__device__ __forceinline__ void launch_done(const Phys<V> &p, unsigned nblocks)
-{
-    if constexpr (is_sr<PREC>()) {
-        if (threadIdx.x == 0) {
-            __threadfence();
-            if (atomicAdd(p.stepd, 1u) == nblocks - 1) {
-                *p.stepc += 1ull;
-                *p.stepd = 0u;
-                __threadfence();
-            }
-        }
-    }
 }
 
 // Rest-state values used by the deviation storage forms.

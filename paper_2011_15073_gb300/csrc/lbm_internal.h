@@ -47,10 +47,6 @@ struct lbm_ctx {
     void *d_da = nullptr;        // per-node Darcy numbers (compute type), or null
     unsigned *d_err = nullptr;   // raised by a kernel whose bounded wait gave up
     unsigned *h_err = nullptr;   // pinned mirror of d_err
-    // Device step count for the stochastic rounding's seeds, and the count
-    // of finished blocks of the running step launch (one allocation).
-    unsigned long long *d_stepc = nullptr;
-    unsigned *d_stepd = nullptr;
     // Replayed step graphs (lbm_step), one per parity of the buffer state
     // (two-buffer: which buffer is current; in place: odd-step form).
     cudaGraphExec_t step_graph[2] = {nullptr, nullptr};

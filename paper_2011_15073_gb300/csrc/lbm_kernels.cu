@@ -46,22 +46,7 @@ __global__ void __launch_bounds__(128)
 step2_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
              const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
 {
-    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p);
     step2_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
-    launch_done<PREC>(p, gridDim.x * gridDim.y);
-}
-// The same for the stochastic-rounding storages with lagged tau and a
-// uniform Darcy number, held to 64 registers (eight blocks per SM, as the
-// other storages get without the cap; the launch-seed code alone made the
-// compiler take 72).
-template <int PREC>
-__global__ void __launch_bounds__(128, 8)
-step2_sr_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
-                const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
-{
-    p.seed = p2.seed = launch_seed<PREC>(p);
-    step2_tile<PREC, 0, 0>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
-    launch_done<PREC>(p, gridDim.x * gridDim.y);
 }
 
 // Four nodes per thread (16-bit storages).  At most 96 registers, so that
@@ -73,9 +58,7 @@ __global__ void __launch_bounds__(128, 5)
 step4_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
              const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
 {
-    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p);
     step4_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 512, blockIdx.y);
-    launch_done<PREC>(p, gridDim.x * gridDim.y);
 }
 
 // tau the next collision of every node starts from, in implicit mode (the
@@ -313,8 +296,6 @@ static cudaError_t step_buffers_tau(lbm_ctx *c, const void *src, void *dst, cons
             (typename St::TauS *)tdst, make_params<typename St::R>(c));
     } else {
         auto *kern = c->d_da ? step2_kernel<PREC, 1, TAU> : step2_kernel<PREC, 0, TAU>;
-        if constexpr (is_sr<PREC>() && TAU == 0)
-            if (!c->d_da) kern = step2_sr_kernel<PREC>;
         kern<<<node_grid(c, 256), 128, 0, c->stream>>>(
             (const typename St::S *)src, (typename St::S *)dst, (const float *)tsrc, (float *)tdst,
             make_params<float>(c), make_params<F2>(c));

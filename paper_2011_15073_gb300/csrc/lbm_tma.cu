@@ -192,7 +192,6 @@ step_tma_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<
 {
     using G = TmaGeom<PREC>;
     constexpr int NS = G::STAGES;
-    if constexpr (is_sr<PREC>()) p.seed = p2.seed = launch_seed<PREC>(p);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[NS], empty[NS];
     constexpr int SB = G::stage_bytes(TAU);
@@ -248,7 +247,6 @@ step_tma_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
     }
-    launch_done<PREC>(p, gridDim.x);
 }
 
 // ------------------------------------------------------------- launcher

@@ -82,27 +82,6 @@ def test_batch_implicit_tau_equals_single_contexts(mods, prec):
             assert np.array_equal(a, w), i
 
 
-@pytest.mark.parametrize("prec", ["f16s", "bf16s"])
-@pytest.mark.parametrize("tau_iters", [0, 2])
-def test_batch_stochastic_equals_single_contexts(mods, prec, tau_iters):
-    """The stochastic-rounding storages in a batch: each case draws the seeds
-    of its own device step count, as a single context does, so from the rest
-    state (no import rounding) the cases evolve bit for bit as alone."""
-    _, _, lbm = mods
-    with lbm.Batch(CASES, prec=prec, clamp_mode=1, tau_iters=tau_iters) as b:
-        b.step(37)
-        b.step(20)
-        got = [lbm.get_state_f64(b.case_ctx(i), c["nx"], c["ny"]) for i, c in enumerate(CASES)]
-    for i, c in enumerate(CASES):
-        with lbm.Cavity(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec=prec,
-                        clamp_mode=1, tau_iters=tau_iters, graph_steps=-1) as cav:
-            cav.step(57)
-            want = cav.get_state_f64()
-        for a, w in zip(got[i], want):
-            assert np.array_equal(a, w), i
-    assert got[0][1].std() > 0   # the thermal field has left the rest state
-
-
 def test_batch_implicit_tau_fp64_parity_with_oracle(mods):
     oracle, inputs, lbm = mods
     cases = CASES[:3]

@@ -43,11 +43,10 @@ def test_variant_names():
     # storages from 2048^2 on (4096^2 with the implicit tau)
     assert bench.step_kernel_name("f16s", 0, 0, 0, 4096) == "step4_kernel"
     assert bench.step_kernel_name("f16s", 0, 0, 0, 2048) == "step4_kernel"
-    assert bench.step_kernel_name("f16s", 0, 0, 0, 1024) == "step2_sr_kernel"
-    assert bench.step_kernel_name("f16d", 0, 0, 0, 1024) == "step2_kernel"
+    assert bench.step_kernel_name("f16s", 0, 0, 0, 1024) == "step2_kernel"
     assert bench.step_kernel_name("f16s", 0, 2, 0, 4096) == "step4_kernel"
     assert bench.step_kernel_name("f16s", 0, 2, 0, 2048) == "step2_kernel"
-    assert bench.step_kernel_name("f16s", 0, 0, 1, 4096) == "step2_sr_kernel"
+    assert bench.step_kernel_name("f16s", 0, 0, 1, 4096) == "step2_kernel"
     assert bench.step_kernel_name("f32d", 0, 0, 0, 4096) == "step2_kernel"
     assert bench.step_kernel_name("f64", 0, 0, 0, 4096) == "step_kernel"
     assert bench.step_kernel_name("f32d", 0, 0, 2, 4096) == "step_tma_kernel"

@@ -137,10 +137,11 @@ def test_header_struct_matches_binding():
     assert flat == [f[0] for f in lbm.Opts._fields_]
 
 
-@pytest.mark.parametrize("opts", [dict(layout=1), dict(layout=1, prec=5), dict(layout=1, prec=4)])
+@pytest.mark.parametrize("opts", [dict(prec=5), dict(prec=6), dict(prec=6, tau_iters=2), dict(layout=1)])
 def test_batch_refuses_what_is_not_built(L, opts):
-    """The batched sweep is not built for the in-place layout (checked
-    before any device work)."""
+    """The batched sweep is not built for the stochastic-rounding storages
+    (a replayed graph would repeat their seeds) or the in-place layout
+    (checked before any device work)."""
     from paper_2011_15073_gb300 import lbm
     o = lbm.default_opts(resid_interval=1000, **opts)
     case = lbm.Case(16, 16, 0.6, 1e-2, 1e5, 6.2, 0.6)
@@ -149,3 +150,10 @@ def test_batch_refuses_what_is_not_built(L, opts):
     assert h.value is None
 
 
+def test_graphs_refused_for_stochastic_storages(L):
+    """A replayed graph would repeat the stochastic rounding's seeds."""
+    from paper_2011_15073_gb300 import lbm
+    for prec in ("f16s", "bf16s"):
+        o = lbm.default_opts(prec=prec, graph_steps=16)
+        h = ctypes.c_void_p()
+        assert L.lbm_init(ctypes.byref(h), 8, 8, 0.6, 1e-2, 1e5, 6.2, 0.6, ctypes.byref(o)) == -7

@@ -3,12 +3,7 @@ replays a captured CUDA graph of an even number of step launches.  The
 graph holds the same kernels with the same arguments, so a run must be bit
 for bit the run of one launch per step, whatever the layout, storage, step
 count (remainders, odd starts) and after the Darcy field changes (which
-drops and recaptures the graphs).  For the stochastic-rounding storages this
-also checks that a replay draws a new seed every step, as plain launches do
-(the kernels take it from the context's device step count): a repeated seed
-rounds differently.  Those runs start from the rest state, because
-importing a state rounds it with bits drawn from the element addresses,
-which differ between two contexts."""
+drops and recaptures the graphs)."""
 import numpy as np
 import pytest
 
@@ -27,8 +22,7 @@ def mods():
 def run(lbm, inputs, nx, ny, prec, layout, graph_steps, chunks, Da=None, Da2=None):
     with lbm.Cavity(nx, ny, CASE["n"], CASE["Da"], CASE["Ra"], CASE["Pr"], CASE["porosity"], prec=prec,
                     layout=layout, clamp_mode=CASE["clamp_mode"], graph_steps=graph_steps) as cav:
-        if prec not in ("f16s", "bf16s"):
-            cav.set_state_f64(*inputs.perturbed_state(cav.get_state_f64(), seed=nx + ny, amp=1e-2))
+        cav.set_state_f64(*inputs.perturbed_state(cav.get_state_f64(), seed=nx + ny, amp=1e-2))
         if Da is not None:
             cav.set_darcy_field(Da)
         for i, k in enumerate(chunks):
@@ -39,7 +33,7 @@ def run(lbm, inputs, nx, ny, prec, layout, graph_steps, chunks, Da=None, Da2=Non
 
 
 @pytest.mark.parametrize("layout", [0, 1], ids=["ab", "aa"])
-@pytest.mark.parametrize("prec", ["f64", "f32d", "f16d", "f16s", "bf16s"])
+@pytest.mark.parametrize("prec", ["f64", "f32d", "f16d"])
 @pytest.mark.parametrize("graph_steps", [0, 16, 7])
 def test_graph_replay_equals_plain_launches(mods, layout, prec, graph_steps):
     inputs, lbm = mods
@@ -51,31 +45,13 @@ def test_graph_replay_equals_plain_launches(mods, layout, prec, graph_steps):
         assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("prec", ["f32d", "f16s"])
-def test_graph_recaptured_after_darcy_field_change(mods, prec):
+def test_graph_recaptured_after_darcy_field_change(mods):
     inputs, lbm = mods
     nx, ny = 96, 40
     Da = inputs.darcy_field(3, nx, ny)
     Da2 = inputs.darcy_field(4, nx, ny)
     chunks = [128, 128, 128, 128]
-    a = run(lbm, inputs, nx, ny, prec, 0, -1, chunks, Da, Da2)
-    b = run(lbm, inputs, nx, ny, prec, 0, 32, chunks, Da, Da2)
+    a = run(lbm, inputs, nx, ny, "f32d", 0, -1, chunks, Da, Da2)
+    b = run(lbm, inputs, nx, ny, "f32d", 0, 32, chunks, Da, Da2)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
-
-
-def test_stochastic_graph_run_differs_from_a_repeated_seed(mods):
-    """The stochastic rounding does depend on the seed: two runs whose step
-    counts start apart (one made a step more before) end in different states
-    after the same number of further steps, graphs or not."""
-    inputs, lbm = mods
-    out = []
-    for pre in (0, 2):
-        with lbm.Cavity(64, 48, CASE["n"], CASE["Da"], CASE["Ra"], CASE["Pr"], CASE["porosity"], prec="f16s",
-                        clamp_mode=CASE["clamp_mode"], graph_steps=16) as cav:
-            f, g, tau = cav.get_state_f64()
-            cav.step(pre)
-            cav.set_state_f64(f, g, tau)   # the rest state again (exact: deviations 0)
-            cav.step(160)
-            out.append(cav.get_state_f64()[0])
-    assert not np.array_equal(out[0], out[1])
