@@ -456,7 +456,11 @@ void orc_collide_node(const orc_lattice *lat, const double f[9],
  *     non-dimensional v-momentum equation), T_m = (T_h + T_c) / 2;
  *   K = Da L^2;  tau = 3 nu + 1/2 (Eq. kinematic_viscosity, c_s^2 = 1/3).
  * Porous model 1 uses the Ergun factor F_eps = 1.75 / sqrt(150 eps^3).
- * Pinned by: the conduction limit and the physics trend tests.
+ * Pinned by tests/test_oracle_mapping.py, which measures the viscosity a
+ * sheared node takes, the momentum one collision adds through buoyancy and
+ * drag, and the diffusion rate of transient conduction, and checks them
+ * against the dimensional groups of Eq. (non_dim_var), the non-dimensional
+ * equations, Eq. (MPL) and a Fourier-series conduction solution.
  * ------------------------------------------------------------------------- */
 int orc_map_params(int nx, int ny, double n, double Da, double Ra, double Pr,
                    double porosity, double Ma, int porous_model,
@@ -519,6 +523,11 @@ struct orc_ctx {
 
 static double K_at(const orc_ctx *c, size_t q) { return c->Kf ? c->Kf[q] : c->p.K; }
 
+/* Per-node permeability K(x) = Da(x) L^2 (reading R17 of the Darcy term of
+ * the momentum equations, node by node).  Pinned by: a uniform field equals
+ * the uniform-K run bit for bit (and the uniform K is pinned against
+ * Da = K / L^2), and a field differing at one node changes that node's
+ * collision into the one of a uniform run at the node's Da and no other. */
 void orc_set_darcy_field(orc_ctx *c, const double *Da)
 {
     if (!Da) {
