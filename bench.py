@@ -38,12 +38,11 @@ STORAGE_NAMES = {"f64": "FP64", "f32": "FP32", "f32d": "FP32 deviation-from-rest
                  "f16d": "FP16 deviation", "f16s": "FP16 deviation (x2^15, stochastic rounding)",
                  "bf16s": "BF16 deviation (stochastic rounding)"}
 TAU_BYTES = {"f64": 16, "f32": 8, "f32d": 8, "bf16d": 8, "f16d": 8, "f16s": 8, "bf16s": 8}
-STAGING_NAMES = {1: "registers, two nodes per thread", 2: "bulk copies to shared memory",
-                 3: "registers, four nodes per thread"}
+STAGING_NAMES = {1: "registers, two nodes per thread", 3: "registers, four nodes per thread"}
 
 
 def parse_variant(v):
-    """'prec[@aa][@tauK][@tma|@reg|@quad]' -> (prec, layout, tau_iters, staging)."""
+    """'prec[@aa][@tauK][@reg|@quad]' -> (prec, layout, tau_iters, staging)."""
     parts = v.split("@")
     layout, tau_iters, staging = 0, 0, 0
     for m in parts[1:]:
@@ -51,8 +50,8 @@ def parse_variant(v):
             layout = 1
         elif m.startswith("tau") and m[3:].isdigit():
             tau_iters = int(m[3:])
-        elif m in ("tma", "reg", "quad"):
-            staging = {"reg": 1, "tma": 2, "quad": 3}[m]
+        elif m in ("reg", "quad"):
+            staging = {"reg": 1, "quad": 3}[m]
         else:
             raise ValueError(f"unknown variant modifier {m!r} in {v!r}")
     return parts[0], layout, tau_iters, staging
@@ -81,7 +80,7 @@ def step_kernel_name(prec, layout, tau_iters, staging, N):
         return "aa_even/aa_odd kernels (alternating)"
     if prec == "f64":
         return "step_kernel"
-    return {1: "step2_kernel", 2: "step_tma_kernel", 3: "step4_kernel"}[resolved_staging(prec, tau_iters, staging, N)]
+    return {1: "step2_kernel", 3: "step4_kernel"}[resolved_staging(prec, tau_iters, staging, N)]
 
 
 def bytes_per_node(prec, tau_iters=0):
@@ -159,20 +158,23 @@ def parse():
                     help="storage of the headline run (f32d: FP32 deviations from the rest state)")
     ap.add_argument("--layout", type=int, default=0, choices=[0, 1],
                     help="0: two buffers (pull); 1: one buffer, in-place AA-pattern streaming")
-    ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--staging", type=int, default=0, choices=[0, 1, 3],
                     help="step-kernel inputs: 0 auto, 1 straight to registers (two nodes per thread), "
-                         "2 bulk copies to shared memory, 3 straight to registers (four nodes per thread)")
+                         "3 straight to registers (four nodes per thread)")
     ap.add_argument("--tau-iters", type=int, default=0,
                     help="0: lagged tau (stored per node); K > 0: node-local implicit tau, K Newton steps")
     ap.add_argument("--variants", default=DEFAULT_VARIANTS,
                     help="other storage precisions measured beside the headline ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--study", choices=["tables", "precision", "batch", "adjoint", "plain", "throughput", "grid"],
+    ap.add_argument("--study", choices=["tables", "precision", "batch", "adjoint", "plain", "throughput", "grid",
+                                        "sensitivity"],
                     default=None,
                     help="physics studies instead of the throughput bench (one JSON line per case)")
     ap.add_argument("--study-N", type=int, default=None)
     ap.add_argument("--study-max-steps", type=int, default=3_000_000)
+    ap.add_argument("--study-prec", default="f32d", help="storage of --study sensitivity")
+    ap.add_argument("--readings", default="", help="';'-separated labels of --study sensitivity (all if empty)")
     return ap.parse_args()
 
 
@@ -497,6 +499,79 @@ def study_tables(args):
                           "seconds": time.perf_counter() - t}), flush=True)
 
 
+def batched_tables(cases, N, opts, max_steps, chunk=20000, window=6, rel=2e-5):
+    """Run table cases as one batch (each a cavity of N x N nodes with the
+    paper's Darcy model; clear fluid as Da = 1e12) in chunks of `chunk` steps
+    until the hot-wall Nu of every case spreads by at most `rel` over the last
+    `window` chunks, or max_steps.  Returns per case (mean Nu over the window,
+    relative spread, steps); the mean is the time average of a limit cycle."""
+    import numpy as np
+
+    from paper_2011_15073_gb300 import lbm
+    cl = [dict(nx=N, ny=N, n=c["n"], Da=c["Da"] if c["Da"] is not None else 1e12, Ra=c["Ra"], Pr=c["Pr"],
+               porosity=1.0) for c in cases]
+    hist = [[] for _ in cl]
+    done = 0
+    with lbm.Batch(cl, porous_model=0, **opts) as b:
+        while done < max_steps:
+            b.step(chunk)
+            done += chunk
+            hot, _ = b.nusselt()
+            if not np.all(np.isfinite(hot)):
+                raise RuntimeError("non-finite Nu in the table batch")
+            for h, v in zip(hist, hot):
+                h.append(float(v))
+            if all(len(h) >= window and max(h[-window:]) - min(h[-window:]) <= rel * abs(h[-1]) for h in hist):
+                break
+    out = []
+    for h in hist:
+        w = h[-window:]
+        m = sum(w) / len(w)
+        out.append((m, (max(w) - min(w)) / abs(m), done))
+    return out
+
+
+# Extra cases beside the paper's: the clear fluid at the porous cases' Pr, and
+# the most permeable porous case at Table 1's Pr (do Pr and drag separate?).
+SENSITIVITY_EXTRA = [
+    ("diag", dict(n=0.6, Da=None, Ra=1e5, Pr=6.2), None),
+    ("diag", dict(n=0.6, Da=1e-1, Ra=1e5, Pr=100.0), None),
+]
+SENSITIVITY_READINGS = [
+    # (label, options, N, Ma)
+    ("literal clamp, lagged tau", dict(clamp_mode=0), 160, 0.1),
+    ("continuous clamp, lagged tau", dict(clamp_mode=1), 160, 0.1),
+    ("literal clamp, implicit tau", dict(clamp_mode=0, tau_iters=2), 160, 0.1),
+    ("literal clamp, Ma 0.05", dict(clamp_mode=0), 160, 0.05),
+    ("continuous clamp, Ma 0.05", dict(clamp_mode=1), 160, 0.05),
+    ("literal clamp, 256^2", dict(clamp_mode=0), 256, 0.1),
+    ("continuous clamp, 256^2", dict(clamp_mode=1), 256, 0.1),
+]
+
+
+def study_sensitivity(args):
+    """Which reading of the unstated parts moves the paper's table values:
+    the clamp of Eq. (MPL) (literal jump at gamma_1 or continuous), the
+    lagged or node-local implicit tau, the Mach number of the velocity scale,
+    and the grid.  FP32-deviation storage (its steady states are within 1e-4
+    of FP64's), the paper's Darcy model, the batched API, one batch per
+    reading."""
+    cases = PAPER_TABLES + SENSITIVITY_EXTRA
+    sel = [r for r in SENSITIVITY_READINGS if not args.readings or r[0] in args.readings.split(";")]
+    for label, opts, N, Ma in sel:
+        N = args.study_N or N
+        max_steps = int(args.study_max_steps * (0.1 / Ma) * (N / 160))
+        t = time.perf_counter()
+        res = batched_tables([c for _, c, _ in cases], N, dict(prec=args.study_prec, Ma=Ma, **opts), max_steps)
+        secs = time.perf_counter() - t
+        for (table, c, nu_paper), (m, spread, steps) in zip(cases, res):
+            print(json.dumps({"study": "sensitivity", "reading": label, "N": N, "Ma": Ma, **opts,
+                              "prec": args.study_prec, "table": table, **c, "nu_hot_mean": m,
+                              "spread": spread, "nu_paper": nu_paper,
+                              "rel_diff": None if nu_paper is None else (m - nu_paper) / nu_paper,
+                              "steps": steps, "batch_seconds": secs}), flush=True)
+
+
 def study_grid(args):
     """Grid independence of the average hot-wall Nu at 128^2, 160^2 and
     192^2 (the paper reports choosing 160^2 without showing the study): three
@@ -517,7 +592,7 @@ def study_grid(args):
                           "rel_diff_160_vs_paper": (nus[160] - nu_paper) / nu_paper}), flush=True)
 
 
-DEFAULT_VARIANTS = "f64,f32,f32d@aa,f32d@tau2,f32d@tma,bf16d,f16d,f16s,f16s@reg,bf16s,f16s@tau2"
+DEFAULT_VARIANTS = "f64,f32,f32d@aa,f32d@tau2,bf16d,f16d,f16s,f16s@reg,bf16s,f16s@tau2"
 PRECISION_VARIANTS = ("f64", "f64@tau4", "f32", "f32@tau2", "f32d", "f16d", "bf16d", "f16s", "bf16s")
 
 
@@ -767,6 +842,9 @@ def main():
     if args.study == "grid":
         study_grid(args)
         return
+    if args.study == "sensitivity":
+        study_sensitivity(args)
+        return
     if args.study == "throughput":
         study_throughput(args)
         return
@@ -801,7 +879,7 @@ def main():
     bpn_main = bytes_per_node(prec, args.tau_iters)
     achieved = bpn_main * N * N / kern / 1e9
     key_main = prec + (f"@tau{args.tau_iters}" if args.tau_iters else "") + \
-        {0: "", 1: "@reg", 2: "@tma", 3: "@quad"}[args.staging] + ("@aa" if args.layout else "")
+        {0: "", 1: "@reg", 3: "@quad"}[args.staging] + ("@aa" if args.layout else "")
     variants = {}
     for v in [p for p in args.variants.split(",") if p and p != key_main]:
         vs, vd = 2, args.variant_delta

@@ -40,8 +40,8 @@ enum {
     LBM_ERR_NONFINITE = -3, /* NaN or Inf found in the fields              */
     LBM_ERR_CUDA = -4,      /* a CUDA runtime call failed                  */
     LBM_ERR_OOM = -5,       /* device memory allocation failed             */
-    LBM_ERR_TIMEOUT = -6,   /* a bounded device wait gave up (sticky: the
-                               run's state is no longer valid)        */
+    LBM_ERR_TIMEOUT = -6,   /* a bounded device wait gave up (reserved: no
+                               kernel of this version waits)          */
     LBM_ERR_UNSUPPORTED = -7,/* option combination not built              */
     LBM_ERR_SIZE = -8       /* grid larger than a fixed-size scratch area  */
 };
@@ -104,12 +104,10 @@ typedef struct {
                           adjoint                                    [0]    */
     int staging;       /* how the step kernel of the two-buffer layout
                           gets its inputs: 1 straight into registers,
-                          two nodes per thread; 2 staged in shared
-                          memory by bulk asynchronous copies, a tile
-                          ahead (F64 gets LBM_ERR_UNSUPPORTED); 3
-                          straight into registers, four nodes per
-                          thread (16-bit storages only, else
-                          LBM_ERR_UNSUPPORTED); 0 the fastest
+                          two nodes per thread; 3 straight into
+                          registers, four nodes per thread (16-bit
+                          storages only, else LBM_ERR_UNSUPPORTED);
+                          2 is not built (LBM_ERR_UNSUPPORTED); 0 the fastest
                           measured: 3 for the 16-bit storages on grids
                           of at least 2048 x 2048 nodes (4096 x 4096
                           with tau_iters > 0), else 1.  The update is
@@ -342,7 +340,8 @@ int lbm_batch_tune(lbm_batch *batch, int steps, int *threads_out);
  * that loaded it until the process exits; grids with more rows are refused
  * with LBM_ERR_SIZE.  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress), so make it before any stream
- * capture.  All calls share the array and it keeps the last call's contents
+ * capture; a call that finds the device's context replaced since (after a
+ * cudaDeviceReset) looks it up again.  All calls share the array and it keeps the last call's contents
  * (every slot a call reads is written earlier in the same call); calls that
  * overlap on the GPU, e.g. on two streams, race on it.
  * Contexts with the in-place layout (layout = 1) get LBM_ERR_UNSUPPORTED.

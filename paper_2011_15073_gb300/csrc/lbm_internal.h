@@ -45,8 +45,6 @@ struct lbm_ctx {
     int n_part = 0;
     double *d_nuloc = nullptr;   // local hot-wall Nu [ny]
     void *d_da = nullptr;        // per-node Darcy numbers (compute type), or null
-    unsigned *d_err = nullptr;   // raised by a kernel whose bounded wait gave up
-    unsigned *h_err = nullptr;   // pinned mirror of d_err
     // Replayed step graphs (lbm_step), one per parity of the buffer state
     // (two-buffer: which buffer is current; in place: odd-step form).
     cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
@@ -73,9 +71,6 @@ cudaError_t launch_export_f64(lbm_ctx *c, double *d_dst15);
 // In-place (AA) layout (lbm_aa.cu): one step, and the conversion of the
 // odd-step form back to the canonical one (no-op if already canonical).
 cudaError_t launch_aa_step(lbm_ctx *c);
-// The same step with the inputs staged by bulk asynchronous copies
-// (lbm_tma.cu; FP32-arithmetic storages only).
-cudaError_t launch_step_tma(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst);
 cudaError_t launch_aa_normalize(lbm_ctx *c);
 int residual_blocks(const lbm_ctx *c);
 

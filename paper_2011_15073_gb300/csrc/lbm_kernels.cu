@@ -304,9 +304,9 @@ static cudaError_t step_buffers_tau(lbm_ctx *c, const void *src, void *dst, cons
 }
 
 // How the step kernel gets its inputs (lbm_opts.staging, resolved): 1
-// straight into registers, two nodes per thread; 2 staged by bulk copies
-// (lbm_tma.cu); 3 straight into registers, four nodes per thread (16-bit
-// storages only; lbm_init refuses it elsewhere).  0 picks 3 for those
+// straight into registers, two nodes per thread; 3 straight into registers,
+// four nodes per thread (16-bit storages only; lbm_init refuses it elsewhere,
+// and refuses 2 everywhere).  0 picks 3 for those
 // storages on grids of at least 2048 x 2048 nodes with lagged tau, or
 // 4096 x 4096 with the implicit tau, else 1.  Measured: 8-21 % faster at
 // 4096^2 (the Darcy-field form gains most), 8 % at 2048^2 with lagged tau
@@ -348,7 +348,6 @@ template <int PREC>
 static cudaError_t step_buffers_t(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
 {
     const int how = staging_of(c);
-    if (how == 2) return launch_step_tma(c, src, dst, tsrc, tdst);
     if (how == 3) return step4_buffers<PREC>(c, src, dst, tsrc, tdst);
     return c->opts.tau_iters > 0 ? step_buffers_tau<PREC, 1>(c, src, dst, tsrc, tdst)
                                  : step_buffers_tau<PREC, 0>(c, src, dst, tsrc, tdst);

@@ -4,6 +4,7 @@
 // Its only scratch is the file-scope array below: one slot of partial sums
 // per grid row, LBM_NOALLOC_MAX_ROWS rows at most (1 MiB).  Every GPU that
 // loads this library holds the array until the process exits.
+#include <cuda.h>  // CUcontext / CUresult types only; no link against libcuda
 #include <math.h>
 #include <stdio.h>
 
@@ -20,19 +21,44 @@ static __device__ __align__(256) double g_row_partials[LBM_NOALLOC_MAX_ROWS * kS
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_scratch[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};  // context the address belongs to
+
+// cuCtxGetCurrent, fetched through the runtime (the library links only the
+// CUDA runtime); null if the driver does not offer it.
+typedef CUresult (*ctx_get_current_fn)(CUcontext *);
+ctx_get_current_fn ctx_get_current()
+{
+    static ctx_get_current_fn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<ctx_get_current_fn>(p);
+    }();
+    return fn;
+}
 
 // Device address of g_row_partials on device `dev` (current).  In host code
 // the symbol's name is only a host-side stand-in, so the address must come
-// from cudaGetSymbolAddress, once per device.
+// from cudaGetSymbolAddress: once per device, and again if the device's
+// context was replaced since (a cudaDeviceReset destroys the primary
+// context, and the array lives at a new address in the next one).  Without
+// cuCtxGetCurrent the address is looked up on every call.
 int scratch_address(int dev, double **out)
 {
     if (dev < 0 || dev >= kMaxDevices) return LBM_ERR_ARG;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch[dev]) {
+    CUcontext cur = nullptr;
+    const ctx_get_current_fn get = ctx_get_current();
+    const bool known = get && get(&cur) == CUDA_SUCCESS && cur;
+    if (!g_scratch[dev] || !known || cur != g_scratch_ctx[dev]) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_row_partials);
         if (e != cudaSuccess || !p) return LBM_ERR_CUDA;
         g_scratch[dev] = static_cast<double *>(p);
+        g_scratch_ctx[dev] = known ? cur : nullptr;
     }
     *out = g_scratch[dev];
     return LBM_OK;

@@ -37,7 +37,7 @@ def test_variant_names():
     assert bench.parse_variant("f32@aa") == ("f32", 1, 0, 0)
     assert bench.parse_variant("f32@tau2") == ("f32", 0, 2, 0)
     assert bench.parse_variant("f32d@aa@tau3") == ("f32d", 1, 3, 0)
-    assert bench.parse_variant("bf16d@tau2@tma") == ("bf16d", 0, 2, 2)
+    assert bench.parse_variant("bf16d@tau2@reg") == ("bf16d", 0, 2, 1)
     assert bench.parse_variant("f16s@quad") == ("f16s", 0, 0, 3)
     # the auto rule of lbm_opts.staging: four nodes per thread for the 16-bit
     # storages from 2048^2 on (4096^2 with the implicit tau)
@@ -49,10 +49,11 @@ def test_variant_names():
     assert bench.step_kernel_name("f16s", 0, 0, 1, 4096) == "step2_kernel"
     assert bench.step_kernel_name("f32d", 0, 0, 0, 4096) == "step2_kernel"
     assert bench.step_kernel_name("f64", 0, 0, 0, 4096) == "step_kernel"
-    assert bench.step_kernel_name("f32d", 0, 0, 2, 4096) == "step_tma_kernel"
     assert bench.bytes_per_node("f32", 2) == 112 and bench.bytes_per_node("f64", 1) == 224
     with pytest.raises(ValueError):
         bench.parse_variant("f32@bogus")
+    with pytest.raises(ValueError):
+        bench.parse_variant("f32d@tma")   # the staged kernel is not built
 
 
 def test_reduced_storage_summary_picks_fastest_within_the_bar():

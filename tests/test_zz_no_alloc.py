@@ -16,8 +16,15 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_noalloc_residual_matches_lbm_residual(prec):
+# (storage, per-node Darcy field, implicit tau steps): the residual kernel
+# reads the state through the same pull and velocity solve as the step, so
+# each storage form, the field and the implicit tau take their own path
+VARIANTS = [("f64", False, 0), ("f32", False, 0), ("bf16d", False, 0), ("f16s", False, 0),
+            ("f32", True, 2), ("f64", True, 4)]
+
+
+@pytest.mark.parametrize("prec,field,tau_iters", VARIANTS)
+def test_noalloc_residual_matches_lbm_residual(prec, field, tau_iters):
     torch = pytest.importorskip("torch")
     import oracle
     from paper_2011_15073_gb300 import inputs, lbm
@@ -29,7 +36,9 @@ def test_noalloc_residual_matches_lbm_residual(prec):
     state = inputs.perturbed_state(rest.get_state(), seed=21)
     snap = torch.empty(3 * nx * ny, dtype=torch.float64, device="cuda:0")
     out = torch.empty(4, dtype=torch.float64, device="cuda:0")
-    with lbm.Cavity(nx, ny, prec=prec, device=0, **case) as cav:
+    with lbm.Cavity(nx, ny, prec=prec, device=0, tau_iters=tau_iters, **case) as cav:
+        if field:
+            cav.set_darcy_field(inputs.darcy_field(31, nx, ny))
         cav.set_state_f64(*state)
         assert math.isinf(cav.residual())
         lbm.residual_noalloc(cav.ctx, snap.data_ptr(), True, out.data_ptr())
