@@ -139,9 +139,15 @@ def recorded_traffic(prec, N):
     return recorded(prec, N)
 
 
-# FP64 pipe of this part: 2 FP64 lanes per SM per cycle (measured in
-# profiles/step_kernel_f64_1536.md), 152 SMs.
-FP64_LANES_PER_SM, N_SM = 2, 152
+
+def alu_peaks(lbm):
+    """Measured FMA throughput of this GPU (lbm_bench_fma_peak): thread-level
+    instructions per second for FP64, FP32 and packed FP32x2 FMAs."""
+    out = {}
+    for kind in ("f64", "f32", "f32x2"):
+        fma, inst = lbm.bench_fma_peak(kind, reps=20)
+        out[kind] = {"fma_per_s": fma, "inst_per_s": inst, "flop_per_s": 2 * fma}
+    return out
 
 
 def parse():
@@ -174,6 +180,10 @@ def parse():
     ap.add_argument("--study-N", type=int, default=None)
     ap.add_argument("--study-max-steps", type=int, default=3_000_000)
     ap.add_argument("--study-prec", default="f32d", help="storage of --study sensitivity")
+    ap.add_argument("--sr-runs", type=int, default=4,
+                    help="rounding streams per stochastic-rounding storage in --study precision")
+    ap.add_argument("--h-sweep", type=lambda t: [float(x) for x in t.split(",") if x], default=[],
+                    help="comma-separated difference steps (log Da) for --study adjoint's single-node sweep")
     ap.add_argument("--readings", default="", help="';'-separated labels of --study sensitivity (all if empty)")
     return ap.parse_args()
 
@@ -614,11 +624,19 @@ def study_precision(args):
         case = dict(n=n, Da=1e-2, Ra=1e5, Pr=6.2, porosity=0.6)
         res = {}
         S = None
+        # the stochastic-rounding storages run once per rounding stream
+        # (lbm_opts.seed), labelled variant#seed beyond the default stream
+        runs = []
         for v in ["f64"] + [x for x in variants if x != "f64"]:
-            prec, layout, tau_iters, staging = parse_variant(v)
+            runs.append(v)
+            if parse_variant(v)[0] in ("f16s", "bf16s"):
+                runs += [f"{v}#{s}" for s in range(1, args.sr_runs)]
+        for v in runs:
+            prec, layout, tau_iters, staging = parse_variant(v.split("#")[0])
+            seed = int(v.split("#")[1]) if "#" in v else 0
             t = time.perf_counter()
             with lbm.Cavity(N, N, prec=prec, resid_interval=1000, clamp_mode=1, layout=layout, tau_iters=tau_iters,
-                            staging=staging, **case) as cav:
+                            staging=staging, seed=seed, **case) as cav:
                 samples = []
                 if v == "f64":
                     S, resid, why = cav.run_to_steady(1e-10, args.study_max_steps)
@@ -647,6 +665,14 @@ def study_precision(args):
                               "dnu_mean_rel": (r["nu_mean"] - ref["nu"]) / ref["nu"], "l2_rel": err,
                               "steps": r["steps"], "residual": r["resid"], "stop": r["stop"],
                               "seconds": r["sec"]}), flush=True)
+        for v in variants:
+            reps = [r for k, r in res.items() if k.split("#")[0] == v]
+            if len(reps) > 1:
+                d = [(r["nu_mean"] - ref["nu"]) / ref["nu"] for r in reps]
+                print(json.dumps({"study": "precision", "N": N, **case, "clamp_mode": 1, "variant": v,
+                                  "streams": len(reps), "dnu_mean_rel_per_stream": d,
+                                  "dnu_mean_rel_mean": float(np.mean(d)), "dnu_mean_rel_spread": float(np.std(d)),
+                                  "dnu_mean_rel_max_abs": float(np.max(np.abs(d)))}), flush=True)
 
 
 def study_plain(args):
@@ -801,6 +827,21 @@ def study_adjoint(args):
             ad = res[prec]["dDa"][j, i] * Da[j, i]
             fd_rel.append(dict(node=[j, i], prec=prec, fd=fd, adjoint=ad,
                                rel=abs(ad - fd) / max(abs(fd), 1e-300)))
+    # step sweep of the single-node differences: truncation shrinks with h^2,
+    # the rounding of J (FP64, 10,000 steps) grows with 1/h
+    sweep = {}
+    for hs in args.h_sweep:
+        rel64, rel32 = [], []
+        for (j, i) in nodes:
+            Dp, Dm = Da.copy(), Da.copy()
+            Dp[j, i] *= np.exp(hs)
+            Dm[j, i] *= np.exp(-hs)
+            fd = (J_of(Dp) - J_of(Dm)) / (2 * hs)
+            for prec, out in (("f64", rel64), ("f32", rel32)):
+                ad = res[prec]["dDa"][j, i] * Da[j, i]
+                out.append(abs(ad - fd) / max(abs(fd), 1e-300))
+        sweep[repr(hs)] = {"max_rel_f64": max(rel64), "median_rel_f64": float(np.median(rel64)),
+                           "max_rel_f32": max(rel32), "median_rel_f32": float(np.median(rel32))}
     v = rng.standard_normal((N, N))
     fd_dir = (J_of(Da * np.exp(h * v)) - J_of(Da * np.exp(-h * v))) / (2 * h)
     dir_ad = {p_: float(np.sum(res[p_]["dDa"] * Da * v)) for p_ in ("f64", "f32")}
@@ -819,6 +860,7 @@ def study_adjoint(args):
                          "rel_f32": abs(dir_ad["f32"] - fd_dir) / abs(fd_dir)},
         "f32_vs_f64_dDa_rel_l2": float(np.linalg.norm(f32["dDa"] - f64["dDa"]) / np.linalg.norm(f64["dDa"])),
         "fd_nodes": fd_rel,
+        "fd_nodes_h_sweep": sweep,
     }), flush=True)
 
 
@@ -880,6 +922,7 @@ def main():
     achieved = bpn_main * N * N / kern / 1e9
     key_main = prec + (f"@tau{args.tau_iters}" if args.tau_iters else "") + \
         {0: "", 1: "@reg", 3: "@quad"}[args.staging] + ("@aa" if args.layout else "")
+    peaks = alu_peaks(lbm)
     variants = {}
     for v in [p for p in args.variants.split(",") if p and p != key_main]:
         vs, vd = 2, args.variant_delta
@@ -898,14 +941,13 @@ def main():
                        "nu_hot": nuv}
         if v == "f64":
             ipn = recorded("f64_fp64_inst_per_node")
-            mhz = clk_summary_max(clk)
-            if ipn and mhz:
-                peak_inst = FP64_LANES_PER_SM * N_SM * mhz * 1e6
+            if ipn:
+                peak_inst = peaks["f64"]["inst_per_s"]
                 ach = N * N / kv * ipn
                 variants[v]["roofline"] = {"bound": "alu", "unit": "FP64 inst/s", "achieved": ach,
                                            "peak": peak_inst, "frac": ach / peak_inst,
                                            "fp64_inst_per_node": ipn,
-                                           "peak_source": "2 FP64 lanes/SM/cycle x 152 SMs x max SM clock"}
+                                           "peak_source": "measured: lbm_bench_fma_peak FP64 FMA throughput"}
     # launch-bound small grid: one launch per step against replayed step graphs
     small = {"grid": [256, 256], "storage": "f32d", "fused_steps": 2 * 5000}
     for key, gs in (("MLUPS_one_launch_per_step", -1), ("MLUPS_replayed_graphs", 0)):
@@ -949,6 +991,7 @@ def main():
         "variants": variants,
         "reduced_storage": reduced_storage_summary(variants, prec, mlups),
         "small_grid": small,
+        "alu_peaks": peaks,
     }
     print(json.dumps(line), flush=True)
 

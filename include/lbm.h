@@ -129,6 +129,11 @@ typedef struct {
                           first use (and again after
                           lbm_set_darcy_field); none is used while the
                           stream is already being captured          [0]    */
+    uint64_t seed;     /* stream of the stochastic rounding (F16S,
+                          BF16S): mixed into every step's seed, so runs
+                          with different seeds round independently;
+                          0 is the default stream.  Other storages
+                          ignore it                                  [0]    */
 } lbm_opts;
 
 /* Lattice-unit parameters the library derived from the problem groups

@@ -268,6 +268,7 @@ void lbm_default_opts(lbm_opts *o)
     o->tau_iters = 0;
     o->staging = 0;
     o->graph_steps = 0;
+    o->seed = 0;
 }
 
 int lbm_init(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra, double Pr,

@@ -146,7 +146,10 @@ inline Phys<V> make_params(const lbm_ctx *c)
     p.tau_iters = c->opts.tau_iters;
     p.tau0 = V(L.tau0);
     p.nu3 = V(3.0 * L.nu_ref);
-    p.seed = mix32(0x9e3779b9u * (uint32_t)(c->steps + 1) ^ (uint32_t)((uint64_t)c->steps >> 32));
+    // the run's own stream (lbm_opts.seed; 0 leaves the default stream)
+    const uint64_t s = c->opts.seed;
+    const uint32_t run = s ? mix32((uint32_t)s ^ mix32((uint32_t)(s >> 32) + 0x68e31da4u)) : 0u;
+    p.seed = mix32(0x9e3779b9u * (uint32_t)(c->steps + 1) ^ (uint32_t)((uint64_t)c->steps >> 32) ^ run);
     return p;
 }
 

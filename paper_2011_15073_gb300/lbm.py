@@ -42,7 +42,7 @@ class Opts(ctypes.Structure):
                 ("resid_interval", ctypes.c_int), ("layout", ctypes.c_int),
                 ("cuda_stream", ctypes.c_void_p), ("device", ctypes.c_int),
                 ("stag_floor", ctypes.c_double), ("tau_iters", ctypes.c_int), ("staging", ctypes.c_int),
-                ("graph_steps", ctypes.c_int)]
+                ("graph_steps", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
 class Lattice(ctypes.Structure):
@@ -94,6 +94,7 @@ SIGNATURES = [
     ("lbm_batch_tune", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("lbm_adjoint_nu", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]),
     ("lbm_residual_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
+    ("lbm_bench_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("lbm_last_cuda_error", ctypes.c_char_p, []),
 ]
@@ -256,6 +257,16 @@ def get_state_f64(ctx, nx, ny):
 def set_state_f64(ctx, f=None, g=None, tau=None):
     conv = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (f, g, tau)]
     _check(lib().lbm_set_state_f64(ctx, *[_ptr(a) for a in conv]), "lbm_set_state_f64")
+
+
+def bench_fma_peak(kind: str, device: int = -1, reps: int = 20):
+    """Measured FMA throughput (lbm_bench.h): kind 'f64', 'f32' or 'f32x2'
+    -> (thread-level FMAs per second, instructions per second)."""
+    k = {"f64": 0, "f32": 1, "f32x2": 2}[kind]
+    f = ctypes.c_double()
+    i = ctypes.c_double()
+    _check(lib().lbm_bench_fma_peak(k, device, reps, ctypes.byref(f), ctypes.byref(i)), "lbm_bench_fma_peak")
+    return f.value, i.value
 
 
 def strerror(code: int) -> str:

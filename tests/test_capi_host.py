@@ -132,7 +132,8 @@ def test_header_struct_matches_binding():
     src = open(os.path.join(ROOT, "include", "lbm.h")).read()
     body = src[src.index("typedef struct {\n    int prec;"):src.index("} lbm_opts;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-    names = re.findall(r"\b(?:int|double|void\s*\*)\s*\**\s*(\w+(?:\s*,\s*\w+)*)\s*;", body.split("{", 1)[1])
+    names = re.findall(r"\b(?:int|double|uint64_t|void\s*\*)\s*\**\s*(\w+(?:\s*,\s*\w+)*)\s*;",
+                       body.split("{", 1)[1])
     flat = [n.strip() for grp in names for n in grp.split(",")]
     assert flat == [f[0] for f in lbm.Opts._fields_]
 
@@ -157,3 +158,13 @@ def test_graphs_refused_for_stochastic_storages(L):
         o = lbm.default_opts(prec=prec, graph_steps=16)
         h = ctypes.c_void_p()
         assert L.lbm_init(ctypes.byref(h), 8, 8, 0.6, 1e-2, 1e5, 6.2, 0.6, ctypes.byref(o)) == -7
+
+
+def test_fma_probe_rejects_bad_arguments():
+    """lbm_bench_fma_peak validates its arguments before touching a device."""
+    import ctypes
+    from paper_2011_15073_gb300 import lbm
+    out = ctypes.c_double()
+    assert lbm.lib().lbm_bench_fma_peak(3, -1, 5, ctypes.byref(out), None) == -1
+    assert lbm.lib().lbm_bench_fma_peak(0, -1, 0, ctypes.byref(out), None) == -1
+    assert lbm.lib().lbm_bench_fma_peak(0, -1, 5, None, None) == -1

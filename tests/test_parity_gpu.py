@@ -231,6 +231,32 @@ def test_deviation_storage_parity(mods, prec, tol_f, tol_g, layout):
     check_tau(tau, t_r, gam_r, ref.lat, prec, df)
 
 
+@pytest.mark.parametrize("prec,tol_f,tol_g", [("bf16s", 4e-3, 4e-2), ("f16s", 4e-4, 5e-3)])
+def test_rounding_stream_seed(mods, prec, tol_f, tol_g):
+    """lbm_opts.seed selects another stochastic-rounding stream: the states
+    differ from the default stream's, and both stay within the stochastic
+    bounds of the oracle after 100 steps."""
+    oracle, inputs, lbm = mods
+    nx, ny = 130, 67
+    c = dict(CASES["thinning"], clamp_mode=1)
+    ref = oracle_for(oracle, nx, ny, c)
+    state = inputs.perturbed_state(ref.get_state(), seed=11)
+    ref.set_state(*state)
+    ref.step(100)
+    f_r, g_r, _ = ref.get_state()
+    out = {}
+    for seed in (0, 7):
+        with lbm.Cavity(nx, ny, c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec=prec,
+                        porous_model=c["porous_model"], clamp_mode=1, seed=seed) as cav:
+            cav.set_state_f64(*state)
+            cav.step(100)
+            out[seed] = cav.get_state_f64()[:2]
+    for f, g in out.values():
+        assert rel_err(f, f_r, W9) < tol_f
+        assert rel_err(g, g_r, W5) < tol_g
+    assert not np.array_equal(out[0][0], out[7][0])
+
+
 @pytest.mark.parametrize("prec,tol_f,tol_g", [("f32", 2e-6, 2e-6)])
 @pytest.mark.parametrize("case", ["thinning", "thickening", "newtonian"])
 @pytest.mark.parametrize("size", [(17, 13), (130, 67), (258, 9)], ids=lambda s: f"{s[0]}x{s[1]}")
