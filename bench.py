@@ -728,44 +728,68 @@ def study_throughput(args):
 def study_batch(args):
     """The paper's kind of sweep (27 cases, n x Da x Ra, grids 128^2-512^2 drawn
     by seed) run to steady state as one batched workload -- one CUDA graph
-    launch looping on the device, block size from the autotuner -- against
-    the same cases run one after another with lbm_run_to_steady."""
+    launch looping on the device, execution plan from the autotuner --
+    against the same cases run one after another with lbm_run_to_steady.
+    FP32 storage cannot bring the residual to 1e-8 (its rounding floor is
+    near 1e-5), so a case also retires on stagnation: no new minimum over 10
+    checks while below 1e-4.  Reported per case: steps, final residual, stop
+    rule, Nu, the Nu drift over 10,000 further steps of the retired state,
+    and for the three smallest cases the hot-wall Nu of an FP64 run to
+    r < 1e-8."""
     from paper_2011_15073_gb300 import inputs, lbm
     max_steps = args.study_max_steps if args.study_max_steps != 3_000_000 else 1_000_000
     cl = [dict(nx=c["N"], ny=c["N"], n=c["n"], Da=c["Da"], Ra=c["Ra"], Pr=6.2, porosity=0.6)
           for c in inputs.sweep_cases(2011)]
-    # FP32 storage cannot bring the residual to 1e-8 (its rounding keeps it
-    # near 1e-5): stagnation below 1e-4 ends a case
-    opts = dict(prec="f32", clamp_mode=1, resid_interval=1000, stag_floor=1e-4)
+    floor = 1e-4
+    opts = dict(prec="f32", clamp_mode=1, resid_interval=1000, stag_floor=floor)
     with lbm.Batch(cl, **opts) as b:
         t = time.perf_counter()
         threads = b.tune(200)
         t_tune = time.perf_counter() - t
+        plan = b.plan()
         t = time.perf_counter()
         steps, res, why = b.run_to_steady(1e-8, max_steps, graph_mode=1)
         t_batch = time.perf_counter() - t
         hot, _ = b.nusselt()
+        b.step(10_000)
+        hot_later, _ = b.nusselt()
     t = time.perf_counter()
     seq = []
     for c in cl:
         with lbm.Cavity(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], **opts) as cav:
-            s, r, w = cav.run_to_steady(1e-8, max_steps)
-            seq.append((s, r, w, cav.nusselt()[0]))
+            s_, r, w = cav.run_to_steady(1e-8, max_steps)
+            seq.append((s_, r, w, cav.nusselt()[0]))
     t_seq = time.perf_counter() - t
-    updates = sum(c["nx"] * c["ny"] * s for c, s in zip(cl, steps))
+    # FP64 reference of the smallest grids, to r < 1e-8
+    small = sorted(range(len(cl)), key=lambda i: (cl[i]["nx"], i))[:3]
+    f64 = {}
+    for i in small:
+        c = cl[i]
+        with lbm.Cavity(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec="f64",
+                        clamp_mode=1, resid_interval=1000) as cav:
+            s_, r, w = cav.run_to_steady(1e-8, 3_000_000)
+            f64[i] = dict(steps=s_, resid=r, stop=["tol", "stagnated", "max_steps"][w], nu=cav.nusselt()[0])
+    updates = sum(c["nx"] * c["ny"] * s_ for c, s_ in zip(cl, steps))
     print(json.dumps({
         "study": "batch", "cases": len(cl), "prec": "f32", "tol": 1e-8, "max_steps": max_steps,
-        "tuned_threads": threads, "tune_seconds": t_tune,
+        "stop_rule": f"r < 1e-8, or no new minimum over 10 checks while r < {floor}, or {max_steps} steps",
+        "tol_met": sum(1 for w in why if w == 0),
+        "tuned_plan": plan, "tuned_threads": threads, "tune_seconds": t_tune,
         "batched": {"seconds": t_batch, "cases_per_s": len(cl) / t_batch, "MLUPS": updates / t_batch / 1e6,
                     "graph_launches": 1},
         "sequential": {"seconds": t_seq, "cases_per_s": len(cl) / t_seq,
                        "MLUPS": sum(c["nx"] * c["ny"] * q[0] for c, q in zip(cl, seq)) / t_seq / 1e6},
         "speedup": t_seq / t_batch,
-        "same_steps": all(s == q[0] for s, q in zip(steps, seq)),
+        "same_steps": all(s_ == q[0] for s_, q in zip(steps, seq)),
         "max_rel_nu_diff": max(abs(h - q[3]) / abs(q[3]) for h, q in zip(hot, seq)),
         "stop_reasons": {k: sum(1 for w in why if w == k) for k in (0, 1, 2, 3)},
-        "per_case": [dict(N=c["nx"], n=c["n"], Da=c["Da"], Ra=c["Ra"], steps=s, resid=float(r), stop=w,
-                          nu=float(h)) for c, s, r, w, h in zip(cl, steps, res, why, hot)],
+        "max_rel_nu_drift_10k": max(abs(a - h) / abs(h) for a, h in zip(hot_later, hot)),
+        "fp64_r1e-8": [dict(case=i, N=cl[i]["nx"], n=cl[i]["n"], Da=cl[i]["Da"], Ra=cl[i]["Ra"],
+                            nu_f32_retired=float(hot[i]), **f64[i],
+                            rel_diff=(float(hot[i]) - f64[i]["nu"]) / f64[i]["nu"]) for i in small],
+        "per_case": [dict(N=c["nx"], n=c["n"], Da=c["Da"], Ra=c["Ra"], steps=s_, resid=float(r), stop=w,
+                          nu=float(h), rel_nu_drift_10k=float(abs(a - h) / abs(h)))
+                     for c, s_, r, w, h, a in zip(cl, steps, res, why, hot, hot_later)],
     }), flush=True)
 
 

@@ -273,8 +273,9 @@ int lbm_adjoint_nu(lbm_ctx *ctx, int64_t steps, int ckpt_every, int from_rest,
 /* ------------------------------------------------------------- sweeps
  * The paper's results are a sweep of independent cavities over n, Da and Ra
  * (section "Results and discussions", Tables 1-2).  A batch runs such a sweep
- * as one workload: each time step is one kernel launch over the row tiles of
- * every active case (grids may differ), every resid_interval steps each
+ * as one workload: each time step covers the row tiles of every active case
+ * (grids may differ) in one launch, or all steps between two checks run in
+ * one persistent launch (lbm_batch_set_plan); every resid_interval steps each
  * case's residual is checked on the device and converged cases stop being
  * stepped.  All cases share the storage precision and the options of
  * lbm_batch_create (the two-buffer layout; resid_interval must be even; the
@@ -316,9 +317,40 @@ int lbm_batch_run_to_steady(lbm_batch *batch, double tol, int64_t max_steps,
 /* Hot- and cold-wall average Nu of every case (host arrays of ncases). */
 int lbm_batch_nusselt(lbm_batch *batch, double *nu_hot, double *nu_cold);
 
-/* Autotune the batched kernel's block size (tile width) by timing `steps`
- * batched steps for each candidate on copies of the current states (the
- * states are restored); *threads_out receives the block size chosen. */
+/* Execution plan of the batched steps.  The row tiles of the active cases
+ * form one list (compacted on the device when cases retire), and a grid of
+ * blocks_per_sm x (SM count) blocks strides over it every step, so a block
+ * takes several tiles -- of one or several cases -- per step.
+ *   LBM_BATCH_PER_STEP: one launch per time step;
+ *   LBM_BATCH_PERSISTENT: one cooperative launch runs all steps between two
+ *     convergence checks, with a grid barrier between steps (blocks_per_sm
+ *     is capped at the blocks that fit on an SM).  Every wait at the
+ *     barrier is bounded (lbm_batch_set_wait_budget); a block that gives up
+ *     raises the batch's error word and every block leaves, after which the
+ *     calls that step the batch return LBM_ERR_TIMEOUT (sticky: the states
+ *     are no longer valid).  If a CUDA graph with the cooperative launch
+ *     cannot be built, lbm_batch_run_to_steady falls back to the per-step
+ *     form.
+ * Both modes run the same tile code: results are identical.
+ * Defaults: per-step, 128 threads, 8 blocks per SM. */
+enum { LBM_BATCH_PER_STEP = 0, LBM_BATCH_PERSISTENT = 1 };
+
+/* Set the plan: mode as above, threads 64, 128 or 256 (tile = 2 x threads
+ * nodes, or threads nodes in FP64), blocks_per_sm 1..64.  Errors:
+ * LBM_ERR_ARG, LBM_ERR_UNSUPPORTED (no block of the persistent kernel fits
+ * on an SM), LBM_ERR_CUDA. */
+int lbm_batch_set_plan(lbm_batch *batch, int mode, int threads, int blocks_per_sm);
+/* Read the plan in effect (blocks_per_sm after the residency cap). */
+int lbm_batch_get_plan(const lbm_batch *batch, int *mode, int *threads, int *blocks_per_sm);
+/* Clock cycles a persistent block waits at a barrier before it gives up
+ * (default 2^31, about one second); cycles >= 1. */
+int lbm_batch_set_wait_budget(lbm_batch *batch, int64_t cycles);
+
+/* Autotune the plan: time `steps` batched steps for every mode x block size
+ * (64, 128, 256) x blocks per SM (2, 4, 8, 16, 32; persistent: those that
+ * fit) on copies of the current states (restored afterwards) and keep the
+ * fastest; *threads_out (may be NULL) receives its block size and
+ * lbm_batch_get_plan the rest. */
 int lbm_batch_tune(lbm_batch *batch, int steps, int *threads_out);
 
 /* Allocation-free form of lbm_residual, for callers that cannot call

@@ -1,7 +1,13 @@
 // lbm_batch.cu -- many independent cavities (a parameter sweep) as one
-// workload: every time step is one launch over a flat list of row tiles of
-// all active cases; convergence is checked per case on the device every
-// resid_interval steps, and converged cases drop out of the tile work.
+// workload.  The row tiles of all active cases form one flat list, compacted
+// on the device whenever cases retire; a fixed grid (a tuned multiple of the
+// SM count) strides over it.  Two execution modes:
+//   per-step: one launch per time step (resid_interval launches per chunk);
+//   persistent: one cooperative launch per chunk that runs all its steps,
+//     with a grid barrier between steps (every wait bounded: a block that
+//     gives up raises the batch's error word and every block leaves).
+// Convergence is checked per case on the device every resid_interval steps,
+// and converged cases drop out of the tile list.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -25,8 +31,8 @@ struct CaseDev {
     Phys<float> pf;
     Phys<F2> p2;
     int tiles_per_row;
-    int tile0;  // first tile of this case in the flat tile list
-    int cur;    // buffer holding the case's current state
+    int ntiles;  // tiles_per_row * ny
+    int cur;     // buffer holding the case's current state
     int pad;
 };
 
@@ -37,22 +43,49 @@ struct Conv {
     int since, active, reason, pad;
 };
 
-// TAU as for step_node: 0 lagged tau (stored per node), 1 node-local
-// implicit tau (every case of a batch shares lbm_opts.tau_iters).
-template <int PREC, int TAU>
-__global__ void __launch_bounds__(256)
-batch_step_kernel(const CaseDev *__restrict__ cases, int ncases, const int *__restrict__ active, int parity)
+// The compacted list of active cases: idx[0..m) the active cases in order,
+// t0[j] the first flat tile of idx[j] (t0[m] = total), hdr = {m, total}.
+struct ActiveList {
+    int *idx;
+    int *t0;
+    int *hdr;
+};
+
+// Grid barrier of the persistent kernel: arrival count and generation.
+struct GridBarrier {
+    unsigned count, gen;
+};
+
+// Rebuild the active list from the per-case flags (one thread; runs once per
+// chunk).
+__device__ void build_active(const CaseDev *cases, const int *active, int n, ActiveList a)
+{
+    int m = 0, t = 0;
+    for (int c = 0; c < n; c++) {
+        if (!active[c]) continue;
+        a.idx[m] = c;
+        a.t0[m] = t;
+        t += cases[c].ntiles;
+        m++;
+    }
+    a.t0[m] = t;
+    a.hdr[0] = m;
+    a.hdr[1] = t;
+}
+
+__global__ void build_active_kernel(const CaseDev *cases, const int *active, int n, ActiveList a)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) build_active(cases, active, n, a);
+}
+
+// One row tile of one case: the same tile bodies as the single-cavity
+// kernels (two nodes per thread, or one node per thread in FP64), so every
+// case evolves bit for bit as it would alone.  TAU as for step_node; FIELD 0
+// when no case has a per-node Darcy field, else 2 (decided per case).
+template <int PREC, int TAU, int FIELD>
+__device__ __forceinline__ void batch_tile(const CaseDev &cd, int local, int parity)
 {
     using St = Store<PREC>;
-    const int t = blockIdx.x;
-    int lo = 0, hi = ncases - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (cases[mid].tile0 <= t) lo = mid; else hi = mid - 1;
-    }
-    if (!active[lo]) return;
-    const CaseDev &cd = cases[lo];
-    const int local = t - cd.tile0;
     const int y = local / cd.tiles_per_row, xb = local - y * cd.tiles_per_row;
     const int s = cd.cur ^ parity;
     const auto *src = (const typename St::S *)cd.dist[s];
@@ -60,22 +93,98 @@ batch_step_kernel(const CaseDev *__restrict__ cases, int ncases, const int *__re
     if constexpr (PREC == LBM_F64) {
         const int x = xb * blockDim.x + threadIdx.x;
         if (x < cd.pd.nx)
-            step_node<PREC, double, 2, TAU>(src, dst, (const double *)cd.tau[s], (double *)cd.tau[s ^ 1], cd.pd,
-                                            x, y);
+            step_node<PREC, double, FIELD, TAU>(src, dst, (const double *)cd.tau[s], (double *)cd.tau[s ^ 1],
+                                                cd.pd, x, y);
     } else {
-        step2_tile<PREC, 2, TAU>(src, dst, (const float *)cd.tau[s], (float *)cd.tau[s ^ 1], cd.pf, cd.p2,
+        step2_tile<PREC, FIELD, TAU>(src, dst, (const float *)cd.tau[s], (float *)cd.tau[s ^ 1], cd.pf, cd.p2,
                                  xb * 2 * (int)blockDim.x, y);
+    }
+}
+
+// Every tile of the active list once, striding by the grid.
+template <int PREC, int TAU, int FIELD>
+__device__ __forceinline__ void batch_sweep(const CaseDev *__restrict__ cases, ActiveList a, int m, int nt,
+                                            int parity)
+{
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        int lo = 0, hi = m - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.t0[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        batch_tile<PREC, TAU, FIELD>(cases[a.idx[lo]], t - a.t0[lo], parity);
+    }
+}
+
+template <int PREC, int TAU, int FIELD>
+__global__ void __launch_bounds__(256)
+batch_step_kernel(const CaseDev *__restrict__ cases, ActiveList a, int parity)
+{
+    batch_sweep<PREC, TAU, FIELD>(cases, a, a.hdr[0], a.hdr[1], parity);
+}
+
+// Bounded grid barrier.  Thread 0 of each block arrives on the counter; the
+// last one resets it and advances the generation, the others poll the
+// generation for at most `budget` clock cycles.  A block that gives up sets
+// *err; a block that sees *err set after the barrier leaves too, so no block
+// waits on one that has gone.  The fences order each block's stores of the
+// finished step before any block's loads of the next.
+__device__ __forceinline__ bool grid_sync(GridBarrier *bar, long long budget, int *err)
+{
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *genp = &bar->gen;
+        const unsigned g = *genp;
+        __threadfence();
+        if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*genp == g) {
+                if (clock64() - t0 > budget) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        if (ok && *(volatile int *)err) ok = 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Persistent form: `steps` time steps in one cooperative launch (all blocks
+// resident), a grid barrier between consecutive steps.
+template <int PREC, int TAU, int FIELD>
+__global__ void __launch_bounds__(256)
+batch_chunk_kernel(const CaseDev *__restrict__ cases, ActiveList a, int steps, GridBarrier *bar,
+                   long long budget, int *err)
+{
+    if (*(volatile int *)err) return;
+    const int m = a.hdr[0], nt = a.hdr[1];
+    for (int s = 0; s < steps; s++) {
+        batch_sweep<PREC, TAU, FIELD>(cases, a, m, nt, s & 1);
+        if (s + 1 < steps && !grid_sync(bar, budget, err)) return;
     }
 }
 
 // After each chunk: read every active case's residual (written by its
 // residual kernels), retire it on tol / stagnation / max_steps / non-finite,
-// and decide whether another chunk runs.  The chunk counter falls by one
-// per call, so the device loop below ends after at most the number of chunks
-// the host allowed, whatever the residuals do.
+// rebuild the active tile list, and decide whether another chunk runs.  The
+// chunk counter falls by one per call, so the device loop below ends after
+// at most the number of chunks the host allowed, whatever the residuals do;
+// a raised error word (a persistent launch gave up a barrier) ends it too.
 __global__ void __launch_bounds__(256)
 batch_update_kernel(Conv *conv, int *active, double *const *smalls, int n, int delta, double tol,
                     double stag_floor, long long max_steps, int *chunks_left, int *go_out,
+                    const CaseDev *cases, ActiveList a, const int *err,
                     cudaGraphConditionalHandle handle, int set_condition)
 {
     __shared__ int any;
@@ -113,9 +222,10 @@ batch_update_kernel(Conv *conv, int *active, double *const *smalls, int n, int d
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        build_active(cases, active, n, a);
         const int left = *chunks_left - 1;
         *chunks_left = left;
-        const int go = (any && left > 0) ? 1 : 0;
+        const int go = (any && left > 0 && !*err) ? 1 : 0;
         *go_out = go;
         if (set_condition) cudaGraphSetConditional(handle, (unsigned)go);
     }
@@ -129,16 +239,27 @@ struct lbm_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
-    int threads = 128;        // block size of the batched kernel (tile = 2x nodes, or 1x in FP64)
+    int sms = 0;
+    // execution plan (lbm_batch_tune / lbm_batch_set_plan): block size (tile
+    // = 2x nodes, or 1x in FP64), grid = blocks_per_sm x SMs, and the mode
+    int threads = 128;
+    int blocks_per_sm = 8;
+    int mode = LBM_BATCH_PER_STEP;
+    long long budget = 1ll << 31;   // clock cycles a persistent block waits at a barrier
     int ntiles = 0;
+    bool any_field = false;   // some case has a per-node Darcy field
     std::vector<CaseDev> host_cases;
     CaseDev *d_cases = nullptr;
     int *d_active = nullptr;
+    ActiveList act{nullptr, nullptr, nullptr};
     Conv *d_conv = nullptr;
     double **d_smalls = nullptr;
     int *d_chunks = nullptr;
     int *d_go = nullptr;
     int *h_go = nullptr;       // pinned
+    GridBarrier *d_bar = nullptr;
+    int *d_err = nullptr;      // raised by a persistent block that gave up a barrier (sticky)
+    int *h_err = nullptr;      // pinned
 };
 
 static thread_local char g_batch_err[256] = "";
@@ -153,10 +274,13 @@ static thread_local char g_batch_err[256] = "";
 
 namespace {
 
+int tile_nodes(const lbm_batch *b) { return b->opts.prec == LBM_F64 ? b->threads : 2 * b->threads; }
+
 int upload_cases(lbm_batch *b)
 {
-    const int tile = b->opts.prec == LBM_F64 ? b->threads : 2 * b->threads;
+    const int tile = tile_nodes(b);
     int t0 = 0;
+    b->any_field = false;
     for (size_t i = 0; i < b->sub.size(); i++) {
         lbm_ctx *c = b->sub[i];
         CaseDev &d = b->host_cases[i];
@@ -168,33 +292,103 @@ int upload_cases(lbm_batch *b)
         d.pf = make_params<float>(c);
         d.p2 = make_params<F2>(c);
         d.tiles_per_row = (c->nx + tile - 1) / tile;
-        d.tile0 = t0;
+        d.ntiles = d.tiles_per_row * c->ny;
         d.cur = c->cur;
-        t0 += d.tiles_per_row * c->ny;
+        if (c->d_da) b->any_field = true;
+        t0 += d.ntiles;
     }
     b->ntiles = t0;
     BK(cudaMemcpyAsync(b->d_cases, b->host_cases.data(), sizeof(CaseDev) * b->sub.size(), cudaMemcpyHostToDevice,
                        b->stream));
+    build_active_kernel<<<1, 32, 0, b->stream>>>(b->d_cases, b->d_active, (int)b->sub.size(), b->act);
+    BK(cudaGetLastError());
     return LBM_OK;
 }
 
-template <int TAU>
-cudaError_t launch_batch_step_tau(lbm_batch *b, int parity)
+// The step and persistent kernels of the batch's storage, tau scheme and
+// Darcy-field mode.
+template <int PREC>
+void *kernel_of(const lbm_batch *b, bool persistent)
 {
-    const int n = (int)b->sub.size();
-    switch (b->opts.prec) {
-    case LBM_F64: batch_step_kernel<LBM_F64, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
-    case LBM_F32: batch_step_kernel<LBM_F32, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
-    case LBM_BF16D: batch_step_kernel<LBM_BF16D, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
-    case LBM_F16D: batch_step_kernel<LBM_F16D, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
-    default: batch_step_kernel<LBM_F32D, TAU><<<b->ntiles, b->threads, 0, b->stream>>>(b->d_cases, n, b->d_active, parity); break;
+    const int t = b->opts.tau_iters > 0 ? 1 : 0, f = b->any_field ? 2 : 0;
+    if (persistent) {
+        if (t) return f ? (void *)batch_chunk_kernel<PREC, 1, 2> : (void *)batch_chunk_kernel<PREC, 1, 0>;
+        return f ? (void *)batch_chunk_kernel<PREC, 0, 2> : (void *)batch_chunk_kernel<PREC, 0, 0>;
     }
-    return cudaGetLastError();
+    if (t) return f ? (void *)batch_step_kernel<PREC, 1, 2> : (void *)batch_step_kernel<PREC, 1, 0>;
+    return f ? (void *)batch_step_kernel<PREC, 0, 2> : (void *)batch_step_kernel<PREC, 0, 0>;
+}
+
+void *kernel_of(const lbm_batch *b, bool persistent)
+{
+    switch (b->opts.prec) {
+    case LBM_F64: return kernel_of<LBM_F64>(b, persistent);
+    case LBM_F32: return kernel_of<LBM_F32>(b, persistent);
+    case LBM_BF16D: return kernel_of<LBM_BF16D>(b, persistent);
+    case LBM_F16D: return kernel_of<LBM_F16D>(b, persistent);
+    default: return kernel_of<LBM_F32D>(b, persistent);
+    }
+}
+
+void *chunk_kernel(const lbm_batch *b) { return kernel_of(b, true); }
+
+// Blocks of `threads` threads of the persistent kernel that fit on one SM
+// (a cooperative launch needs every block resident).
+int resident_blocks(const lbm_batch *b, int threads)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, chunk_kernel(b), threads, 0) != cudaSuccess) return 0;
+    return nb;
+}
+
+int grid_blocks(const lbm_batch *b)
+{
+    int bps = b->blocks_per_sm;
+    if (b->mode == LBM_BATCH_PERSISTENT) {
+        const int r = resident_blocks(b, b->threads);
+        if (bps > r) bps = r;
+    }
+    return (bps < 1 ? 1 : bps) * b->sms;
 }
 
 cudaError_t launch_batch_step(lbm_batch *b, int parity)
 {
-    return b->opts.tau_iters > 0 ? launch_batch_step_tau<1>(b, parity) : launch_batch_step_tau<0>(b, parity);
+    const CaseDev *cases = b->d_cases;
+    ActiveList a = b->act;
+    void *args[] = {(void *)&cases, (void *)&a, (void *)&parity};
+    return cudaLaunchKernel(kernel_of(b, false), dim3(grid_blocks(b)), dim3(b->threads), args, 0, b->stream);
+}
+
+// `steps` steps of every active case: per-step launches, or one persistent
+// cooperative launch (its barrier reset first).
+cudaError_t launch_batch_steps(lbm_batch *b, int steps)
+{
+    if (steps <= 0) return cudaSuccess;
+    if (b->mode == LBM_BATCH_PER_STEP) {
+        for (int s = 0; s < steps; s++) {
+            const cudaError_t e = launch_batch_step(b, s & 1);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    cudaError_t e = cudaMemsetAsync(b->d_bar, 0, sizeof(GridBarrier), b->stream);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid_blocks(b));
+    cfg.blockDim = dim3(b->threads);
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const CaseDev *cases = b->d_cases;
+    ActiveList a = b->act;
+    GridBarrier *bar = b->d_bar;
+    long long budget = b->budget;
+    int *err = b->d_err;
+    void *args[] = {(void *)&cases, (void *)&a, (void *)&steps, (void *)&bar, (void *)&budget, (void *)&err};
+    return cudaLaunchKernelExC(&cfg, chunk_kernel(b), args);
 }
 
 double default_floor(const lbm_opts &o)
@@ -208,11 +402,11 @@ double default_floor(const lbm_opts &o)
 int enqueue_chunk(lbm_batch *b, double tol, long long max_steps, cudaGraphConditionalHandle h, int set_cond)
 {
     const int delta = b->opts.resid_interval;
-    for (int s = 0; s < delta; s++) BK(launch_batch_step(b, s & 1));
+    BK(launch_batch_steps(b, delta));
     for (lbm_ctx *c : b->sub) BK(lbm::launch_residual(c, false));
     batch_update_kernel<<<1, 256, 0, b->stream>>>(b->d_conv, b->d_active, b->d_smalls, (int)b->sub.size(), delta,
-                                                  tol, default_floor(b->opts), max_steps, b->d_chunks, b->d_go, h,
-                                                  set_cond);
+                                                  tol, default_floor(b->opts), max_steps, b->d_chunks, b->d_go,
+                                                  b->d_cases, b->act, b->d_err, h, set_cond);
     BK(cudaGetLastError());
     return LBM_OK;
 }
@@ -225,11 +419,17 @@ void free_batch(lbm_batch *b)
     for (lbm_ctx *c : b->sub) lbm_destroy(c);
     cudaFree(b->d_cases);
     cudaFree(b->d_active);
+    cudaFree(b->act.idx);
+    cudaFree(b->act.t0);
+    cudaFree(b->act.hdr);
     cudaFree(b->d_conv);
     cudaFree(b->d_smalls);
     cudaFree(b->d_chunks);
     cudaFree(b->d_go);
     cudaFreeHost(b->h_go);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_err);
+    cudaFreeHost(b->h_err);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -238,8 +438,18 @@ int set_all_active(lbm_batch *b, int v)
 {
     std::vector<int> a(b->sub.size(), v);
     BK(cudaMemcpyAsync(b->d_active, a.data(), sizeof(int) * a.size(), cudaMemcpyHostToDevice, b->stream));
+    build_active_kernel<<<1, 32, 0, b->stream>>>(b->d_cases, b->d_active, (int)b->sub.size(), b->act);
+    BK(cudaGetLastError());
     BK(cudaStreamSynchronize(b->stream));
     return LBM_OK;
+}
+
+// Read the error word: LBM_ERR_TIMEOUT once a persistent block gave up.
+int batch_err(lbm_batch *b)
+{
+    BK(cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    return *b->h_err ? LBM_ERR_TIMEOUT : LBM_OK;
 }
 
 }  // namespace
@@ -290,6 +500,16 @@ int lbm_batch_create(lbm_batch **out, const lbm_case *cases, int ncases, const l
             const size_t n = b->sub.size();
             BK(cudaMalloc(&b->d_cases, sizeof(CaseDev) * n));
             BK(cudaMalloc(&b->d_active, sizeof(int) * n));
+            BK(cudaMemset(b->d_active, 0, sizeof(int) * n));
+            BK(cudaMalloc(&b->act.idx, sizeof(int) * n));
+            BK(cudaMalloc(&b->act.t0, sizeof(int) * (n + 1)));
+            BK(cudaMalloc(&b->act.hdr, sizeof(int) * 2));
+            BK(cudaMalloc(&b->d_bar, sizeof(GridBarrier)));
+            BK(cudaMalloc(&b->d_err, sizeof(int)));
+            BK(cudaMemset(b->d_err, 0, sizeof(int)));
+            BK(cudaMallocHost(&b->h_err, sizeof(int)));
+            *b->h_err = 0;
+            BK(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device));
             BK(cudaMalloc(&b->d_conv, sizeof(Conv) * n));
             BK(cudaMalloc(&b->d_smalls, sizeof(double *) * n));
             BK(cudaMalloc(&b->d_chunks, sizeof(int)));
@@ -330,11 +550,23 @@ int lbm_batch_step(lbm_batch *b, int64_t k)
     if (rc) return rc;
     rc = set_all_active(b, 1);
     if (rc) return rc;
-    for (int64_t s = 0; s < k; s++) BK(launch_batch_step(b, (int)(s & 1)));
-    if (k & 1)
-        for (lbm_ctx *c : b->sub) c->cur ^= 1;
+    if (int e = batch_err(b)) return e;
+    // in pieces of an even number of steps (each case then ends a piece in
+    // the buffer it started it in), then the odd remainder
+    const int64_t piece = 1 << 20;
+    for (int64_t done = 0; done < k;) {
+        int64_t n = k - done < piece ? k - done : piece;
+        if (n > 1) n &= ~int64_t(1);
+        BK(launch_batch_steps(b, (int)n));
+        if (n & 1) {
+            for (lbm_ctx *c : b->sub) c->cur ^= 1;
+            rc = upload_cases(b);
+            if (rc) return rc;
+        }
+        done += n;
+    }
     for (lbm_ctx *c : b->sub) c->steps += k;
-    return LBM_OK;
+    return b->mode == LBM_BATCH_PERSISTENT ? batch_err(b) : LBM_OK;
 }
 
 int lbm_batch_run_to_steady(lbm_batch *b, double tol, int64_t max_steps, int graph_mode, int64_t *steps,
@@ -342,6 +574,7 @@ int lbm_batch_run_to_steady(lbm_batch *b, double tol, int64_t max_steps, int gra
 {
     if (!b || max_steps < 0 || !(tol >= 0) || (graph_mode != 0 && graph_mode != 1)) return LBM_ERR_ARG;
     BK(cudaSetDevice(b->device));
+    if (int e = batch_err(b)) return e;
     const int n = (int)b->sub.size();
     const int delta = b->opts.resid_interval;
     int rc = upload_cases(b);
@@ -370,7 +603,7 @@ int lbm_batch_run_to_steady(lbm_batch *b, double tol, int64_t max_steps, int gra
     BK(cudaMemcpyAsync(b->d_chunks, &chunks_i, sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BK(cudaStreamSynchronize(b->stream));
 
-    if (chunks_i > 0) {
+    for (int attempt = 0; chunks_i > 0 && attempt < 2; attempt++) {
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;
         BK(cudaGraphCreate(&graph, 0));
@@ -403,6 +636,7 @@ int lbm_batch_run_to_steady(lbm_batch *b, double tol, int64_t max_steps, int gra
             if (rc2 == LBM_OK && ec != cudaSuccess) rc2 = LBM_ERR_CUDA;
         }
         if (rc2 == LBM_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc2 = LBM_ERR_CUDA;
+        const bool exec_launched = rc2 == LBM_OK;
         if (rc2 == LBM_OK) {
             if (graph_mode == 0) {
                 for (;;) {
@@ -422,11 +656,18 @@ int lbm_batch_run_to_steady(lbm_batch *b, double tol, int64_t max_steps, int gra
         }
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
-        if (rc2 != LBM_OK) {
-            snprintf(g_batch_err, sizeof(g_batch_err), "batch graph: %s", cudaGetErrorString(cudaGetLastError()));
-            return rc2;
+        if (rc2 == LBM_OK) break;
+        const cudaError_t last = cudaGetLastError();
+        if (attempt == 0 && b->mode == LBM_BATCH_PERSISTENT && !exec_launched) {
+            // the graph with the cooperative launch could not be built here:
+            // the per-step form runs the same steps
+            b->mode = LBM_BATCH_PER_STEP;
+            continue;
         }
+        snprintf(g_batch_err, sizeof(g_batch_err), "batch graph: %s", cudaGetErrorString(last));
+        return rc2;
     }
+    if (int e = batch_err(b)) return e;
     BK(cudaMemcpyAsync(conv.data(), b->d_conv, sizeof(Conv) * n, cudaMemcpyDeviceToHost, b->stream));
     BK(cudaStreamSynchronize(b->stream));
     int out_rc = LBM_OK;
@@ -450,10 +691,52 @@ int lbm_batch_nusselt(lbm_batch *b, double *hot, double *cold)
     return LBM_OK;
 }
 
+int lbm_batch_set_plan(lbm_batch *b, int mode, int threads, int blocks_per_sm)
+{
+    if (!b || (mode != LBM_BATCH_PER_STEP && mode != LBM_BATCH_PERSISTENT) ||
+        (threads != 64 && threads != 128 && threads != 256) || blocks_per_sm < 1 || blocks_per_sm > 64)
+        return LBM_ERR_ARG;
+    BK(cudaSetDevice(b->device));
+    const int old_mode = b->mode, old_threads = b->threads;
+    b->mode = mode;
+    b->threads = threads;
+    if (mode == LBM_BATCH_PERSISTENT && resident_blocks(b, threads) < 1) {
+        b->mode = old_mode;
+        b->threads = old_threads;
+        return LBM_ERR_UNSUPPORTED;
+    }
+    b->blocks_per_sm = blocks_per_sm;
+    return upload_cases(b);
+}
+
+int lbm_batch_get_plan(const lbm_batch *b, int *mode, int *threads, int *blocks_per_sm)
+{
+    if (!b) return LBM_ERR_ARG;
+    if (mode) *mode = b->mode;
+    if (threads) *threads = b->threads;
+    if (blocks_per_sm) {
+        int bps = b->blocks_per_sm;
+        if (b->mode == LBM_BATCH_PERSISTENT) {
+            const int r = resident_blocks(b, b->threads);
+            if (bps > r) bps = r;
+        }
+        *blocks_per_sm = bps;
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_set_wait_budget(lbm_batch *b, int64_t cycles)
+{
+    if (!b || cycles < 1) return LBM_ERR_ARG;
+    b->budget = cycles;
+    return LBM_OK;
+}
+
 int lbm_batch_tune(lbm_batch *b, int steps, int *threads_out)
 {
     if (!b || steps < 2) return LBM_ERR_ARG;
     BK(cudaSetDevice(b->device));
+    if (int e = batch_err(b)) return e;
     steps &= ~1;  // even: every case ends in the buffer it started in
     // keep the states: time on copies, restore afterwards
     std::vector<void *> save_d(b->sub.size(), nullptr), save_t(b->sub.size(), nullptr);
@@ -466,29 +749,52 @@ int lbm_batch_tune(lbm_batch *b, int steps, int *threads_out)
             cudaMemcpyAsync(save_t[i], c->buf.tau[c->cur], tb, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
             rc = LBM_ERR_CUDA;
     }
-    const int cand[3] = {64, 128, 256};
+    // candidates: mode x block size x blocks per SM (the grid is a multiple
+    // of the SM count; each block strides over the tiles, so the blocks per
+    // SM set how many tiles -- and cases -- one block takes per step)
+    struct Plan { int mode, threads, bps; };
+    std::vector<Plan> cand;
+    for (int mode : {LBM_BATCH_PER_STEP, LBM_BATCH_PERSISTENT})
+        for (int th : {64, 128, 256})
+            for (int bps : {2, 4, 8, 16, 32}) {
+                if (mode == LBM_BATCH_PERSISTENT) {
+                    b->mode = mode;
+                    const int r = resident_blocks(b, th);
+                    b->mode = LBM_BATCH_PER_STEP;
+                    if (bps > r) continue;
+                }
+                cand.push_back({mode, th, bps});
+            }
     float best_ms = 1e30f;
-    int best = b->threads;
+    Plan best{b->mode, b->threads, b->blocks_per_sm};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (rc == LBM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) rc = LBM_ERR_CUDA;
     if (rc == LBM_OK) rc = set_all_active(b, 1);
-    for (int ci = 0; ci < 3 && rc == LBM_OK; ci++) {
-        b->threads = cand[ci];
+    for (size_t ci = 0; ci < cand.size() && rc == LBM_OK; ci++) {
+        b->mode = cand[ci].mode;
+        b->threads = cand[ci].threads;
+        b->blocks_per_sm = cand[ci].bps;
         rc = upload_cases(b);
         if (rc) break;
-        for (int s = 0; s < 2 && rc == LBM_OK; s++)
-            if (launch_batch_step(b, s & 1) != cudaSuccess) rc = LBM_ERR_CUDA;   // warm-up
+        if (launch_batch_steps(b, 2) != cudaSuccess) {   // warm-up; a plan that cannot launch is skipped
+            cudaGetLastError();
+            continue;
+        }
         cudaEventRecord(e0, b->stream);
-        for (int s = 0; s < steps && rc == LBM_OK; s++)
-            if (launch_batch_step(b, s & 1) != cudaSuccess) rc = LBM_ERR_CUDA;
+        const cudaError_t le = launch_batch_steps(b, steps);
         cudaEventRecord(e1, b->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) rc = LBM_ERR_CUDA;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (rc == LBM_OK && ms < best_ms) {
+        // a persistent plan that gave up a barrier is not a candidate; its
+        // error word is cleared (the states are restored below)
+        const bool gave_up = batch_err(b) != LBM_OK;
+        if (gave_up && cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+        if (rc == LBM_OK && le == cudaSuccess && !gave_up && ms < best_ms) {
             best_ms = ms;
             best = cand[ci];
         }
+        cudaGetLastError();
     }
     for (size_t i = 0; i < b->sub.size(); i++) {
         lbm_ctx *c = b->sub[i];
@@ -506,9 +812,12 @@ int lbm_batch_tune(lbm_batch *b, int steps, int *threads_out)
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    b->threads = best;
+    b->mode = best.mode;
+    b->threads = best.threads;
+    b->blocks_per_sm = best.bps;
     if (rc == LBM_OK) rc = upload_cases(b);
-    if (threads_out) *threads_out = best;
+    if (rc == LBM_OK) rc = batch_err(b);
+    if (threads_out) *threads_out = best.threads;
     return rc;
 }
 

@@ -94,6 +94,10 @@ SIGNATURES = [
     ("lbm_batch_tune", ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     ("lbm_adjoint_nu", ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D, _D]),
     ("lbm_residual_noalloc", ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
+    ("lbm_batch_set_plan", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("lbm_batch_get_plan", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
+    ("lbm_batch_set_wait_budget", ctypes.c_int, [_VP, ctypes.c_int64]),
     ("lbm_bench_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("lbm_last_cuda_error", ctypes.c_char_p, []),
@@ -334,6 +338,20 @@ class Batch:
         t = ctypes.c_int()
         _check(lib().lbm_batch_tune(self.h, int(steps), ctypes.byref(t)), "lbm_batch_tune")
         return t.value
+
+    def set_plan(self, mode, threads=128, blocks_per_sm=8):
+        """mode 'per_step' / 'persistent' (or 0 / 1)."""
+        m = {"per_step": 0, "persistent": 1}.get(mode, mode)
+        _check(lib().lbm_batch_set_plan(self.h, int(m), int(threads), int(blocks_per_sm)), "lbm_batch_set_plan")
+
+    def plan(self):
+        m, t, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().lbm_batch_get_plan(self.h, ctypes.byref(m), ctypes.byref(t), ctypes.byref(b)),
+               "lbm_batch_get_plan")
+        return {"mode": ("per_step", "persistent")[m.value], "threads": t.value, "blocks_per_sm": b.value}
+
+    def set_wait_budget(self, cycles):
+        _check(lib().lbm_batch_set_wait_budget(self.h, int(cycles)), "lbm_batch_set_wait_budget")
 
 
 class Cavity:

@@ -1,7 +1,8 @@
 """The batched sweep (lbm_batch_*) against single contexts and the oracle.
 
-A batch steps many cavities of different sizes in one launch per step, one
-row tile per block; each case must evolve exactly as it would alone:
+A batch steps many cavities of different sizes over one list of row tiles
+(per-step launches or one persistent launch per chunk); each case must
+evolve exactly as it would alone:
 * FP32: bit-for-bit equal to the same case stepped as a single context
   (the batched kernel runs the same tile code on the same numbers), with
   the lagged and with the node-local implicit tau;
@@ -150,6 +151,76 @@ def test_batch_run_stops_at_max_steps(mods):
     assert steps == [1000, 1000] and why == [2, 2]
 
 
+PLANS = [("per_step", 64, 2), ("per_step", 256, 32), ("persistent", 128, 4), ("persistent", 64, 1)]
+
+
+@pytest.mark.parametrize("plan", PLANS, ids=lambda p: f"{p[0]}-{p[1]}x{p[2]}")
+@pytest.mark.parametrize("prec,tau_iters", [("f32d", 0), ("f64", 0), ("f32", 2)])
+def test_batch_plans_equal_single_contexts(mods, plan, prec, tau_iters):
+    """Every execution plan (per-step or persistent launches, block size,
+    blocks per SM) runs the same tile code: bit for bit the single contexts,
+    over an odd number of steps and after a case drops out of the tile list."""
+    oracle, inputs, lbm = mods
+    st = start_states(oracle, inputs, CASES)
+    with lbm.Batch(CASES, prec=prec, clamp_mode=1, tau_iters=tau_iters) as b:
+        b.set_plan(*plan)
+        assert b.plan()["mode"] == plan[0]
+        for i, (_, s) in enumerate(st):
+            lbm.set_state_f64(b.case_ctx(i), *s)
+        b.step(37)
+        got = [lbm.get_state_f64(b.case_ctx(i), c["nx"], c["ny"]) for i, c in enumerate(CASES)]
+    for i, c in enumerate(CASES):
+        with lbm.Cavity(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec=prec,
+                        clamp_mode=1, tau_iters=tau_iters) as cav:
+            cav.set_state_f64(*st[i][1])
+            cav.step(37)
+            want = cav.get_state_f64()
+        for a, w in zip(got[i], want):
+            assert np.array_equal(a, w), i
+
+
+@pytest.mark.parametrize("plan", [("per_step", 128, 8), ("persistent", 128, 4)])
+def test_batch_run_to_steady_plans_agree(mods, plan):
+    """Run-to-steady with cases that retire at different chunks (the tile
+    list shrinks on the device): per case the same steps, residual and Nu
+    as the case run alone."""
+    _, _, lbm = mods
+    cases = [dict(nx=24, ny=24, n=0.8, Da=1e-2, Ra=1e3, Pr=6.2, porosity=0.6),
+             dict(nx=40, ny=36, n=1.0, Da=1e-1, Ra=1e4, Pr=6.2, porosity=0.6),
+             dict(nx=20, ny=28, n=0.6, Da=1e-3, Ra=1e4, Pr=6.2, porosity=1.0)]
+    with lbm.Batch(cases, prec="f64", clamp_mode=1, resid_interval=200) as b:
+        b.set_plan(*plan)
+        steps, res, why = b.run_to_steady(1e-8, 400_000, graph_mode=1)
+        hot, _ = b.nusselt()
+    assert all(w == 0 for w in why) and len(set(steps)) > 1, (steps, why)
+    for i, c in enumerate(cases):
+        with lbm.Cavity(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec="f64",
+                        clamp_mode=1, resid_interval=200) as cav:
+            s1, r1, w1 = cav.run_to_steady(1e-8, 400_000)
+            h1 = cav.nusselt()[0]
+        assert (steps[i], why[i]) == (s1, w1)
+        assert res[i] == pytest.approx(r1, rel=1e-12)
+        assert hot[i] == h1
+
+
+def test_persistent_barrier_gives_up_within_its_budget(mods):
+    """A wait budget of a few cycles makes the persistent kernel's blocks
+    give up the barrier between steps: every block leaves (no wait is
+    unbounded) and the batch reports LBM_ERR_TIMEOUT, then keeps reporting
+    it (the states are no longer valid)."""
+    _, _, lbm = mods
+    cases = [dict(nx=256, ny=256, n=0.8, Da=1e-2, Ra=1e4, Pr=6.2, porosity=0.6)] * 3
+    with lbm.Batch(cases, prec="f32", resid_interval=100) as b:
+        b.set_plan("persistent", 128, 4)
+        b.set_wait_budget(4)
+        with pytest.raises(lbm.LBMError) as e:
+            b.step(20)
+        assert e.value.code == -6
+        with pytest.raises(lbm.LBMError) as e:
+            b.run_to_steady(1e-8, 1000)
+        assert e.value.code == -6
+
+
 def test_batch_tune_keeps_states(mods):
     oracle, inputs, lbm = mods
     st = start_states(oracle, inputs, CASES)
@@ -158,8 +229,10 @@ def test_batch_tune_keeps_states(mods):
             lbm.set_state_f64(b.case_ctx(i), *s)
         before = [lbm.get_state_f64(b.case_ctx(i), c["nx"], c["ny"]) for i, c in enumerate(CASES)]
         t = b.tune(20)
+        plan = b.plan()
         after = [lbm.get_state_f64(b.case_ctx(i), c["nx"], c["ny"]) for i, c in enumerate(CASES)]
-    assert t in (64, 128, 256)
+    assert t in (64, 128, 256) and plan["threads"] == t
+    assert plan["mode"] in ("per_step", "persistent") and plan["blocks_per_sm"] >= 1
     for x, y in zip(before, after):
         for a, w in zip(x, y):
             assert np.array_equal(a, w)
