@@ -180,6 +180,8 @@ def parse():
     ap.add_argument("--study-N", type=int, default=None)
     ap.add_argument("--study-max-steps", type=int, default=3_000_000)
     ap.add_argument("--study-prec", default="f32d", help="storage of --study sensitivity")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: an independent cavity per rank; strong: one cavity in row slabs over the ranks")
     ap.add_argument("--sr-runs", type=int, default=4,
                     help="rounding streams per stochastic-rounding storage in --study precision")
     ap.add_argument("--h-sweep", type=lambda t: [float(x) for x in t.split(",") if x], default=[],
@@ -886,6 +888,65 @@ def study_adjoint(args):
     }), flush=True)
 
 
+def run_strong(args, torch, lbm, rank, world, local):
+    """Strong scaling: ONE N x N cavity split into row slabs over the ranks
+    (paper_2011_15073_gb300.slabs.DistributedSlab): every fused step is
+    followed by the halo exchange with the ranks above and below (NCCL
+    send/recv of 4 x N values per cut each way), the Nusselt number and the
+    residual by an all-reduce of their sums.  A bench step is `delta` fused
+    steps + Nu + residual; value = N^2 x delta x steps / max-over-ranks time."""
+    import torch.distributed as dist
+    from paper_2011_15073_gb300 import slabs
+    N, prec, delta = args.N, args.prec, args.delta
+    slab = slabs.DistributedSlab(N, N, CASE["n"], CASE["Da"], CASE["Ra"], CASE["Pr"], CASE["porosity"], prec=prec) \
+        if world > 1 else None
+    cav = None if world > 1 else lbm.Cavity(N, N, prec=prec, cuda_stream=torch.cuda.current_stream(), **CASE)
+
+    def bench_step():
+        if slab is not None:
+            slab.step(delta)
+            return slab.nusselt()[0], slab.residual()
+        cav.step(delta)
+        return cav.nusselt()[0], cav.residual()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(3, args.warmup)):
+        bench_step()
+    barrier()
+    with Clocks(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        for _ in range(args.steps):
+            nu, _r = bench_step()
+        t1.record()
+        barrier()
+    total = max_over_ranks(t0.elapsed_time(t1) / 1e3, world, "cuda")
+    if cav is not None:
+        cav.close()
+    if rank != 0:
+        return
+    y0, y1 = slabs.partition(N, world)[0]
+    line = {
+        "metric": "fused MRT step MLUPS", "value": N * N * delta * args.steps / total / 1e6, "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic",
+        "config": {"workload": f"one cavity {N}x{N} in {world} row slabs (rank 0: rows {y0}-{y1}), "
+                               f"{STORAGE_NAMES[prec]} storage; halo exchange every fused step",
+                   "grid": [N, N], "fused_steps_per_bench_step": delta, "parallelism": f"row slabs x{world}",
+                   "halo_bytes_per_cut_per_step": 2 * 4 * N * {"f64": 8}.get(prec, 2 if "16" in prec else 4)},
+        "gpu_launches": args.steps * delta * (1 + (4 if world > 1 else 0)),
+        "clocks": clk.summary(),
+        "nu_hot": nu,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.study == "adjoint":
@@ -923,6 +984,9 @@ def main():
     torch.cuda.set_device(local)
     from paper_2011_15073_gb300 import lbm
     lbm.lib()
+    if args.scaling == "strong":
+        run_strong(args, torch, lbm, rank, world, local)
+        return
     stream = torch.cuda.Stream()
     N, prec, delta = args.N, args.prec, args.delta
 

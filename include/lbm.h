@@ -353,6 +353,69 @@ int lbm_batch_set_wait_budget(lbm_batch *batch, int64_t cycles);
  * lbm_batch_get_plan the rest. */
 int lbm_batch_tune(lbm_batch *batch, int steps, int *threads_out);
 
+/* ------------------------------------------------- row-slab decomposition
+ * One cavity split into horizontal slabs of rows, one per context (and per
+ * GPU or rank), as a domain decomposition of the fused step: the pull
+ * scheme reads each node's neighbours from the previous state, so a slab
+ * needs, per step, only the populations that cross its cut rows -- per cut
+ * node 3 D2Q9 populations (f2, f5, f6 upward; f4, f7, f8 downward) and 1
+ * D2Q5 population (g2 upward, g4 downward) each way.  A slab context keeps
+ * one ghost row beyond each cut; after every step the caller packs the
+ * outgoing populations (lbm_halo_pack), moves them to the neighbours
+ * (device copies, peer copies or NCCL send/recv), and unpacks what arrives
+ * into the ghost rows (lbm_halo_unpack).  Interior nodes then compute
+ * exactly what the undivided cavity computes (bit for bit with FP64 and FP32
+ * storage; with stochastic rounding the random bits depend on the slab's
+ * own node offsets).  Wall Nusselt numbers and residuals become sums over
+ * each slab's interior rows that the caller adds up across slabs
+ * (lbm_nusselt_sums, lbm_residual_sums: an all-reduce of a few doubles).
+ * Slab contexts take lbm_step, lbm_fields, lbm_nusselt (average over the
+ * slab's interior rows), the state calls and lbm_set_darcy_field (arrays
+ * of the context's local rows, ghost rows included); lbm_run_to_steady,
+ * lbm_adjoint_nu and lbm_residual_noalloc return LBM_ERR_UNSUPPORTED. */
+
+/* Create the slab of global rows [y0, y1) of an nx x ny cavity (the other
+ * arguments as lbm_init; L = nx, so the lattice mapping is the cavity's).
+ * The context has (y1 - y0) local rows plus a ghost row below if y0 > 0 and
+ * above if y1 < ny.  The two-buffer layout only (layout 1 gets
+ * LBM_ERR_UNSUPPORTED).  Errors: as lbm_init; LBM_ERR_ARG for a bad range. */
+int lbm_init_slab(lbm_ctx **out, int nx, int ny, int y0, int y1, double n, double Da, double Ra,
+                  double Pr, double porosity, const lbm_opts *opts);
+
+/* The slab's first global row *y0, its interior local rows [*row_lo,
+ * *row_hi) and its local row count *ny_local (a whole cavity: 0, 0, ny, ny).
+ * Any pointer may be NULL. */
+int lbm_slab_rows(const lbm_ctx *ctx, int *y0, int *row_lo, int *row_hi, int *ny_local);
+
+/* Bytes of one halo message: 4 planes x nx values in the storage type. */
+size_t lbm_halo_bytes(const lbm_ctx *ctx);
+
+/* Copy the populations leaving the current state through the lower cut
+ * (f4, f7, f8, g4 of the bottom interior row) into d_lo and through the
+ * upper cut (f2, f5, f6, g2 of the top interior row) into d_hi: device
+ * buffers of lbm_halo_bytes each, plane-major [4][nx]; NULL skips a side.
+ * Asynchronous on the context's stream.  Errors: LBM_ERR_ARG (a buffer for a
+ * side with no neighbour), LBM_ERR_CUDA. */
+int lbm_halo_pack(lbm_ctx *ctx, void *d_lo, void *d_hi);
+
+/* Write the lower neighbour's d_hi message (its upward populations) into
+ * the ghost row below and the upper neighbour's d_lo message into the ghost
+ * row above; NULL skips a side.  Asynchronous.  Errors as lbm_halo_pack. */
+int lbm_halo_unpack(lbm_ctx *ctx, const void *d_lo, const void *d_hi);
+
+/* Sums over the interior rows of the hot- and cold-wall Nu_j of
+ * lbm_nusselt (the cavity's average is the sum over all slabs / ny).
+ * Synchronous. */
+int lbm_nusselt_sums(lbm_ctx *ctx, double *hot_sum, double *cold_sum);
+
+/* The seven sums of lbm_residual over the interior rows, against the
+ * previous call's snapshot: sums[2c] = sum (phi_c - phi_c,prev)^2,
+ * sums[2c + 1] = sum phi_c^2 for phi = u_x, u_y, T, and sums[6] the count of
+ * non-finite values.  Across slabs: add the sums, then r = max over c of
+ * sqrt(sum[2c] / sum[2c+1]).  The first call stores the snapshot and
+ * returns +inf in sums[0], sums[2], sums[4].  Synchronous. */
+int lbm_residual_sums(lbm_ctx *ctx, double *sums);
+
 /* Allocation-free form of lbm_residual, for callers that cannot call
  * cudaMalloc at the point where they check convergence: host code that must
  * not block (cudaMalloc and cudaFree can synchronise the device and stall

@@ -297,6 +297,7 @@ extern "C" int lbm_adjoint_nu(lbm_ctx *c, int64_t steps, int ckpt_every, int fro
 {
     if (!c || steps < 1 || ckpt_every < 1) return LBM_ERR_ARG;
     if (c->opts.layout != 0 || c->opts.tau_iters != 0) return LBM_ERR_UNSUPPORTED;
+    if (c->row_lo != 0 || c->row_hi != c->ny) return LBM_ERR_UNSUPPORTED;   // whole cavities only
     if (cudaSetDevice(c->device) != cudaSuccess) return LBM_ERR_CUDA;
     switch (c->opts.prec) {
     case LBM_F64: return run_adjoint<LBM_F64>(c, steps, ckpt_every, from_rest, J, dDa, dn, dRa, peak_bytes);

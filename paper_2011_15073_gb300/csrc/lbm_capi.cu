@@ -271,8 +271,10 @@ void lbm_default_opts(lbm_opts *o)
     o->seed = 0;
 }
 
-int lbm_init(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra, double Pr,
-             double porosity, const lbm_opts *opts)
+// A context of ny local rows; rows [row_lo, row_hi) are global rows
+// [y0, ...) of a cavity of ny_glob rows (a whole cavity: 0, ny, 0, ny).
+static int create_ctx(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra, double Pr, double porosity,
+                      const lbm_opts *opts, int row_lo, int row_hi, int y0, int ny_glob)
 {
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
@@ -288,6 +290,10 @@ int lbm_init(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra, doub
     if (!c) return LBM_ERR_OOM;
     c->nx = nx;
     c->ny = ny;
+    c->row_lo = row_lo;
+    c->row_hi = row_hi;
+    c->y0 = y0;
+    c->ny_glob = ny_glob;
     c->opts = o;
     c->lat = L;
     rc = init_ctx(c);
@@ -296,6 +302,87 @@ int lbm_init(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra, doub
         return rc;
     }
     *out = c;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_ctx **out, int nx, int ny, double n, double Da, double Ra, double Pr,
+             double porosity, const lbm_opts *opts)
+{
+    return create_ctx(out, nx, ny, n, Da, Ra, Pr, porosity, opts, 0, ny, 0, ny);
+}
+
+int lbm_init_slab(lbm_ctx **out, int nx, int ny, int y0, int y1, double n, double Da, double Ra, double Pr,
+                  double porosity, const lbm_opts *opts)
+{
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (ny < 2 || y0 < 0 || y1 > ny || y1 <= y0) return LBM_ERR_ARG;
+    if (opts && opts->layout != 0) return LBM_ERR_UNSUPPORTED;
+    const int glo = y0 > 0 ? 1 : 0, ghi = y1 < ny ? 1 : 0;
+    const int local = y1 - y0 + glo + ghi;
+    if (local < 2) return LBM_ERR_ARG;
+    return create_ctx(out, nx, local, n, Da, Ra, Pr, porosity, opts, glo, glo + (y1 - y0), y0, ny);
+}
+
+int lbm_slab_rows(const lbm_ctx *c, int *y0, int *row_lo, int *row_hi, int *ny_local)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (y0) *y0 = c->y0;
+    if (row_lo) *row_lo = c->row_lo;
+    if (row_hi) *row_hi = c->row_hi;
+    if (ny_local) *ny_local = c->ny;
+    return LBM_OK;
+}
+
+size_t lbm_halo_bytes(const lbm_ctx *c) { return c ? 4 * (size_t)c->nx * c->dist_elem : 0; }
+
+static bool is_slab(const lbm_ctx *c) { return c->row_lo != 0 || c->row_hi != c->ny || c->ny_glob != c->ny; }
+
+int lbm_halo_pack(lbm_ctx *c, void *d_lo, void *d_hi)
+{
+    if (!c) return LBM_ERR_ARG;
+    if ((d_lo && c->row_lo == 0) || (d_hi && c->row_hi == c->ny)) return LBM_ERR_ARG;   // no neighbour there
+    CK(cudaSetDevice(c->device));
+    CK(lbm::launch_halo_pack(c, d_lo, d_hi));
+    return LBM_OK;
+}
+
+int lbm_halo_unpack(lbm_ctx *c, const void *d_lo, const void *d_hi)
+{
+    if (!c) return LBM_ERR_ARG;
+    if ((d_lo && c->row_lo == 0) || (d_hi && c->row_hi == c->ny)) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(lbm::launch_halo_unpack(c, d_lo, d_hi));
+    return LBM_OK;
+}
+
+int lbm_nusselt_sums(lbm_ctx *c, double *hot_sum, double *cold_sum)
+{
+    if (!c) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    if (int rc0 = canonical(c)) return rc0;
+    CK(lbm::launch_nusselt(c));
+    CK(cudaMemcpyAsync(c->h_small + 6, c->d_small + 6, sizeof(double) * 2, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (hot_sum) *hot_sum = c->h_small[6];
+    if (cold_sum) *cold_sum = c->h_small[7];
+    return LBM_OK;
+}
+
+int lbm_residual_sums(lbm_ctx *c, double *sums)
+{
+    if (!c || !sums) return LBM_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    if (int rc0 = canonical(c)) return rc0;
+    if (!c->d_snap) CK(cudaMalloc(&c->d_snap, sizeof(double) * 3 * (size_t)c->nx * c->ny));
+    const bool first = !c->have_snap;
+    CK(lbm::launch_residual(c, first));
+    CK(cudaMemcpyAsync(c->h_small + 8, c->d_small + 8, sizeof(double) * 7, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_snap = true;
+    for (int i = 0; i < 7; i++) sums[i] = c->h_small[8 + i];
+    if (first)
+        for (int i = 0; i < 3; i++) sums[2 * i] = INFINITY;
     return LBM_OK;
 }
 
@@ -445,6 +532,7 @@ int lbm_run_to_steady(lbm_ctx *c, double tol, int64_t max_steps, int64_t *steps_
                       int *reason)
 {
     if (!c || max_steps < 0 || !(tol >= 0)) return LBM_ERR_ARG;
+    if (is_slab(c)) return LBM_ERR_UNSUPPORTED;   // its ghost rows need an exchange every step
     c->have_snap = false;
     double r = INFINITY, best = INFINITY;
     int rc = lbm_residual(c, &r);

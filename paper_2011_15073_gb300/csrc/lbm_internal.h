@@ -52,6 +52,12 @@ struct lbm_ctx {
     bool have_snap = false;
     bool aa_form_o = false;      // in-place layout: state in the odd-step form
     int64_t steps = 0;
+    // Row slab of a larger cavity (lbm_init_slab): local rows [row_lo,
+    // row_hi) are the global rows [y0, y0 + row_hi - row_lo) of a cavity of
+    // ny_glob rows; the local rows outside (at most one below, one above) are
+    // ghost rows that lbm_halo_unpack fills with the neighbours' populations.
+    // A whole cavity has row_lo = 0, row_hi = ny, y0 = 0, ny_glob = ny.
+    int row_lo = 0, row_hi = 0, y0 = 0, ny_glob = 0;
 };
 
 namespace lbm {
@@ -72,6 +78,12 @@ cudaError_t launch_export_f64(lbm_ctx *c, double *d_dst15);
 // odd-step form back to the canonical one (no-op if already canonical).
 cudaError_t launch_aa_step(lbm_ctx *c);
 cudaError_t launch_aa_normalize(lbm_ctx *c);
+// Halo exchange of a row slab (lbm_kernels.cu): copy the populations that
+// leave through the cut rows into d_lo / d_hi (4 planes x nx values each, in
+// the storage type), and the received ones into the ghost rows.  A null
+// buffer skips that side.
+cudaError_t launch_halo_pack(lbm_ctx *c, void *d_lo, void *d_hi);
+cudaError_t launch_halo_unpack(lbm_ctx *c, const void *d_lo, const void *d_hi);
 int residual_blocks(const lbm_ctx *c);
 
 }  // namespace lbm

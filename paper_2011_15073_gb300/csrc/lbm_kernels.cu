@@ -131,16 +131,18 @@ __device__ double streamed_T(const typename Store<PREC>::S *__restrict__ src,
 // Wall Nusselt numbers: one block; row j of the hot wall gets
 // Nu_j = -L (9 theta_0 - theta_1 - 8) / 3, the cold wall the outward
 // L (9 theta_{nx-1} - theta_{nx-2}) / 3, theta = (T - T_c) / (T_h - T_c).
+// Rows [row_lo, row_hi) (all rows of a whole cavity, the interior rows of a
+// slab); small[0..1] the averages over them, small[6..7] the sums.
 template <int PREC, bool REV>
 __global__ void __launch_bounds__(256)
 nusselt_kernel(const typename Store<PREC>::S *__restrict__ src, Phys<typename Store<PREC>::R> p,
                double T_hot, double T_cold, double Lw, double *__restrict__ small,
-               double *__restrict__ nuloc)
+               double *__restrict__ nuloc, int row_lo, int row_hi)
 {
     __shared__ double sh[32];
     const double dT = T_hot - T_cold;
     double sh_hot = 0.0, sh_cold = 0.0;
-    for (int j = threadIdx.x; j < p.ny; j += blockDim.x) {
+    for (int j = row_lo + threadIdx.x; j < row_hi; j += blockDim.x) {
         const double t0 = (streamed_T<PREC, REV>(src, p, 0, j) - T_cold) / dT;
         const double t1 = (streamed_T<PREC, REV>(src, p, 1, j) - T_cold) / dT;
         const double ta = (streamed_T<PREC, REV>(src, p, p.nx - 1, j) - T_cold) / dT;
@@ -154,26 +156,30 @@ nusselt_kernel(const typename Store<PREC>::S *__restrict__ src, Phys<typename St
     const double a = block_sum(sh_hot, sh);
     const double b = block_sum(sh_cold, sh);
     if (threadIdx.x == 0) {
-        small[0] = a / p.ny;
-        small[1] = b / p.ny;
+        small[0] = a / (row_hi - row_lo);
+        small[1] = b / (row_hi - row_lo);
+        small[6] = a;
+        small[7] = b;
     }
 }
 
 // Convergence residual, pass 1: each block accumulates, over a fixed
-// grid-stride set of nodes, sum (phi - phi_prev)^2 and sum phi^2 for
-// phi in {u_x, u_y, T} plus a count of non-finite values, and writes its
-// seven partial sums to part[blockIdx.x * 8 + 0..6].  The snapshot is updated.
+// grid-stride set of the nodes of rows [row_lo, row_hi), sum (phi -
+// phi_prev)^2 and sum phi^2 for phi in {u_x, u_y, T} plus a count of
+// non-finite values, and writes its seven partial sums to
+// part[blockIdx.x * 8 + 0..6].  The snapshot is updated.
 template <int PREC, bool REV>
 __global__ void __launch_bounds__(256)
 residual_kernel(const typename Store<PREC>::S *__restrict__ src,
                 const typename Store<PREC>::TauS *__restrict__ tsrc, Phys<typename Store<PREC>::R> p,
-                double *__restrict__ snap, double *__restrict__ part, int first)
+                double *__restrict__ snap, double *__restrict__ part, int first, int row_lo, int row_hi)
 {
     using R = typename Store<PREC>::R;
     __shared__ double sh[32];
     const int64_t n = (int64_t)p.nx * p.ny;
+    const int64_t q_end = (int64_t)p.nx * row_hi;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+    for (int64_t q = (int64_t)p.nx * row_lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < q_end;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int y = (int)(q / p.nx), x = (int)(q - (int64_t)y * p.nx);
         R f[9], g[5];
@@ -197,7 +203,8 @@ residual_kernel(const typename Store<PREC>::S *__restrict__ src,
 }
 
 // Pass 2: one block sums the partials in block order and writes
-// small[2..4] = relative change of u_x, u_y, T and small[5] = non-finite count.
+// small[2..4] = relative change of u_x, u_y, T, small[5] = non-finite count
+// and small[8..14] the seven totals (the sums a decomposed run adds up).
 __global__ void __launch_bounds__(256)
 residual_final_kernel(const double *__restrict__ part, int nb, double *__restrict__ small)
 {
@@ -214,6 +221,7 @@ residual_final_kernel(const double *__restrict__ part, int nb, double *__restric
             small[2 + c] = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
         }
         small[5] = tot[6];
+        for (int c = 0; c < 7; c++) small[8 + c] = tot[c];
     }
 }
 
@@ -320,7 +328,7 @@ static int staging_of(const lbm_ctx *c)
     const bool p16 = c->opts.prec == LBM_BF16D || c->opts.prec == LBM_F16D || c->opts.prec == LBM_F16S ||
                      c->opts.prec == LBM_BF16S;
     const int min_side = c->opts.tau_iters > 0 ? 4096 : 2048;
-    if (p16 && c->nx >= min_side && c->ny >= min_side) return 3;
+    if (p16 && c->nx >= min_side && c->ny_glob >= min_side) return 3;
     return 1;
 }
 
@@ -382,7 +390,7 @@ static cudaError_t nusselt_t(lbm_ctx *c)
     auto *kern = c->opts.layout == 1 ? nusselt_kernel<PREC, true> : nusselt_kernel<PREC, false>;
     kern<<<1, 256, 0, c->stream>>>(
         (const typename St::S *)c->buf.dist[c->cur], make_params<typename St::R>(c), c->lat.T_hot,
-        c->lat.T_cold, c->lat.L, c->d_small, c->d_nuloc);
+        c->lat.T_cold, c->lat.L, c->d_small, c->d_nuloc, c->row_lo, c->row_hi);
     return cudaGetLastError();
 }
 
@@ -394,7 +402,7 @@ static cudaError_t residual_t(lbm_ctx *c, bool first)
     auto *kern = c->opts.layout == 1 ? residual_kernel<PREC, true> : residual_kernel<PREC, false>;
     kern<<<nb, 256, 0, c->stream>>>(
         (const typename St::S *)c->buf.dist[c->cur], (const typename St::TauS *)c->buf.tau[c->cur],
-        make_params<typename St::R>(c), c->d_snap, c->d_part, first ? 1 : 0);
+        make_params<typename St::R>(c), c->d_snap, c->d_part, first ? 1 : 0, c->row_lo, c->row_hi);
     residual_final_kernel<<<1, 256, 0, c->stream>>>(c->d_part, nb, c->d_small);
     return cudaGetLastError();
 }
@@ -425,6 +433,67 @@ static cudaError_t export_t(lbm_ctx *c, double *out)
                                                      out + (int64_t)14 * c->nx * c->ny);
     }
     return cudaGetLastError();
+}
+
+// Halo exchange of a row slab.  Populations that leave a slab through its
+// upper cut are those with e_y = +1 (f2, f5, f6 and g2: planes 2, 5, 6, 11),
+// read from the top interior row; through its lower cut those with e_y = -1
+// (f4, f7, f8, g4: planes 4, 7, 8, 13), read from the bottom interior row.
+// A neighbour writes what it receives into the ghost row its pull reads
+// them from.  Buffers hold 4 x nx values of the storage type, plane-major.
+__device__ __forceinline__ int up_plane(int q) { return q == 0 ? 2 : (q == 1 ? 5 : (q == 2 ? 6 : 11)); }
+__device__ __forceinline__ int down_plane(int q) { return q == 0 ? 4 : (q == 1 ? 7 : (q == 2 ? 8 : 13)); }
+
+template <class E>
+__global__ void halo_pack_kernel(const E *__restrict__ dist, int64_t plane, int64_t pitch, int nx, int row_lo,
+                                 int row_hi, E *__restrict__ lo, E *__restrict__ hi)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+    if (x >= nx) return;
+    if (hi) hi[(int64_t)q * nx + x] = dist[up_plane(q) * plane + (int64_t)(row_hi - 1) * pitch + x];
+    if (lo) lo[(int64_t)q * nx + x] = dist[down_plane(q) * plane + (int64_t)row_lo * pitch + x];
+}
+
+template <class E>
+__global__ void halo_unpack_kernel(E *__restrict__ dist, int64_t plane, int64_t pitch, int nx, int ny,
+                                   const E *__restrict__ lo, const E *__restrict__ hi)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+    if (x >= nx) return;
+    // from below: the lower neighbour's upward populations, into ghost row 0
+    if (lo) dist[up_plane(q) * plane + x] = lo[(int64_t)q * nx + x];
+    // from above: the upper neighbour's downward populations, into ghost row ny - 1
+    if (hi) dist[down_plane(q) * plane + (int64_t)(ny - 1) * pitch + x] = hi[(int64_t)q * nx + x];
+}
+
+template <class E>
+static cudaError_t halo_t(lbm_ctx *c, void *lo, void *hi, const void *rlo, const void *rhi, bool pack)
+{
+    const dim3 grid((c->nx + 255) / 256, 4);
+    E *dist = (E *)c->buf.dist[c->cur];
+    if (pack)
+        halo_pack_kernel<E><<<grid, 256, 0, c->stream>>>(dist, c->plane, c->pitch, c->nx, c->row_lo, c->row_hi,
+                                                         (E *)lo, (E *)hi);
+    else
+        halo_unpack_kernel<E><<<grid, 256, 0, c->stream>>>(dist, c->plane, c->pitch, c->nx, c->ny,
+                                                           (const E *)rlo, (const E *)rhi);
+    return cudaGetLastError();
+}
+
+static cudaError_t halo(lbm_ctx *c, void *lo, void *hi, const void *rlo, const void *rhi, bool pack)
+{
+    switch (c->dist_elem) {
+    case 2: return halo_t<uint16_t>(c, lo, hi, rlo, rhi, pack);
+    case 4: return halo_t<uint32_t>(c, lo, hi, rlo, rhi, pack);
+    case 8: return halo_t<uint64_t>(c, lo, hi, rlo, rhi, pack);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_halo_pack(lbm_ctx *c, void *d_lo, void *d_hi) { return halo(c, d_lo, d_hi, nullptr, nullptr, true); }
+cudaError_t launch_halo_unpack(lbm_ctx *c, const void *d_lo, const void *d_hi)
+{
+    return halo(c, nullptr, nullptr, d_lo, d_hi, false);
 }
 
 #define LBM_DISPATCH(fn, ...)                                      \

@@ -156,6 +156,7 @@ extern "C" int lbm_residual_noalloc(lbm_ctx *c, double *d_snapshot, int first, d
     if (!c || !d_snapshot || !d_result) return LBM_ERR_ARG;
     if (c->ny > LBM_NOALLOC_MAX_ROWS) return LBM_ERR_SIZE;
     if (c->opts.layout != 0) return LBM_ERR_UNSUPPORTED;   // two-buffer layout only
+    if (c->row_lo != 0 || c->row_hi != c->ny) return LBM_ERR_UNSUPPORTED;   // whole cavities only
     if (cudaSetDevice(c->device) != cudaSuccess) return LBM_ERR_CUDA;
     double *part = nullptr;
     const int rc = scratch_address(c->device, &part);

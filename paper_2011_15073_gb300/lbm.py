@@ -98,6 +98,15 @@ SIGNATURES = [
     ("lbm_batch_get_plan", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int)]),
     ("lbm_batch_set_wait_budget", ctypes.c_int, [_VP, ctypes.c_int64]),
+    ("lbm_init_slab", ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.POINTER(Opts)]),
+    ("lbm_slab_rows", ctypes.c_int, [_VP] + [ctypes.POINTER(ctypes.c_int)] * 4),
+    ("lbm_halo_bytes", ctypes.c_size_t, [_VP]),
+    ("lbm_halo_pack", ctypes.c_int, [_VP, _VP, _VP]),
+    ("lbm_halo_unpack", ctypes.c_int, [_VP, _VP, _VP]),
+    ("lbm_nusselt_sums", ctypes.c_int, [_VP, _D, _D]),
+    ("lbm_residual_sums", ctypes.c_int, [_VP, _D]),
     ("lbm_bench_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("lbm_last_cuda_error", ctypes.c_char_p, []),
@@ -261,6 +270,47 @@ def get_state_f64(ctx, nx, ny):
 def set_state_f64(ctx, f=None, g=None, tau=None):
     conv = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (f, g, tau)]
     _check(lib().lbm_set_state_f64(ctx, *[_ptr(a) for a in conv]), "lbm_set_state_f64")
+
+
+def init_slab(nx, ny, y0, y1, n, Da, Ra, Pr, porosity=0.6, **opts):
+    """Create the row slab [y0, y1) of an nx x ny cavity; returns a context handle."""
+    h = _VP()
+    o = default_opts(**opts)
+    _check(lib().lbm_init_slab(ctypes.byref(h), nx, ny, y0, y1, n, Da, Ra, Pr, porosity, ctypes.byref(o)),
+           "lbm_init_slab")
+    return h.value
+
+
+def slab_rows(ctx):
+    """(y0, row_lo, row_hi, ny_local) of a context."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().lbm_slab_rows(ctx, *[ctypes.byref(x) for x in v]), "lbm_slab_rows")
+    return tuple(x.value for x in v)
+
+
+def halo_bytes(ctx) -> int:
+    return int(lib().lbm_halo_bytes(ctx))
+
+
+def halo_pack(ctx, d_lo, d_hi):
+    _check(lib().lbm_halo_pack(ctx, d_lo, d_hi), "lbm_halo_pack")
+
+
+def halo_unpack(ctx, d_lo, d_hi):
+    _check(lib().lbm_halo_unpack(ctx, d_lo, d_hi), "lbm_halo_unpack")
+
+
+def nusselt_sums(ctx):
+    h = ctypes.c_double()
+    c = ctypes.c_double()
+    _check(lib().lbm_nusselt_sums(ctx, ctypes.byref(h), ctypes.byref(c)), "lbm_nusselt_sums")
+    return h.value, c.value
+
+
+def residual_sums(ctx):
+    s = np.zeros(7)
+    _check(lib().lbm_residual_sums(ctx, _ptr(s)), "lbm_residual_sums")
+    return s
 
 
 def bench_fma_peak(kind: str, device: int = -1, reps: int = 20):
