@@ -865,7 +865,8 @@ def study_adjoint(args):
                 ad = res[prec]["dDa"][j, i] * Da[j, i]
                 out.append(abs(ad - fd) / max(abs(fd), 1e-300))
         sweep[repr(hs)] = {"max_rel_f64": max(rel64), "median_rel_f64": float(np.median(rel64)),
-                           "max_rel_f32": max(rel32), "median_rel_f32": float(np.median(rel32))}
+                           "max_rel_f32": max(rel32), "median_rel_f32": float(np.median(rel32)),
+                           "rel_f64_per_node": rel64}
     v = rng.standard_normal((N, N))
     fd_dir = (J_of(Da * np.exp(h * v)) - J_of(Da * np.exp(-h * v))) / (2 * h)
     dir_ad = {p_: float(np.sum(res[p_]["dDa"] * Da * v)) for p_ in ("f64", "f32")}

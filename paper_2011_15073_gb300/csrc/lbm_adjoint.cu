@@ -25,9 +25,16 @@ namespace {
 
 using namespace lbm;
 
-// Parameters of the chain from (n, Ra, Da) to the lattice coefficients.
+// Parameters of the chain from (n, Ra, Da) to the lattice coefficients,
+// with the per-case constants of the parameter gradients computed once on
+// the host: dn = a_nu dJ/dnu_ref + dJ/d(n - 1), dRa = b_nu dJ/dnu_ref +
+// b_wT dJ/d(1/tauT), and 1/Da for a uniform Darcy number.
 struct Chain {
     double n, Ra, tauT;  // power-law index, Rayleigh number, thermal tau
+    double a_nu;         // d nu_ref / dn = nu_ref ln(Ra) / 2
+    double b_nu;         // d nu_ref / dRa = -nu_ref (2 - n) / (2 Ra)
+    double b_wT;         // d (1/tauT) / dRa = (tauT - 1/2) / (2 Ra tauT^2)
+    double inv_Da;       // 1 / Da of a uniform permeability
 };
 
 // Seed: lambda_T = dJ/ds_T.  Nu_hot = mean_j -L (9 theta_0 - theta_1 - 8)/3
@@ -55,16 +62,32 @@ __global__ void adj_seed_kernel(V *__restrict__ lam, Phys<V> p, double coef0, do
     }
 }
 
+// Sum of v over a block of 128 threads (fixed order); thread 0 gets it.
+__device__ __forceinline__ double block128_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    const double t = threadIdx.x == 0 ? (sh[0] + sh[1]) + (sh[2] + sh[3]) : 0.0;
+    __syncthreads();
+    return t;
+}
+
 // One reverse step: lam_out (adjoint of s_{t+1}) -> lam_in (adjoint of s_t),
-// recomputing the collision of every node from s_t.
+// recomputing the collision of every node from s_t.  The per-node Darcy
+// gradient accumulates in gDa (FP64, one slot per node); the n and Ra
+// gradients are summed over the block and accumulate in the block's slot of
+// gnb / gRab (FP64; fixed order, so the result is deterministic).
 template <int PREC, class V>
 __global__ void __launch_bounds__(128)
 adj_step_kernel(const typename Store<PREC>::S *__restrict__ st, const typename Store<PREC>::TauS *__restrict__ tst,
                 const V *__restrict__ lam_out, V *__restrict__ lam_in, double *__restrict__ gDa,
-                double *__restrict__ gn, double *__restrict__ gRa, Phys<V> p, Chain ch)
+                double *__restrict__ gnb, double *__restrict__ gRab, Phys<V> p, Chain ch)
 {
+    __shared__ double sh[4];
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= p.nx) return;
+    V dn = V(0), dRa = V(0);
+    if (x < p.nx) {
     const int64_t P = p.plane, W = p.pitch;
     const int64_t k = (int64_t)y * W + x;
     V f[9], g[5];
@@ -97,20 +120,22 @@ adj_step_kernel(const typename Store<PREC>::S *__restrict__ st, const typename S
     if (xr) G[3 * P + k + 1] = gb[3]; else G[1 * P + k] = -gb[3];
     if (yt) G[4 * P + k + W] = gb[4]; else G[2 * P + k] = gb[4];
     lam_in[14 * P + k] = tb_prev;
-    // parameters: porous coefficients of this node -> Da(x)
+    // parameters: porous coefficients of this node -> Da(x) (K = Da L^2, so
+    // every coefficient scales as 1/Da or 1/sqrt(Da)), in the compute type
     const Porous<V> q = porous_at(p, k);
-    const double Da = p.da ? double(load_da(p, k)) : double(p.eps / (p.eps_invK * p.L2));
-    const double dDa = -(double(q.heK) * double(pa.heK) + double(q.eK) * double(pa.eK)) / Da -
-                       (double(q.c1) * double(pa.c1) + double(q.eFsK) * double(pa.eFsK)) / (2.0 * Da);
+    const V iDa = p.da ? vrcp(load_da(p, k)) : V(ch.inv_Da);
+    const V dDa = -iDa * (vfma(q.heK, pa.heK, q.eK * pa.eK) + V(0.5) * vfma(q.c1, pa.c1, q.eFsK * pa.eFsK));
     // nu_ref = Pr Ra^(-(2-n)/2) U_c L, n - 1, and 1/tauT with tauT - 1/2 ~ Ra^(-1/2)
-    const double nu_ref = double(p.nu_ref), wT = double(p.omegaT);
-    const double dn = double(pa.nu_ref) * nu_ref * 0.5 * log(ch.Ra) + double(pa.nm1);
-    const double dRa = double(pa.nu_ref) * (-nu_ref * (2.0 - ch.n) / (2.0 * ch.Ra)) +
-                       double(pa.omegaT) * wT * wT * (ch.tauT - 0.5) / (2.0 * ch.Ra);
-    const int64_t q0 = (int64_t)y * p.nx + x;
-    gDa[q0] += dDa;
-    gn[q0] += dn;
-    gRa[q0] += dRa;
+    dn = vfma(pa.nu_ref, V(ch.a_nu), pa.nm1);
+    dRa = vfma(pa.nu_ref, V(ch.b_nu), pa.omegaT * V(ch.b_wT));
+    gDa[(int64_t)y * p.nx + x] += double(dDa);
+    }
+    const double sn = block128_sum(double(dn), sh), sR = block128_sum(double(dRa), sh);
+    if (threadIdx.x == 0) {
+        const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        gnb[b] += sn;
+        gRab[b] += sR;
+    }
 }
 
 // Single-block FP64 sum of n values (fixed order).
@@ -186,7 +211,9 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
     const int seg_len = (int)(steps < ckpt ? steps : ckpt);
     char *seg = (char *)alloc((dist_bytes + tau_bytes) * (size_t)(seg_len > 0 ? seg_len : 1));
     V *lam[2] = {(V *)alloc(lam_bytes), (V *)alloc(lam_bytes)};
-    double *g3 = (double *)alloc(sizeof(double) * 3 * nn);
+    const dim3 grid((c->nx + 127) / 128, c->ny);
+    const size_t nblk = (size_t)grid.x * grid.y;
+    double *g3 = (double *)alloc(sizeof(double) * (nn + 2 * nblk));   // dDa per node, dn / dRa per block
     double *red = (double *)alloc(sizeof(double) * 4);
     if (!ck || !seg || !lam[0] || !lam[1] || !g3 || !red) {
         cleanup();
@@ -195,7 +222,7 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
     // device memory of this run: the context's two state buffers plus the
     // checkpoints, one segment of states, two adjoint buffers and the gradients
     const double total = (double)(dist_bytes + tau_bytes) * (double)(nseg + seg_len + 2) + 2.0 * lam_bytes +
-                         sizeof(double) * 3.0 * nn;
+                         sizeof(double) * (double)(nn + 2 * nblk);
     if (peak_bytes) *peak_bytes = total;
     if (from_rest) {
         c->cur = 0;
@@ -229,20 +256,24 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
     if (rc == LBM_OK) {
         cudaMemsetAsync(lam[0], 0, lam_bytes, c->stream);
         cudaMemsetAsync(lam[1], 0, lam_bytes, c->stream);
-        cudaMemsetAsync(g3, 0, sizeof(double) * 3 * nn, c->stream);
+        cudaMemsetAsync(g3, 0, sizeof(double) * (nn + 2 * nblk), c->stream);
         adj_seed_kernel<V><<<(c->ny + 127) / 128, 128, 0, c->stream>>>(lam[0], pv, -3.0 * L / (c->ny * dT),
                                                                        L / (3.0 * c->ny * dT));
         if (cudaGetLastError() != cudaSuccess) rc = LBM_ERR_CUDA;
     }
     // reverse sweep, one segment at a time
-    Chain chain{c->lat.n, 0.0, c->lat.tauT};
+    Chain chain{c->lat.n, 0.0, c->lat.tauT, 0.0, 0.0, 0.0, 0.0};
     {
         // Ra from the mapping: tauT - 1/2 = 3 U_c L / sqrt(Ra)
         const double Uc = c->opts.Ma / sqrt(3.0);
         const double r = 3.0 * Uc * L / (c->lat.tauT - 0.5);
         chain.Ra = r * r;
+        const double nu_ref = c->lat.nu_ref, wT = 1.0 / c->lat.tauT;
+        chain.a_nu = nu_ref * 0.5 * log(chain.Ra);
+        chain.b_nu = -nu_ref * (2.0 - chain.n) / (2.0 * chain.Ra);
+        chain.b_wT = wT * wT * (chain.tauT - 0.5) / (2.0 * chain.Ra);
+        chain.inv_Da = c->lat.L * c->lat.L / c->lat.K;
     }
-    const dim3 grid((c->nx + 127) / 128, c->ny);
     for (int64_t j = nseg - 1; j >= 0 && rc == LBM_OK; j--) {
         const int64_t len = (j + 1) * ckpt <= steps ? ckpt : steps - j * ckpt;
         // states s_{j ckpt + i}, i = 0..len-1, recomputed from the checkpoint
@@ -252,7 +283,7 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
             if (lbm::launch_step_buffers(c, sgd(i - 1), sgd(i), sgt(i - 1), sgt(i)) != cudaSuccess) rc = LBM_ERR_CUDA;
         for (int i = (int)len - 1; i >= 0 && rc == LBM_OK; i--) {
             adj_step_kernel<PREC, V><<<grid, 128, 0, c->stream>>>(sgd(i), sgt(i), lam[cur], lam[cur ^ 1], g3,
-                                                                 g3 + nn, g3 + 2 * nn, pv, chain);
+                                                                 g3 + nn, g3 + nn + nblk, pv, chain);
             if (cudaGetLastError() != cudaSuccess) rc = LBM_ERR_CUDA;
             cur ^= 1;
         }
@@ -260,8 +291,8 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
     // reductions: sum of the n and Ra partials, and lambda_0 on tau for tau_0(n, Ra)
     double h[3] = {0, 0, 0};
     if (rc == LBM_OK) {
-        sum_kernel<<<1, 256, 0, c->stream>>>(g3 + nn, (int64_t)nn, red);
-        sum_kernel<<<1, 256, 0, c->stream>>>(g3 + 2 * nn, (int64_t)nn, red + 1);
+        sum_kernel<<<1, 256, 0, c->stream>>>(g3 + nn, (int64_t)nblk, red);
+        sum_kernel<<<1, 256, 0, c->stream>>>(g3 + nn + nblk, (int64_t)nblk, red + 1);
         tau0_sum_kernel<V><<<1, 256, 0, c->stream>>>(lam[cur], pv, red + 2);
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpyAsync(h, red, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream) ||
