@@ -49,16 +49,17 @@ step2_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PRE
     step2_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
 }
 
-// Four nodes per thread (16-bit storages).  At most 96 registers, so that
-// five 128-thread blocks fit on an SM: more bytes in flight per SM than the
-// 64-80-register blocks of step2_kernel (measured against caps of 80 and
-// 128 registers: both slower).
+// Four nodes per thread (16-bit storages): 64-thread blocks of 256 nodes,
+// at most 96 registers so that ten blocks (20 warps) fit on an SM: more
+// bytes in flight per SM than the 64-80-register blocks of step2_kernel
+// (measured against caps of 80 and 128 registers: both slower; 128-thread
+// blocks at five per SM: 2 % slower).
 template <int PREC, int FIELD, int TAU>
-__global__ void __launch_bounds__(128, 5)
+__global__ void __launch_bounds__(64, 10)
 step4_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
              const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
 {
-    step4_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 512, blockIdx.y);
+    step4_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
 }
 
 // tau the next collision of every node starts from, in implicit mode (the
@@ -337,7 +338,7 @@ static cudaError_t step4_buffers_tau(lbm_ctx *c, const void *src, void *dst, con
 {
     using St = Store<PREC>;
     auto *kern = c->d_da ? step4_kernel<PREC, 1, TAU> : step4_kernel<PREC, 0, TAU>;
-    kern<<<node_grid(c, 512), 128, 0, c->stream>>>((const typename St::S *)src, (typename St::S *)dst,
+    kern<<<node_grid(c, 256), 64, 0, c->stream>>>((const typename St::S *)src, (typename St::S *)dst,
                                                   (const float *)tsrc, (float *)tdst, make_params<float>(c),
                                                   make_params<F2>(c));
     return cudaGetLastError();

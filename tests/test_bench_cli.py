@@ -59,10 +59,10 @@ def test_variant_names():
 def test_reduced_storage_summary_picks_fastest_within_the_bar():
     import bench
     v = {"f64": {"MLUPS": 2000.0},
-         "f16s": {"MLUPS": 69000.0, "dnu_rel_vs_f64_256": 7.6e-4},
-         "bf16s": {"MLUPS": 71000.0, "dnu_rel_vs_f64_256": 2.4e-3},    # faster, misses the bar
-         "f16d": {"MLUPS": 74000.0, "dnu_rel_vs_f64_256": 0.14},
-         "f32": {"MLUPS": 54000.0, "dnu_rel_vs_f64_256": None}}       # no record: not a candidate
+         "f16s": {"MLUPS": 69000.0, "dnu_rel_vs_f64_512": 7.6e-4},
+         "bf16s": {"MLUPS": 71000.0, "dnu_rel_vs_f64_512": 2.4e-3},    # faster, misses the bar
+         "f16d": {"MLUPS": 74000.0, "dnu_rel_vs_f64_512": 0.14},
+         "f32": {"MLUPS": 54000.0, "dnu_rel_vs_f64_512": None}}       # no record: not a candidate
     s = bench.reduced_storage_summary(v, "f32d", 57000.0)
     assert s["variant"] == "f16s" and s["speedup_vs_f64_storage"] == 69000.0 / 2000.0
     assert bench.reduced_storage_summary({"f16s": v["f16s"]}, "f32d", 1.0) is None   # no FP64 run to compare
