@@ -135,6 +135,19 @@ def recorded_dnu(storage):
     return recorded(storage, None, PRECISION_FILE)
 
 
+def recorded_dnu_detail(storage):
+    """The per-n spread line of the precision record for this storage (text), or None."""
+    try:
+        with open(PRECISION_FILE) as fh:
+            for line in fh:
+                parts = line.split(None, 2)
+                if len(parts) == 3 and parts[0] == "detail" and parts[1] == storage:
+                    return parts[2].strip()
+    except OSError:
+        pass
+    return None
+
+
 def recorded_traffic(prec, N):
     """DRAM bytes per launch of the step kernel at this grid, or None."""
     return recorded(prec, N)
@@ -305,6 +318,7 @@ def reduced_storage_summary(variants, prec, mlups):
         return None
     best = max(cands)
     return {"variant": best[1], "MLUPS": best[0], "dnu_rel_vs_f64": best[2],
+            "dnu_detail": recorded_dnu_detail(best[1]), "dnu_grid": [512, 512],
             "speedup_vs_f64_storage": best[0] / f64["MLUPS"], "f64_MLUPS": f64["MLUPS"],
             "dnu_source": "recorded: bench.py --study precision --study-N 512 (512^2 steady state, n = 0.6 and 1.0, "
                           "max over 4 rounding streams of the 20-sample mean), against FP64 storage on the GPU, "

@@ -39,15 +39,15 @@ __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restr
 }
 
 // One tile of a row: thread t of the block updates nodes xbase + 2t and
-// xbase + 2t + 1 of row y.  A warp whose 64 nodes lie in an interior row and
-// inside the row takes the fast path -- aligned pair loads and stores, the
+// xbase + 2t + 1 of row y.  A warp whose 64 nodes and their neighbours are
+// all interior takes the fast path -- aligned pair loads and stores, the
 // x-shifted populations exchanged by warp shuffles, both nodes' arithmetic
-// on the packed FP32x2 pipe; the warp at the ragged end of a row and the
-// warps of the top and bottom rows update their nodes one at a time with the
-// wall rules.  The branch is uniform per warp.  In the first and last warp
-// of a row the packed result of the wall node itself (x = 0 or nx - 1) used a
-// value from beyond the wall, so that one node is then updated again with
-// the wall rules.  TAU as for step_node.
+// on the packed FP32x2 pipe; any warp that touches a wall or the ragged end
+// of a row updates its nodes one at a time with the wall rules.  The branch
+// is uniform per warp.  (Handing the side-wall warps to the packed path, as
+// step4_tile does, costs this tile 8-40 registers per thread in its
+// single-cavity and batched kernels; at 64 nodes per warp the wall warps are
+// a small share of a row.)  TAU as for step_node.
 template <int PREC, int FIELD = 2, int TAU = 0>
 __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__restrict__ src,
                                            typename Store<PREC>::S *__restrict__ dst,
@@ -59,7 +59,7 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
     const int lane = threadIdx.x & 31;
     const int x0 = xbase + 2 * threadIdx.x;
     const int wx = xbase + 2 * (threadIdx.x & ~31);
-    const bool fast = y > 0 && y < p.ny - 1 && wx + 64 <= p.nx;
+    const bool fast = y > 0 && y < p.ny - 1 && wx > 0 && wx + 64 < p.nx;
     if (!fast) {
         for (int j = 0; j < 2; j++)
             if (x0 + j < p.nx) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, x0 + j, y);
@@ -98,9 +98,6 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
 #pragma unroll
     for (int i = 0; i < 5; i++) St::sdv2(dst + (9 + i) * P, k, g[i], float(rest_g(i)), rng);
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tdst + k) = tau.v;
-    // the wall node of the first / last warp of the row, again with the wall rules
-    if (x0 == 0) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, 0, y);
-    if (x0 + 1 == p.nx - 1) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, p.nx - 1, y);
 }
 
 // One pair of nodes of a four-node tile: the 14 stored words of the pair
@@ -136,10 +133,14 @@ __device__ __forceinline__ F2 pair_words(const Phys<F2> &p2, const uint32_t (&in
 // permutes and one warp shuffle (lane 0 / 31 load their halo word), the two
 // pairs are collided one after the other, and each population row is
 // stored as one 8-byte word.  The top and bottom rows and the warp at the
-// ragged end of a row update their nodes one at a time with the wall rules;
-// in the first and last warp of a row the wall node is updated again with
-// them after the packed pass, as in step2_tile.  Results equal step2_tile's
-// wherever both take the packed path.
+// ragged end of a row update their nodes one at a time with the wall rules.
+// The first and last warp of a row take the packed path too (at 128 nodes
+// per warp, updating them one node at a time cost 6 % of a 4096-wide row's
+// nodes three times the instructions); the packed result of the wall node
+// itself (x = 0 or nx - 1) used a value from beyond the wall -- the previous
+// row's tail or the next row's head, inside the allocation -- so that one
+// node is then updated again with the wall rules.  Results equal
+// step2_tile's wherever both take the packed path.
 template <int PREC, int FIELD, int TAU>
 __device__ __forceinline__ void step4_tile(const typename Store<PREC>::S *__restrict__ src,
                                            typename Store<PREC>::S *__restrict__ dst,

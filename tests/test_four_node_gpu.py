@@ -2,11 +2,11 @@
 (lbm_opts.staging = 3) against the two-node kernel (staging = 1) and the
 oracle.
 
-Wherever both kernels take their packed path (a warp of an interior row
-whose nodes lie inside the row: 64 nodes for the two-node kernel, 128 for the
-four-node one; the side-wall node itself excepted, which both update again
-with the wall rules) they run the same packed arithmetic on the same values
-and draw the same random bits.  Elsewhere a kernel updates its nodes one at a
+Wherever both kernels take their packed path (two-node kernel: a warp of 64
+nodes whose nodes and neighbours are all interior; four-node kernel: a warp
+of 128 nodes inside an interior row, the side-wall node itself excepted,
+which it updates again with the wall rules) they run the same packed
+arithmetic on the same values and draw the same random bits.  Elsewhere a kernel updates its nodes one at a
 time with the wall rules: scalar arithmetic, which the compiler may contract
 into other fused multiply-adds (the relaxation time can differ in its last
 bits), and other random bits for the stochastic-rounding storages.  So, one
@@ -49,11 +49,16 @@ def cavity(lbm, nx, ny, c, prec, staging, tau_iters=0):
 
 def fast_path(nx, ny, span):
     """Nodes that a kernel with warps of `span` nodes updates on its packed
-    path (warps start at multiples of span along each row; a warp that ends
-    beyond the row, and the side-wall nodes, go one node at a time)."""
+    path (warps start at multiples of span along each row).  Two-node
+    kernel (span 64): warps whose nodes and neighbours are all interior.
+    Four-node kernel (span 128): every warp that lies inside an interior
+    row, except the side-wall nodes themselves."""
     x = np.arange(nx)
     wx = x - x % span
-    fx = (wx + span <= nx) & (x > 0) & (x < nx - 1)
+    if span == 64:
+        fx = (wx > 0) & (wx + span < nx)
+    else:
+        fx = (wx + span <= nx) & (x > 0) & (x < nx - 1)
     y = np.arange(ny)
     fy = (y > 0) & (y < ny - 1)
     return fy[:, None] & fx[None, :]
