@@ -19,6 +19,7 @@
 #include "lbm_adjoint.cuh"
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "lbm_trace.h"
 #include "lbm_step.cuh"
 
 namespace {
@@ -274,20 +275,58 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
         chain.b_wT = wT * wT * (chain.tauT - 0.5) / (2.0 * chain.Ra);
         chain.inv_Da = c->lat.L * c->lat.L / c->lat.K;
     }
+    // One segment's kernels: the states s_{j ckpt + i}, i = 1..len-1,
+    // recomputed from the copy of the checkpoint in slot 0, then the reverse
+    // steps i = len-1..0 from adjoint buffer `c0`.
+    auto segment = [&](int len, int c0) -> int {
+        for (int i = 1; i < len; i++)
+            if (lbm::launch_step_buffers(c, sgd(i - 1), sgd(i), sgt(i - 1), sgt(i)) != cudaSuccess)
+                return LBM_ERR_CUDA;
+        int cc = c0;
+        for (int i = len - 1; i >= 0; i--) {
+            adj_step_kernel<PREC, V><<<grid, 128, 0, c->stream>>>(sgd(i), sgt(i), lam[cc], lam[cc ^ 1], g3,
+                                                                 g3 + nn, g3 + nn + nblk, pv, chain);
+            if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+            cc ^= 1;
+        }
+        return LBM_OK;
+    };
+    // Full segments replay one captured graph per parity of the adjoint
+    // buffer they start from (same kernels, same arguments: identical
+    // results); a shorter last segment, or a stream that is already being
+    // captured, runs plain launches.
+    cudaGraphExec_t seg_exec[2] = {nullptr, nullptr};
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    const bool can_capture = cudaStreamIsCapturing(c->stream, &cap_status) == cudaSuccess &&
+                             cap_status == cudaStreamCaptureStatusNone && ckpt >= 2;
     for (int64_t j = nseg - 1; j >= 0 && rc == LBM_OK; j--) {
         const int64_t len = (j + 1) * ckpt <= steps ? ckpt : steps - j * ckpt;
-        // states s_{j ckpt + i}, i = 0..len-1, recomputed from the checkpoint
         cudaMemcpyAsync(sgd(0), ckd(j), dist_bytes, cudaMemcpyDeviceToDevice, c->stream);
         cudaMemcpyAsync(sgt(0), ckt(j), tau_bytes, cudaMemcpyDeviceToDevice, c->stream);
-        for (int i = 1; i < len && rc == LBM_OK; i++)
-            if (lbm::launch_step_buffers(c, sgd(i - 1), sgd(i), sgt(i - 1), sgt(i)) != cudaSuccess) rc = LBM_ERR_CUDA;
-        for (int i = (int)len - 1; i >= 0 && rc == LBM_OK; i--) {
-            adj_step_kernel<PREC, V><<<grid, 128, 0, c->stream>>>(sgd(i), sgt(i), lam[cur], lam[cur ^ 1], g3,
-                                                                 g3 + nn, g3 + nn + nblk, pv, chain);
-            if (cudaGetLastError() != cudaSuccess) rc = LBM_ERR_CUDA;
-            cur ^= 1;
+        bool replayed = false;
+        if (can_capture && len == ckpt) {
+            if (!seg_exec[cur]) {
+                cudaGraph_t g = nullptr;
+                if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                    const int rs = segment((int)len, cur);
+                    const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+                    if (rs == LBM_OK && ee == cudaSuccess && g &&
+                        cudaGraphInstantiate(&seg_exec[cur], g, 0) != cudaSuccess)
+                        seg_exec[cur] = nullptr;
+                    if (g) cudaGraphDestroy(g);
+                    cudaGetLastError();
+                }
+            }
+            if (seg_exec[cur]) {
+                if (cudaGraphLaunch(seg_exec[cur], c->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
+                replayed = true;
+            }
         }
+        if (!replayed && rc == LBM_OK) rc = segment((int)len, cur);
+        if (len & 1) cur ^= 1;
     }
+    for (auto &e : seg_exec)
+        if (e) cudaGraphExecDestroy(e);
     // reductions: sum of the n and Ra partials, and lambda_0 on tau for tau_0(n, Ra)
     double h[3] = {0, 0, 0};
     if (rc == LBM_OK) {
@@ -326,6 +365,7 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
 extern "C" int lbm_adjoint_nu(lbm_ctx *c, int64_t steps, int ckpt_every, int from_rest, double *J, double *dDa,
                               double *dn, double *dRa, double *peak_bytes)
 {
+    LBM_TRACE("lbm_adjoint_nu");
     if (!c || steps < 1 || ckpt_every < 1) return LBM_ERR_ARG;
     if (c->opts.layout != 0 || c->opts.tau_iters != 0) return LBM_ERR_UNSUPPORTED;
     if (c->row_lo != 0 || c->row_hi != c->ny) return LBM_ERR_UNSUPPORTED;   // whole cavities only

@@ -17,6 +17,7 @@
 
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
+#include "lbm_trace.h"
 #include "lbm_step.cuh"
 
 namespace {
@@ -544,6 +545,7 @@ int lbm_batch_get_case(lbm_batch *b, int i, lbm_ctx **ctx)
 
 int lbm_batch_step(lbm_batch *b, int64_t k)
 {
+    LBM_TRACE("lbm_batch_step");
     if (!b || k < 0) return LBM_ERR_ARG;
     BK(cudaSetDevice(b->device));
     int rc = upload_cases(b);   // current buffers of every case
@@ -572,6 +574,7 @@ int lbm_batch_step(lbm_batch *b, int64_t k)
 int lbm_batch_run_to_steady(lbm_batch *b, double tol, int64_t max_steps, int graph_mode, int64_t *steps,
                             double *resid, int *reason)
 {
+    LBM_TRACE("lbm_batch_run_to_steady");
     if (!b || max_steps < 0 || !(tol >= 0) || (graph_mode != 0 && graph_mode != 1)) return LBM_ERR_ARG;
     BK(cudaSetDevice(b->device));
     if (int e = batch_err(b)) return e;
@@ -734,6 +737,7 @@ int lbm_batch_set_wait_budget(lbm_batch *b, int64_t cycles)
 
 int lbm_batch_tune(lbm_batch *b, int steps, int *threads_out)
 {
+    LBM_TRACE("lbm_batch_tune");
     if (!b || steps < 2) return LBM_ERR_ARG;
     BK(cudaSetDevice(b->device));
     if (int e = batch_err(b)) return e;

@@ -8,6 +8,7 @@
 #include <new>
 
 #include "lbm_internal.h"
+#include "lbm_trace.h"
 
 static thread_local char g_last_cuda[256] = "";
 
@@ -340,6 +341,7 @@ static bool is_slab(const lbm_ctx *c) { return c->row_lo != 0 || c->row_hi != c-
 
 int lbm_halo_pack(lbm_ctx *c, void *d_lo, void *d_hi)
 {
+    LBM_TRACE("lbm_halo_pack");
     if (!c) return LBM_ERR_ARG;
     if ((d_lo && c->row_lo == 0) || (d_hi && c->row_hi == c->ny)) return LBM_ERR_ARG;   // no neighbour there
     CK(cudaSetDevice(c->device));
@@ -349,6 +351,7 @@ int lbm_halo_pack(lbm_ctx *c, void *d_lo, void *d_hi)
 
 int lbm_halo_unpack(lbm_ctx *c, const void *d_lo, const void *d_hi)
 {
+    LBM_TRACE("lbm_halo_unpack");
     if (!c) return LBM_ERR_ARG;
     if ((d_lo && c->row_lo == 0) || (d_hi && c->row_hi == c->ny)) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
@@ -440,6 +443,7 @@ int lbm_get_lattice(const lbm_ctx *c, lbm_lattice *out)
 
 int lbm_step(lbm_ctx *c, int64_t k)
 {
+    LBM_TRACE("lbm_step");
     if (!c || k < 0) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
     int64_t t = 0;
@@ -476,6 +480,7 @@ int lbm_synchronize(lbm_ctx *c)
 
 int lbm_fields(lbm_ctx *c, double *rho, double *ux, double *uy, double *T, double *nu)
 {
+    LBM_TRACE("lbm_fields");
     if (!c) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
     if (int rc0 = canonical(c)) return rc0;
@@ -494,6 +499,7 @@ int lbm_fields(lbm_ctx *c, double *rho, double *ux, double *uy, double *T, doubl
 
 int lbm_nusselt(lbm_ctx *c, double *hot, double *cold, double *local)
 {
+    LBM_TRACE("lbm_nusselt");
     if (!c) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
     if (int rc0 = canonical(c)) return rc0;
@@ -509,6 +515,7 @@ int lbm_nusselt(lbm_ctx *c, double *hot, double *cold, double *local)
 
 int lbm_residual(lbm_ctx *c, double *resid)
 {
+    LBM_TRACE("lbm_residual");
     if (!c) return LBM_ERR_ARG;
     CK(cudaSetDevice(c->device));
     if (int rc0 = canonical(c)) return rc0;
@@ -531,6 +538,7 @@ int lbm_residual(lbm_ctx *c, double *resid)
 int lbm_run_to_steady(lbm_ctx *c, double tol, int64_t max_steps, int64_t *steps_done, double *resid,
                       int *reason)
 {
+    LBM_TRACE("lbm_run_to_steady");
     if (!c || max_steps < 0 || !(tol >= 0)) return LBM_ERR_ARG;
     if (is_slab(c)) return LBM_ERR_UNSUPPORTED;   // its ghost rows need an exchange every step
     c->have_snap = false;
