@@ -214,7 +214,9 @@ class DistributedSlab:
 
     def exchange(self):
         """Send this slab's cut populations to the neighbours and fill the
-        ghost rows with theirs."""
+        ghost rows with theirs (nothing to do for a single slab)."""
+        if not (self.has_lo or self.has_hi):
+            return
         self.ops.pack(self._ptr(self.send_lo), self._ptr(self.send_hi))
         ops = []
         P2P = self.dist.P2POp
