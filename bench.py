@@ -919,7 +919,8 @@ def run_strong(args, torch, lbm, rank, world, local):
     import torch.distributed as dist
     from paper_2011_15073_gb300 import slabs
     N, prec, delta = args.N, args.prec, args.delta
-    if not dist.is_initialized():   # one rank: a group of one, so the same slab path runs
+    own_group = not dist.is_initialized()
+    if own_group:   # one rank: a group of one, so the same slab path runs
         with socket.socket() as sk:
             sk.bind(("127.0.0.1", 0))
             port = sk.getsockname()[1]
@@ -948,6 +949,8 @@ def run_strong(args, torch, lbm, rank, world, local):
         barrier()
     total = max_over_ranks(t0.elapsed_time(t1) / 1e3, world, "cuda")
     slab.ops.close()
+    if own_group:
+        dist.destroy_process_group()
     if rank != 0:
         return
     y0, y1 = slabs.partition(N, world)[0]
