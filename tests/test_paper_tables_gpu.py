@@ -21,21 +21,34 @@ reason for each tolerance):
 """
 import pytest
 
+from golden.paper import paper_tables
+
 pytestmark = pytest.mark.gpu
 
-# (table, n, Da (None: clear fluid), Ra, Pr, paper's Nu, tolerance)
-CASES = [
-    ("table1", 0.6, None, 1e5, 100.0, 12.95289, 0.12),
-    ("table1", 1.0, None, 1e5, 100.0, 4.69148, 0.02),
-    ("table1", 1.4, None, 1e5, 100.0, 2.44821, 0.035),
-    ("case1", 0.6, 1e-3, 1e5, 6.2, 9.249539, 0.04),
-    ("case1", 1.0, 1e-3, 1e5, 6.2, 2.430419, 0.01),
-    ("case1", 1.4, 1e-3, 1e5, 6.2, 1.300101, 0.01),
-    ("case2", 0.6, 1e-2, 1e5, 6.2, 12.835687, 0.13),
-    ("case2", 0.6, 1e-1, 1e5, 6.2, 13.316177, 0.15),
-    ("case3", 0.6, 1e-2, 1e3, 6.2, 1.068697, 0.03),
-    ("case3", 0.6, 1e-2, 1e4, 6.2, 4.411946, 0.02),
+# (table, n, Da (None: clear fluid), Ra, Pr, tolerance); the paper's value
+# comes from tests/golden/paper_tables.txt
+TOLERANCES = [
+    ("table1", 0.6, None, 1e5, 100.0, 0.12),
+    ("table1", 1.0, None, 1e5, 100.0, 0.02),
+    ("table1", 1.4, None, 1e5, 100.0, 0.035),
+    ("case1", 0.6, 1e-3, 1e5, 6.2, 0.04),
+    ("case1", 1.0, 1e-3, 1e5, 6.2, 0.01),
+    ("case1", 1.4, 1e-3, 1e5, 6.2, 0.01),
+    ("case2", 0.6, 1e-2, 1e5, 6.2, 0.13),
+    ("case2", 0.6, 1e-1, 1e5, 6.2, 0.15),
+    ("case3", 0.6, 1e-2, 1e3, 6.2, 0.03),
+    ("case3", 0.6, 1e-2, 1e4, 6.2, 0.02),
 ]
+
+
+def _paper_nu(table, n, Da, Ra, Pr):
+    for r in paper_tables():
+        if (r["case"] == table or r["table"] == table) and (r["n"], r["Da"], r["Ra"], r["Pr"]) == (n, Da, Ra, Pr):
+            return r["nu"]
+    raise KeyError((table, n, Da, Ra, Pr))
+
+
+CASES = [(t, n, Da, Ra, Pr, _paper_nu(t, n, Da, Ra, Pr), tol) for t, n, Da, Ra, Pr, tol in TOLERANCES]
 
 
 @pytest.fixture(scope="module")
