@@ -168,3 +168,27 @@ def test_fma_probe_rejects_bad_arguments():
     assert lbm.lib().lbm_bench_fma_peak(3, -1, 5, ctypes.byref(out), None) == -1
     assert lbm.lib().lbm_bench_fma_peak(0, -1, 0, ctypes.byref(out), None) == -1
     assert lbm.lib().lbm_bench_fma_peak(0, -1, 5, None, None) == -1
+
+
+def test_slab_and_batch_calls_validate_arguments_before_the_device():
+    """Slab creation, slab queries, halo and partial-sum calls and the batch
+    plan calls reject bad arguments with LBM_ERR_ARG before any CUDA call."""
+    import ctypes
+    from paper_2011_15073_gb300 import lbm
+    lib = lbm.lib()
+    h = ctypes.c_void_p()
+    o = lbm.default_opts()
+    for (ny, y0, y1) in [(1, 0, 1), (40, -1, 10), (40, 10, 41), (40, 20, 20), (40, 30, 20)]:
+        assert lib.lbm_init_slab(ctypes.byref(h), 32, ny, y0, y1, 0.6, 1e-2, 1e5, 6.2, 0.6, ctypes.byref(o)) == -1
+        assert h.value is None
+    o.layout = 1   # the in-place layout has no slab form
+    assert lib.lbm_init_slab(ctypes.byref(h), 32, 40, 0, 20, 0.6, 1e-2, 1e5, 6.2, 0.6, ctypes.byref(o)) == -7
+    assert lib.lbm_slab_rows(None, None, None, None, None) == -1
+    assert lib.lbm_halo_bytes(None) == 0
+    assert lib.lbm_halo_pack(None, None, None) == -1
+    assert lib.lbm_halo_unpack(None, None, None) == -1
+    assert lib.lbm_nusselt_sums(None, None, None) == -1
+    assert lib.lbm_residual_sums(None, None) == -1
+    assert lib.lbm_batch_set_plan(None, 0, 128, 8) == -1
+    assert lib.lbm_batch_get_plan(None, None, None, None) == -1
+    assert lib.lbm_batch_set_wait_budget(None, 100) == -1
