@@ -240,6 +240,21 @@ size_t lbm_state_bytes(const lbm_ctx *ctx);
 int lbm_get_state(lbm_ctx *ctx, void *host, size_t bytes);
 int lbm_set_state(lbm_ctx *ctx, const void *host, size_t bytes);
 
+/* Checkpoint / resume.  A checkpoint is a self-describing byte blob in host
+ * memory (caller-owned, lbm_checkpoint_bytes long): a versioned header
+ * (magic "LBMCKPT1", grid, storage, layout, tau scheme, slab rows, the
+ * lattice-unit parameters, the step count and lbm_opts.seed) followed by
+ * the native state of lbm_get_state.  Loading it into a context created
+ * with the same grid, parameters and options restores the state and the
+ * step count, so the run continues exactly as the saved one would have
+ * after the save (the stochastic rounding's seeds included).  A per-node
+ * Darcy field is not part of it: set it again.  Both calls are synchronous.
+ * Errors: LBM_ERR_ARG (size, or a blob that is not a checkpoint of a run
+ * with the same grid, storage, options and parameters), LBM_ERR_CUDA. */
+size_t lbm_checkpoint_bytes(const lbm_ctx *ctx);
+int lbm_checkpoint_save(lbm_ctx *ctx, void *host, size_t bytes);
+int lbm_checkpoint_load(lbm_ctx *ctx, const void *host, size_t bytes);
+
 /* The post-collision state as FP64 host arrays: f[9][ny][nx], g[5][ny][nx]
  * and tau[ny][nx] (full population values, deviations resolved).  The
  * import rounds to the storage precision.  Any pointer may be NULL (skipped

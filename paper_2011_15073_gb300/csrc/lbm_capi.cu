@@ -606,6 +606,75 @@ int lbm_set_state(lbm_ctx *c, const void *host, size_t bytes)
     return LBM_OK;
 }
 
+// ---- checkpoints: a versioned header, then the native state.
+namespace {
+const char kCkptMagic[8] = {'L', 'B', 'M', 'C', 'K', 'P', 'T', '1'};
+constexpr uint32_t kCkptVersion = 1;
+struct CkptHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    int32_t nx, ny, prec, layout, tau_iters, row_lo, row_hi, ny_glob;
+    int64_t steps;
+    uint64_t seed, state_bytes;
+    lbm_lattice lat;
+};
+
+bool same_lattice(const lbm_lattice &a, const lbm_lattice &b)
+{
+    // every parameter the step uses, compared exactly
+    return a.nx == b.nx && a.ny == b.ny && a.n == b.n && a.nu_ref == b.nu_ref && a.gamma_scale == b.gamma_scale &&
+           a.gamma1 == b.gamma1 && a.gamma2 == b.gamma2 && a.clamp_mode == b.clamp_mode && a.K == b.K &&
+           a.eps == b.eps && a.Feps == b.Feps && a.gbeta == b.gbeta && a.Tm == b.Tm && a.tauT == b.tauT &&
+           a.s_e == b.s_e && a.s_p == b.s_p && a.T_hot == b.T_hot && a.T_cold == b.T_cold && a.L == b.L &&
+           a.tau0 == b.tau0 && a.prec == b.prec;
+}
+}  // namespace
+
+size_t lbm_checkpoint_bytes(const lbm_ctx *c) { return c ? sizeof(CkptHeader) + lbm_state_bytes(c) : 0; }
+
+int lbm_checkpoint_save(lbm_ctx *c, void *host, size_t bytes)
+{
+    if (!c || !host || bytes != lbm_checkpoint_bytes(c)) return LBM_ERR_ARG;
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kCkptMagic, 8);
+    h.version = kCkptVersion;
+    h.header_bytes = (uint32_t)sizeof(CkptHeader);
+    h.nx = c->nx;
+    h.ny = c->ny;
+    h.prec = c->opts.prec;
+    h.layout = c->opts.layout;
+    h.tau_iters = c->opts.tau_iters;
+    h.row_lo = c->row_lo;
+    h.row_hi = c->row_hi;
+    h.ny_glob = c->ny_glob;
+    h.steps = c->steps;
+    h.seed = c->opts.seed;
+    h.state_bytes = lbm_state_bytes(c);
+    h.lat = c->lat;
+    const int rc = lbm_get_state(c, (char *)host + sizeof(CkptHeader), lbm_state_bytes(c));
+    if (rc != LBM_OK) return rc;
+    memcpy(host, &h, sizeof(h));
+    return LBM_OK;
+}
+
+int lbm_checkpoint_load(lbm_ctx *c, const void *host, size_t bytes)
+{
+    if (!c || !host || bytes != lbm_checkpoint_bytes(c)) return LBM_ERR_ARG;
+    CkptHeader h;
+    memcpy(&h, host, sizeof(h));
+    if (memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != kCkptVersion || h.header_bytes != sizeof(CkptHeader) ||
+        h.nx != c->nx || h.ny != c->ny || h.prec != c->opts.prec || h.layout != c->opts.layout ||
+        h.tau_iters != c->opts.tau_iters || h.row_lo != c->row_lo || h.row_hi != c->row_hi ||
+        h.ny_glob != c->ny_glob || h.seed != c->opts.seed || h.state_bytes != lbm_state_bytes(c) ||
+        !same_lattice(h.lat, c->lat) || h.steps < 0)
+        return LBM_ERR_ARG;
+    const int rc = lbm_set_state(c, (const char *)host + sizeof(CkptHeader), lbm_state_bytes(c));
+    if (rc != LBM_OK) return rc;
+    c->steps = h.steps;   // the stochastic rounding's seed sequence resumes where it was
+    return LBM_OK;
+}
+
 int lbm_get_state_f64(lbm_ctx *c, double *f, double *g, double *tau)
 {
     if (!c) return LBM_ERR_ARG;

@@ -107,6 +107,9 @@ SIGNATURES = [
     ("lbm_halo_unpack", ctypes.c_int, [_VP, _VP, _VP]),
     ("lbm_nusselt_sums", ctypes.c_int, [_VP, _D, _D]),
     ("lbm_residual_sums", ctypes.c_int, [_VP, _D]),
+    ("lbm_checkpoint_bytes", ctypes.c_size_t, [_VP]),
+    ("lbm_checkpoint_save", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    ("lbm_checkpoint_load", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     ("lbm_bench_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("lbm_last_cuda_error", ctypes.c_char_p, []),
@@ -270,6 +273,19 @@ def get_state_f64(ctx, nx, ny):
 def set_state_f64(ctx, f=None, g=None, tau=None):
     conv = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (f, g, tau)]
     _check(lib().lbm_set_state_f64(ctx, *[_ptr(a) for a in conv]), "lbm_set_state_f64")
+
+
+def checkpoint_save(ctx) -> bytes:
+    """The run's checkpoint blob (header + native state)."""
+    nb = int(lib().lbm_checkpoint_bytes(ctx))
+    buf = (ctypes.c_char * nb)()
+    _check(lib().lbm_checkpoint_save(ctx, ctypes.cast(buf, _VP), nb), "lbm_checkpoint_save")
+    return bytes(buf)
+
+
+def checkpoint_load(ctx, blob: bytes):
+    buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+    _check(lib().lbm_checkpoint_load(ctx, ctypes.cast(buf, _VP), len(blob)), "lbm_checkpoint_load")
 
 
 def init_slab(nx, ny, y0, y1, n, Da, Ra, Pr, porosity=0.6, **opts):
@@ -464,6 +480,12 @@ class Cavity:
 
     def state_bytes(self):
         return state_bytes(self.ctx)
+
+    def checkpoint(self) -> bytes:
+        return checkpoint_save(self.ctx)
+
+    def restore(self, blob: bytes):
+        checkpoint_load(self.ctx, blob)
 
     def get_state(self, host):
         get_state(self.ctx, host)

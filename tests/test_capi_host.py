@@ -192,3 +192,11 @@ def test_slab_and_batch_calls_validate_arguments_before_the_device():
     assert lib.lbm_batch_set_plan(None, 0, 128, 8) == -1
     assert lib.lbm_batch_get_plan(None, None, None, None) == -1
     assert lib.lbm_batch_set_wait_budget(None, 100) == -1
+
+
+def test_checkpoint_calls_validate_arguments():
+    from paper_2011_15073_gb300 import lbm
+    lib = lbm.lib()
+    assert lib.lbm_checkpoint_bytes(None) == 0
+    assert lib.lbm_checkpoint_save(None, None, 0) == -1
+    assert lib.lbm_checkpoint_load(None, None, 0) == -1
