@@ -110,6 +110,7 @@ SIGNATURES = [
     ("lbm_checkpoint_bytes", ctypes.c_size_t, [_VP]),
     ("lbm_checkpoint_save", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     ("lbm_checkpoint_load", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
+    ("lbm_debug_padding_canary", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ulonglong)]),
     ("lbm_bench_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("lbm_last_cuda_error", ctypes.c_char_p, []),
@@ -327,6 +328,13 @@ def residual_sums(ctx):
     s = np.zeros(7)
     _check(lib().lbm_residual_sums(ctx, _ptr(s)), "lbm_residual_sums")
     return s
+
+
+def debug_padding_canary(ctx) -> int:
+    """Nonzero bytes in the pitch padding of the state planes (lbm_debug.h): 0 unless a kernel wrote outside the rows."""
+    n = ctypes.c_ulonglong()
+    _check(lib().lbm_debug_padding_canary(ctx, ctypes.byref(n)), "lbm_debug_padding_canary")
+    return n.value
 
 
 def bench_fma_peak(kind: str, device: int = -1, reps: int = 20):
