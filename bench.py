@@ -1106,4 +1106,9 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    try:
+        main()
+    finally:
+        _dist = sys.modules.get("torch.distributed")
+        if _dist is not None and _dist.is_available() and _dist.is_initialized():
+            _dist.destroy_process_group()

@@ -39,7 +39,7 @@ def torch_grad(nx, ny, Da, steps, state, clamp_mode):
     f, g, tau = ts.step(f, g, tau, p, steps)
     J = ts.nusselt_hot(g, p)
     J.backward()
-    return float(J), Dt.grad.numpy(), float(n.grad), float(Ra.grad)
+    return float(J.detach()), Dt.grad.numpy(), float(n.grad), float(Ra.grad)
 
 
 @pytest.mark.parametrize("clamp_mode", [1, 0])
