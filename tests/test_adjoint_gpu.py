@@ -136,7 +136,7 @@ def test_autograd_function_carries_the_adjoint(mods):
                     clamp_mode=1) as cav:
         cav.set_darcy_field(Da.detach().numpy())
         J0, dDa, dn, dRa, _ = cav.adjoint_nu(steps, ckpt_every=100, from_rest=True)
-    assert float(J) == J0
+    assert float(J.detach()) == J0
     assert np.array_equal(Da.grad.numpy(), 2.0 * dDa)
     assert float(n.grad) == 2.0 * dn and float(Ra.grad) == 2.0 * dRa
     # direction in log Da
