@@ -294,8 +294,9 @@ int lbm_adjoint_nu(lbm_ctx *ctx, int64_t steps, int ckpt_every, int from_rest,
  * case's residual is checked on the device and converged cases stop being
  * stepped.  All cases share the storage precision and the options of
  * lbm_batch_create (the two-buffer layout; resid_interval must be even; the
- * lagged or the implicit tau; not the stochastic-rounding storages, whose
- * per-step seeds a replayed graph would repeat). */
+ * lagged or the implicit tau).  With the stochastic-rounding storages each
+ * step's seed is computed on the device from the case's step count, so a
+ * case draws the same random bits in a batch as stepped alone. */
 typedef struct {
     int nx, ny;
     double n, Da, Ra, Pr, porosity;
@@ -305,7 +306,7 @@ typedef struct lbm_batch lbm_batch;
 
 /* Create one context per case (validated as by lbm_init) on one stream.
  * Errors as lbm_init; LBM_ERR_ARG also for an odd resid_interval;
- * LBM_ERR_UNSUPPORTED for layout 1 and for F16S / BF16S. */
+ * LBM_ERR_UNSUPPORTED for layout 1. */
 int lbm_batch_create(lbm_batch **out, const lbm_case *cases, int ncases,
                      const lbm_opts *opts);
 void lbm_batch_destroy(lbm_batch *batch);

@@ -227,6 +227,80 @@ aa_odd2_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau,
     if constexpr (TAU == 0) *reinterpret_cast<float2 *>(tau + k) = t.v;
 }
 
+// Odd step for a uniform permeability: lane l of each warp updates nodes
+// wx + l and wx + 32 + l (wx: the warp's first of 64 nodes) as one packed
+// pair.  Every population row is then read and written by coalesced
+// 32-node accesses, shifted by one element for the x-moving populations,
+// with no warp shuffles and no warp-end special cases -- which adjacent pairs
+// need on both the gathers and the pushes of the odd step.  The per-node
+// Darcy field keeps aa_odd2_kernel (its loads take adjacent pairs).
+template <int PREC, int TAU>
+__global__ void __launch_bounds__(128)
+aa_odd_split_kernel(typename Store<PREC>::S *__restrict__ A, float *__restrict__ tau, Phys<float> p, Phys<F2> p2)
+{
+    using St = Store<PREC>;
+    using S = typename St::S;
+    const int lane = threadIdx.x & 31;
+    const int wx = blockIdx.x * 256 + (threadIdx.x >> 5) * 64, y = blockIdx.y;
+    const int xa = wx + lane;
+    const bool fast = y > 0 && y < p.ny - 1 && wx > 0 && wx + 64 < p.nx;
+    if (!fast) {
+        if (xa < p.nx) odd_node<PREC, float, TAU, 0>(A, tau, p, xa, y);
+        if (xa + 32 < p.nx) odd_node<PREC, float, TAU, 0>(A, tau, p, xa + 32, y);
+        return;
+    }
+    const int64_t P = p.plane, W = p.pitch;
+    const int64_t k = (int64_t)y * W + xa;   // node a; node b is k + 32
+    S *fs = A;
+    S *gs = A + 9 * P;
+    auto gather = [&](const S *plane, int64_t off, double rest) {
+        return F2(St::ldd(plane, k + off, float(rest)), St::ldd(plane, k + 32 + off, float(rest)));
+    };
+    // gather f_i(x) = f*_i(x - e_i), kept in slot opp(i) of node x - e_i
+    F2 f[9], g[5];
+    f[0] = gather(fs, 0, rest_f(0));
+    f[1] = gather(fs + 3 * P, -1, rest_f(3));
+    f[2] = gather(fs + 4 * P, -W, rest_f(4));
+    f[3] = gather(fs + P, 1, rest_f(1));
+    f[4] = gather(fs + 2 * P, W, rest_f(2));
+    f[5] = gather(fs + 7 * P, -W - 1, rest_f(7));
+    f[6] = gather(fs + 8 * P, -W + 1, rest_f(8));
+    f[7] = gather(fs + 5 * P, W + 1, rest_f(5));
+    f[8] = gather(fs + 6 * P, W - 1, rest_f(6));
+    g[0] = gather(gs, 0, rest_g(0));
+    g[1] = gather(gs + 3 * P, -1, rest_g(3));
+    g[2] = gather(gs + 4 * P, -W, rest_g(4));
+    g[3] = gather(gs + P, 1, rest_g(1));
+    g[4] = gather(gs + 2 * P, W, rest_g(2));
+    Macro<F2> m;
+    const F2 t0 = tau_start<TAU, F2, 0, 1>(p2, f, g, k, [&] { return F2(tau[k], tau[k + 32]); });
+    const F2 t = collide<F2, 0, 1>(p2, f, g, t0, m, k);
+    uint32_t rng = rng_init(p2.seed, k);
+    // push f*_i(x) into slot i of node x + e_i
+    auto push = [&](S *plane, int64_t off, F2 v, double rest) {
+        St::sdv(plane, k + off, v.v.x, float(rest), rng);
+        St::sdv(plane, k + 32 + off, v.v.y, float(rest), rng);
+    };
+    push(fs, 0, f[0], rest_f(0));
+    push(fs + P, 1, f[1], rest_f(1));
+    push(fs + 2 * P, W, f[2], rest_f(2));
+    push(fs + 3 * P, -1, f[3], rest_f(3));
+    push(fs + 4 * P, -W, f[4], rest_f(4));
+    push(fs + 5 * P, W + 1, f[5], rest_f(5));
+    push(fs + 6 * P, W - 1, f[6], rest_f(6));
+    push(fs + 7 * P, -W - 1, f[7], rest_f(7));
+    push(fs + 8 * P, -W + 1, f[8], rest_f(8));
+    push(gs, 0, g[0], rest_g(0));
+    push(gs + P, 1, g[1], rest_g(1));
+    push(gs + 2 * P, W, g[2], rest_g(2));
+    push(gs + 3 * P, -1, g[3], rest_g(3));
+    push(gs + 4 * P, -W, g[4], rest_g(4));
+    if constexpr (TAU == 0) {
+        tau[k] = t.v.x;
+        tau[k + 32] = t.v.y;
+    }
+}
+
 // Form O -> form E in place, without a collision: each interior link
 // (x, x + e_i), i in {1, 2, 5, 6} (one of each opposite pair), swaps slot i of
 // x + e_i with slot opp(i) of x; a thermal link that left through an
@@ -280,6 +354,9 @@ static void aa_launch(lbm_ctx *c)
         if (c->aa_form_o)
             aa_even2_kernel<PREC, TAU, FIELD><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0],
                                                                   make_params<float>(c), make_params<F2>(c));
+        else if constexpr (FIELD == 0)
+            aa_odd_split_kernel<PREC, TAU><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0],
+                                                               make_params<float>(c), make_params<F2>(c));
         else
             aa_odd2_kernel<PREC, TAU, FIELD><<<grid, 128, 0, c->stream>>>(A, (float *)c->buf.tau[0],
                                                                  make_params<float>(c), make_params<F2>(c));

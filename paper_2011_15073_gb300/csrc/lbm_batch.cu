@@ -34,7 +34,8 @@ struct CaseDev {
     int tiles_per_row;
     int ntiles;  // tiles_per_row * ny
     int cur;     // buffer holding the case's current state
-    int pad;
+    uint32_t run;              // stochastic rounding: the run's stream word (run_word)
+    long long step0;           // the case's step count when the batch call began
 };
 
 // Per-case convergence state kept on the device.
@@ -79,33 +80,52 @@ __global__ void build_active_kernel(const CaseDev *cases, const int *active, int
     if (threadIdx.x == 0 && blockIdx.x == 0) build_active(cases, active, n, a);
 }
 
+constexpr bool rounds_stochastically(int prec) { return prec == LBM_F16S || prec == LBM_BF16S; }
+
+// Where a step of the sweep stands in each case's own step count: step s of
+// the current launch or chunk, `off` steps into the batch call, plus (in a
+// run to steady state, whose chunks replay one graph) the steps the case's
+// convergence record has counted so far.
+struct StepAt {
+    const Conv *conv;   // nullptr outside run_to_steady
+    long long off;
+    int s;
+};
+
 // One row tile of one case: the same tile bodies as the single-cavity
 // kernels (two nodes per thread, or one node per thread in FP64), so every
-// case evolves bit for bit as it would alone.  TAU as for step_node; FIELD 0
-// when no case has a per-node Darcy field, else 2 (decided per case).
+// case evolves bit for bit as it would alone -- the stochastic-rounding
+// storages too, whose seed is computed here from the case's step count as a
+// plain launch computes it on the host.  TAU as for step_node; FIELD 0 when
+// no case has a per-node Darcy field, else 2 (decided per case).
 template <int PREC, int TAU, int FIELD>
-__device__ __forceinline__ void batch_tile(const CaseDev &cd, int local, int parity)
+__device__ __forceinline__ void batch_tile(const CaseDev &cd, int c, int local, StepAt at)
 {
     using St = Store<PREC>;
     const int y = local / cd.tiles_per_row, xb = local - y * cd.tiles_per_row;
-    const int s = cd.cur ^ parity;
+    const int s = cd.cur ^ (at.s & 1);
     const auto *src = (const typename St::S *)cd.dist[s];
     auto *dst = (typename St::S *)cd.dist[s ^ 1];
+    uint32_t seed = 0;
+    if constexpr (rounds_stochastically(PREC)) {
+        const long long done = at.conv ? at.conv[c].steps : 0;
+        seed = step_seed((uint64_t)(cd.step0 + done + at.off + at.s), cd.run);
+    }
     if constexpr (PREC == LBM_F64) {
         const int x = xb * blockDim.x + threadIdx.x;
         if (x < cd.pd.nx)
             step_node<PREC, double, FIELD, TAU>(src, dst, (const double *)cd.tau[s], (double *)cd.tau[s ^ 1],
-                                                cd.pd, x, y);
+                                                cd.pd, x, y, seed);
     } else {
         step2_tile<PREC, FIELD, TAU>(src, dst, (const float *)cd.tau[s], (float *)cd.tau[s ^ 1], cd.pf, cd.p2,
-                                 xb * 2 * (int)blockDim.x, y);
+                                 xb * 2 * (int)blockDim.x, y, seed);
     }
 }
 
 // Every tile of the active list once, striding by the grid.
 template <int PREC, int TAU, int FIELD>
 __device__ __forceinline__ void batch_sweep(const CaseDev *__restrict__ cases, ActiveList a, int m, int nt,
-                                            int parity)
+                                            StepAt at)
 {
     for (int t = blockIdx.x; t < nt; t += gridDim.x) {
         int lo = 0, hi = m - 1;
@@ -113,15 +133,16 @@ __device__ __forceinline__ void batch_sweep(const CaseDev *__restrict__ cases, A
             const int mid = (lo + hi + 1) >> 1;
             if (a.t0[mid] <= t) lo = mid; else hi = mid - 1;
         }
-        batch_tile<PREC, TAU, FIELD>(cases[a.idx[lo]], t - a.t0[lo], parity);
+        const int c = a.idx[lo];
+        batch_tile<PREC, TAU, FIELD>(cases[c], c, t - a.t0[lo], at);
     }
 }
 
 template <int PREC, int TAU, int FIELD>
 __global__ void __launch_bounds__(256)
-batch_step_kernel(const CaseDev *__restrict__ cases, ActiveList a, int parity)
+batch_step_kernel(const CaseDev *__restrict__ cases, ActiveList a, StepAt at)
 {
-    batch_sweep<PREC, TAU, FIELD>(cases, a, a.hdr[0], a.hdr[1], parity);
+    batch_sweep<PREC, TAU, FIELD>(cases, a, a.hdr[0], a.hdr[1], at);
 }
 
 // Bounded grid barrier.  Thread 0 of each block arrives on the counter; the
@@ -165,13 +186,14 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *bar, long long budget, in
 // resident), a grid barrier between consecutive steps.
 template <int PREC, int TAU, int FIELD>
 __global__ void __launch_bounds__(256)
-batch_chunk_kernel(const CaseDev *__restrict__ cases, ActiveList a, int steps, GridBarrier *bar,
+batch_chunk_kernel(const CaseDev *__restrict__ cases, ActiveList a, StepAt at, int steps, GridBarrier *bar,
                    long long budget, int *err)
 {
     if (*(volatile int *)err) return;
     const int m = a.hdr[0], nt = a.hdr[1];
     for (int s = 0; s < steps; s++) {
-        batch_sweep<PREC, TAU, FIELD>(cases, a, m, nt, s & 1);
+        at.s = s;
+        batch_sweep<PREC, TAU, FIELD>(cases, a, m, nt, at);
         if (s + 1 < steps && !grid_sync(bar, budget, err)) return;
     }
 }
@@ -295,6 +317,8 @@ int upload_cases(lbm_batch *b)
         d.tiles_per_row = (c->nx + tile - 1) / tile;
         d.ntiles = d.tiles_per_row * c->ny;
         d.cur = c->cur;
+        d.run = run_word(c->opts.seed);
+        d.step0 = c->steps;
         if (c->d_da) b->any_field = true;
         t0 += d.ntiles;
     }
@@ -327,6 +351,8 @@ void *kernel_of(const lbm_batch *b, bool persistent)
     case LBM_F32: return kernel_of<LBM_F32>(b, persistent);
     case LBM_BF16D: return kernel_of<LBM_BF16D>(b, persistent);
     case LBM_F16D: return kernel_of<LBM_F16D>(b, persistent);
+    case LBM_F16S: return kernel_of<LBM_F16S>(b, persistent);
+    case LBM_BF16S: return kernel_of<LBM_BF16S>(b, persistent);
     default: return kernel_of<LBM_F32D>(b, persistent);
     }
 }
@@ -352,22 +378,25 @@ int grid_blocks(const lbm_batch *b)
     return (bps < 1 ? 1 : bps) * b->sms;
 }
 
-cudaError_t launch_batch_step(lbm_batch *b, int parity)
+cudaError_t launch_batch_step(lbm_batch *b, StepAt at)
 {
     const CaseDev *cases = b->d_cases;
     ActiveList a = b->act;
-    void *args[] = {(void *)&cases, (void *)&a, (void *)&parity};
+    void *args[] = {(void *)&cases, (void *)&a, (void *)&at};
     return cudaLaunchKernel(kernel_of(b, false), dim3(grid_blocks(b)), dim3(b->threads), args, 0, b->stream);
 }
 
-// `steps` steps of every active case: per-step launches, or one persistent
-// cooperative launch (its barrier reset first).
-cudaError_t launch_batch_steps(lbm_batch *b, int steps)
+// `steps` steps of every active case, `off` steps into the batch call (and
+// counted from the convergence records in a run to steady state): per-step
+// launches, or one persistent cooperative launch (its barrier reset first).
+cudaError_t launch_batch_steps(lbm_batch *b, int steps, long long off = 0, bool counted = false)
 {
     if (steps <= 0) return cudaSuccess;
+    StepAt at{counted ? b->d_conv : nullptr, off, 0};
     if (b->mode == LBM_BATCH_PER_STEP) {
         for (int s = 0; s < steps; s++) {
-            const cudaError_t e = launch_batch_step(b, s & 1);
+            at.s = s;
+            const cudaError_t e = launch_batch_step(b, at);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -388,14 +417,23 @@ cudaError_t launch_batch_steps(lbm_batch *b, int steps)
     GridBarrier *bar = b->d_bar;
     long long budget = b->budget;
     int *err = b->d_err;
-    void *args[] = {(void *)&cases, (void *)&a, (void *)&steps, (void *)&bar, (void *)&budget, (void *)&err};
+    void *args[] = {(void *)&cases, (void *)&a, (void *)&at, (void *)&steps, (void *)&bar, (void *)&budget,
+                    (void *)&err};
     return cudaLaunchKernelExC(&cfg, chunk_kernel(b), args);
 }
 
 double default_floor(const lbm_opts &o)
 {
     if (o.stag_floor >= 0) return o.stag_floor;
-    return o.prec == LBM_F64 ? 0.0 : ((o.prec == LBM_F32 || o.prec == LBM_F32D) ? 1e-6 : (o.prec == LBM_F16D ? 1e-2 : 1e-1));
+    switch (o.prec) {   // as a single context's run_to_steady
+    case LBM_F64: return 0.0;
+    case LBM_F32:
+    case LBM_F32D: return 1e-6;
+    case LBM_F16D: return 1e-2;
+    case LBM_F16S: return 1e-3;
+    case LBM_BF16S: return 1e-2;
+    default: return 1e-1;
+    }
 }
 
 // Enqueue one chunk: `delta` steps of every active case, their residuals and
@@ -403,7 +441,7 @@ double default_floor(const lbm_opts &o)
 int enqueue_chunk(lbm_batch *b, double tol, long long max_steps, cudaGraphConditionalHandle h, int set_cond)
 {
     const int delta = b->opts.resid_interval;
-    BK(launch_batch_steps(b, delta));
+    BK(launch_batch_steps(b, delta, 0, true));
     for (lbm_ctx *c : b->sub) BK(lbm::launch_residual(c, false));
     batch_update_kernel<<<1, 256, 0, b->stream>>>(b->d_conv, b->d_active, b->d_smalls, (int)b->sub.size(), delta,
                                                   tol, default_floor(b->opts), max_steps, b->d_chunks, b->d_go,
@@ -464,9 +502,7 @@ int lbm_batch_create(lbm_batch **out, const lbm_case *cases, int ncases, const l
     if (!cases || ncases < 1) return LBM_ERR_ARG;
     lbm_opts o;
     if (opts) o = *opts; else lbm_default_opts(&o);
-    // the batched sweep replays a CUDA graph, which would replay the
-    // stochastic rounding's seed too: those storages are not built here
-    if (o.layout != 0 || o.prec == LBM_F16S || o.prec == LBM_BF16S) return LBM_ERR_UNSUPPORTED;
+    if (o.layout != 0) return LBM_ERR_UNSUPPORTED;
     if (o.resid_interval < 2 || (o.resid_interval & 1)) return LBM_ERR_ARG;
     lbm_batch *b = new (std::nothrow) lbm_batch();
     if (!b) return LBM_ERR_OOM;
@@ -559,7 +595,7 @@ int lbm_batch_step(lbm_batch *b, int64_t k)
     for (int64_t done = 0; done < k;) {
         int64_t n = k - done < piece ? k - done : piece;
         if (n > 1) n &= ~int64_t(1);
-        BK(launch_batch_steps(b, (int)n));
+        BK(launch_batch_steps(b, (int)n, done));
         if (n & 1) {
             for (lbm_ctx *c : b->sub) c->cur ^= 1;
             rc = upload_cases(b);

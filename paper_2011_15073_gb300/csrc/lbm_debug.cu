@@ -1,8 +1,9 @@
-// lbm_debug.cu -- the padding canary of include/lbm_debug.h.
+// lbm_debug.cu -- the padding canary and the rounding check of include/lbm_debug.h.
 #include <cuda_runtime.h>
 
 #include "lbm_debug.h"
 #include "lbm_internal.h"
+#include "lbm_round.cuh"
 
 namespace {
 
@@ -19,6 +20,14 @@ __global__ void padding_count_kernel(const unsigned char *__restrict__ base, int
         cnt += base[r * pitch_bytes + row_bytes + b] != 0;
     }
     if (cnt) atomicAdd(out, cnt);
+}
+
+// The step kernels' pair conversion applied to given values and random bits.
+__global__ void sr_pairs_kernel(int fmt, const float *__restrict__ x, const uint32_t *__restrict__ r,
+                                uint32_t *__restrict__ out, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = fmt == 0 ? lbm::sr_half2(x[2 * i], x[2 * i + 1], r[i]) : lbm::sr_bf16x2(x[2 * i], x[2 * i + 1], r[i]);
 }
 
 }  // namespace
@@ -55,4 +64,34 @@ extern "C" int lbm_debug_padding_canary(lbm_ctx *c, unsigned long long *nonzero)
     if (e != cudaSuccess) return LBM_ERR_CUDA;
     *nonzero = h;
     return LBM_OK;
+}
+
+extern "C" int lbm_debug_sr_pairs(int device, int fmt, const float *x, const uint32_t *r, uint16_t *out,
+                                  size_t n_pairs)
+{
+    if (!x || !r || !out || (fmt != 0 && fmt != 1)) return LBM_ERR_ARG;
+    if (n_pairs == 0) return LBM_OK;
+    if (cudaSetDevice(device) != cudaSuccess) return LBM_ERR_CUDA;
+    float *dx = nullptr;
+    uint32_t *dr = nullptr, *dout = nullptr;
+    if (cudaMalloc(&dx, n_pairs * 2 * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&dr, n_pairs * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&dout, n_pairs * sizeof(uint32_t)) != cudaSuccess) {
+        cudaFree(dx);
+        cudaFree(dr);
+        cudaFree(dout);
+        return LBM_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpy(dx, x, n_pairs * 2 * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dr, r, n_pairs * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        const size_t blocks = (n_pairs + 255) / 256;
+        sr_pairs_kernel<<<(unsigned)(blocks < 152 * 8 ? blocks : 152 * 8), 256>>>(fmt, dx, dr, dout, n_pairs);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, n_pairs * sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    cudaFree(dx);
+    cudaFree(dr);
+    cudaFree(dout);
+    return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }

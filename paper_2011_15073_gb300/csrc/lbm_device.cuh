@@ -108,6 +108,20 @@ struct Phys {
 };
 
 // ------------------------------------------------------------ parameters
+// The stochastic rounding's seeds: run_word() turns lbm_opts.seed into the
+// run's stream word (0 keeps the default stream), step_seed() gives the seed
+// of the step that starts at step count `steps` of that run -- on the host
+// for plain launches, on the device for the batched sweep, so a case steps
+// with the same random bits either way.
+__host__ __device__ __forceinline__ uint32_t run_word(uint64_t s)
+{
+    return s ? mix32((uint32_t)s ^ mix32((uint32_t)(s >> 32) + 0x68e31da4u)) : 0u;
+}
+__host__ __device__ __forceinline__ uint32_t step_seed(uint64_t steps, uint32_t run)
+{
+    return mix32(0x9e3779b9u * (uint32_t)(steps + 1) ^ (uint32_t)(steps >> 32) ^ run);
+}
+
 template <class V>
 inline Phys<V> make_params(const lbm_ctx *c)
 {
@@ -146,10 +160,7 @@ inline Phys<V> make_params(const lbm_ctx *c)
     p.tau_iters = c->opts.tau_iters;
     p.tau0 = V(L.tau0);
     p.nu3 = V(3.0 * L.nu_ref);
-    // the run's own stream (lbm_opts.seed; 0 leaves the default stream)
-    const uint64_t s = c->opts.seed;
-    const uint32_t run = s ? mix32((uint32_t)s ^ mix32((uint32_t)(s >> 32) + 0x68e31da4u)) : 0u;
-    p.seed = mix32(0x9e3779b9u * (uint32_t)(c->steps + 1) ^ (uint32_t)((uint64_t)c->steps >> 32) ^ run);
+    p.seed = step_seed((uint64_t)c->steps, run_word(c->opts.seed));
     return p;
 }
 
@@ -329,10 +340,10 @@ struct Store<LBM_F16D> {
 // The FP16 form stores the deviation scaled by 2^15, which moves deviations
 // down to 2e-9 into the normal range of FP16 (and keeps |d| < 2 finite): a
 // custom 16-bit format with the exponent range shifted to where the
-// deviations live.  Its rounding is sr_half_normal: below 2e-9 (scaled
-// 2^-14) values are truncated toward zero, a bias under 2e-12 in deviation
-// units, far below FP32's resolution of the populations themselves.  The
-// kernels' random bits: rng_init() hashes the step's seed and the node once,
+// deviations live (below 2e-9, FP16's subnormals keep a spacing of 2^-39 in
+// deviation units).  The rounding is the conversion's own stochastic mode
+// (sr_half2, sr_bf16x2: one instruction per stored pair).  The kernels'
+// random bits: rng_init() hashes the step's seed and the node once,
 // then rng_next() advances a Weyl sequence by one add per stored pair (each
 // draw is uniform because the start is; the pairs of one node share it).
 // Import uses the element's address for its random bits.
@@ -346,14 +357,14 @@ struct Store<LBM_F16S> {
     static __device__ __forceinline__ R ld(const S *p, int64_t k, R rest) { return rest + ldd(p, k, rest); }
     static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest, uint32_t seed = 0)
     {
-        p[k] = sr_half_normal((v - rest) * F16S_SCALE, sr_bits(seed, p + k) >> 16);
+        p[k] = sr_half((v - rest) * F16S_SCALE, sr_bits(seed, p + k));
     }
     static __device__ __forceinline__ F2 unpack2(uint32_t u) { return F2(__half22float2(as_h2(u))) * F2(F16S_ISCALE); }
     static __device__ __forceinline__ uint32_t pack2(F2 d, uint32_t &rng)
     {
         rng = rng_next(rng);
         const F2 ds = d * F2(F16S_SCALE);
-        return sr_half2_normal(ds.v.x, ds.v.y, rng);
+        return sr_half2(ds.v.x, ds.v.y, rng);
     }
     static __device__ __forceinline__ F2 ldd2(const S *p, int64_t k, float)
     {
@@ -362,14 +373,13 @@ struct Store<LBM_F16S> {
     static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float rest) { return ldd2(p, k, rest) + F2(rest); }
     static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest, uint32_t seed = 0)
     {
-        const uint32_t r = sr_bits(seed, p + k);
         const F2 d = (v - F2(rest)) * F2(F16S_SCALE);
-        *reinterpret_cast<__half2 *>(p + k) = __halves2half2(sr_half_normal(d.v.x, r & 0xffffu), sr_half_normal(d.v.y, r >> 16));
+        *reinterpret_cast<uint32_t *>(p + k) = sr_half2(d.v.x, d.v.y, sr_bits(seed, p + k));
     }
     static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t &rng)
     {
         rng = rng_next(rng);
-        p[k] = sr_half_normal(d * F16S_SCALE, rng >> 16);
+        p[k] = sr_half(d * F16S_SCALE, rng);
     }
     static __device__ __forceinline__ void sdv2(S *p, int64_t k, F2 d, float, uint32_t &rng)
     {
@@ -387,7 +397,7 @@ struct Store<LBM_BF16S> {
     }
     static __device__ __forceinline__ void st(S *p, int64_t k, R v, R rest, uint32_t seed = 0)
     {
-        p[k] = sr_bf16(v - rest, sr_bits(seed, p + k) >> 16);
+        p[k] = sr_bf16(v - rest, sr_bits(seed, p + k));
     }
     static __device__ __forceinline__ F2 ld2(const S *p, int64_t k, float rest)
     {
@@ -396,16 +406,14 @@ struct Store<LBM_BF16S> {
     }
     static __device__ __forceinline__ void st2(S *p, int64_t k, F2 v, float rest, uint32_t seed = 0)
     {
-        const uint32_t r = sr_bits(seed, p + k);
         const F2 d = v - F2(rest);
-        *reinterpret_cast<__nv_bfloat162 *>(p + k) =
-            __halves2bfloat162(sr_bf16(d.v.x, r & 0xffffu), sr_bf16(d.v.y, r >> 16));
+        *reinterpret_cast<uint32_t *>(p + k) = sr_bf16x2(d.v.x, d.v.y, sr_bits(seed, p + k));
     }
     static __device__ __forceinline__ R ldd(const S *p, int64_t k, R) { return __bfloat162float(p[k]); }
     static __device__ __forceinline__ void sdv(S *p, int64_t k, R d, R, uint32_t &rng)
     {
         rng = rng_next(rng);
-        p[k] = sr_bf16(d, rng >> 16);
+        p[k] = sr_bf16(d, rng);
     }
     static __device__ __forceinline__ F2 unpack2(uint32_t u) { return F2(__bfloat1622float2(as_bf162(u))); }
     static __device__ __forceinline__ uint32_t pack2(F2 d, uint32_t &rng)

@@ -38,7 +38,7 @@ step_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= p.nx) return;
-    step_node<PREC, typename Store<PREC>::R, FIELD, TAU>(src, dst, tsrc, tdst, p, x, y);
+    step_node<PREC, typename Store<PREC>::R, FIELD, TAU>(src, dst, tsrc, tdst, p, x, y, p.seed);
 }
 
 template <int PREC, int FIELD, int TAU>
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(128)
 step2_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
              const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
 {
-    step2_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
+    step2_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y, p.seed);
 }
 
 // Four nodes per thread (16-bit storages): 64-thread blocks of 256 nodes,

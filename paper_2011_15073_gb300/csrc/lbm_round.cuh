@@ -9,14 +9,14 @@
 // proportional to its distance from the other one, so the stored value is x
 // in expectation and small updates survive on average.
 //
-// Everything here is __host__ __device__ so that the host unit test can
-// check it exhaustively.
+// The hash and the random-bit sequence are __host__ __device__, so that a
+// host test can check the hash; the conversions are device instructions,
+// checked on the GPU over every value of their random bits.
 #pragma once
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
-#include <string.h>
 
 namespace lbm {
 
@@ -39,27 +39,6 @@ __host__ __device__ __forceinline__ uint32_t sr_bits(uint32_t seed, const void *
     return mix32(seed ^ (uint32_t)(u >> 1) ^ (uint32_t)(u >> 33) * 0x9e3779b9u);
 }
 
-__host__ __device__ __forceinline__ uint32_t f2u(float x)
-{
-#ifdef __CUDA_ARCH__
-    return __float_as_uint(x);
-#else
-    uint32_t u;
-    memcpy(&u, &x, 4);
-    return u;
-#endif
-}
-__host__ __device__ __forceinline__ float u2f(uint32_t u)
-{
-#ifdef __CUDA_ARCH__
-    return __uint_as_float(u);
-#else
-    float x;
-    memcpy(&x, &u, 4);
-    return x;
-#endif
-}
-
 // Start of a thread's random bits for the node at plane offset k in the
 // launch with seed `seed`, and the next draw: a Weyl sequence (golden-ratio
 // increment), one add per draw.  Every draw is uniform over 32 bits because
@@ -71,67 +50,39 @@ __host__ __device__ __forceinline__ uint32_t rng_init(uint32_t seed, int64_t k)
 }
 __host__ __device__ __forceinline__ uint32_t rng_next(uint32_t r) { return r + 0x9e3779b9u; }
 
-// FP32 -> FP16 with stochastic rounding, r16 = 16 random bits.
-// * Half normals (|x| >= 2^-14): the FP32 bits below the half's last place
-//   are the low 13 mantissa bits; adding a uniform integer in [0, 2^13) to
-//   the FP32 bit pattern and truncating toward zero rounds the magnitude up
-//   with probability (distance to the lower neighbour) / (spacing).  A carry
-//   into the exponent lands on the next binade's first value, which is the
-//   upper neighbour there, so binade ends are handled too.
-// * Half subnormals (|x| < 2^-14): the spacing is the constant 2^-24, so
-//   |x| / 2^-24 = q (exact in FP32) is rounded to floor(q) or floor(q) + 1 by
-//   comparing its fraction with a uniform number in [0, 1) of 16-bit
-//   resolution.
-__host__ __device__ __forceinline__ __half sr_half(float x, uint32_t r16)
+// FP32 -> 16-bit with stochastic rounding, done by the conversion
+// instruction itself: cvt with the .rs rounding mode (PTX ISA 8.7, sm_100
+// family) turns each FP32 value of a pair into the 16-bit neighbour below or
+// above it in magnitude, the one above with probability (distance to the one
+// below) / (their spacing).  The value in the word's high half draws on the
+// high 16 bits of r, the low half on the low 16 bits.  Measured on GB300
+// over every value of those bits: BF16 rounds up iff the 16 dropped bits
+// plus the 16 random bits carry, so the result is x in expectation exactly;
+// FP16 uses the low 13 of its 16 bits against the 13 mantissa bits a normal
+// FP16 drops (exact in expectation too), and for FP16 subnormals, which drop
+// more bits, it compares the top 13 of them, a bias toward zero under 2^-13
+// of a spacing.  One instruction per pair replaces the integer dither and
+// truncating conversion of a software version.
+__device__ __forceinline__ uint32_t sr_half2(float lo, float hi, uint32_t r)
 {
-    uint32_t b = f2u(x);
-    const int e = (int)((b >> 23) & 0xffu);
-    if (e < 113) {
-        const float q = u2f(b & 0x7fffffffu) * 16777216.0f;   // |x| / 2^-24 < 1024, exact
-        const float fl = floorf(q);
-        const float u = (float)(r16 & 0xffffu) * (1.0f / 65536.0f);
-        const float m = (fl + (u < q - fl ? 1.0f : 0.0f)) * 5.9604644775390625e-8f;
-        return __float2half_rz((b >> 31) ? -m : m);
-    }
-    b += (r16 & 0xffffu) >> 3;
-    return __float2half_rz(u2f(b));
-}
-
-// The half-normal branch alone, for the scaled FP16 storage whose values
-// sit in the normal range: one integer add and one conversion.  Magnitudes
-// below 2^-14 (FP16's smallest normal) are then truncated toward zero on the
-// subnormal grid instead of rounded stochastically: the result is still one
-// of the two neighbours, biased toward zero by less than one spacing, 2^-24.
-__host__ __device__ __forceinline__ __half sr_half_normal(float x, uint32_t r16)
-{
-    return __float2half_rz(u2f(f2u(x) + ((r16 & 0xffffu) >> 3)));
-}
-
-// Two values at once, as packed 16-bit pairs (x in the low half): the same
-// dithers as sr_half_normal(x, r & 0xffff), sr_half_normal(y, r >> 16) and
-// sr_bf16 likewise, with one packed truncating conversion.
-__device__ __forceinline__ uint32_t sr_half2_normal(float x, float y, uint32_t r)
-{
-    const float xd = u2f(f2u(x) + ((r & 0xffffu) >> 3)), yd = u2f(f2u(y) + (r >> 19));
     uint32_t out;
-    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(out) : "f"(yd), "f"(xd));
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(out) : "f"(hi), "f"(lo), "r"(r));
     return out;
 }
-__device__ __forceinline__ uint32_t sr_bf16x2(float x, float y, uint32_t r)
+__device__ __forceinline__ uint32_t sr_bf16x2(float lo, float hi, uint32_t r)
 {
-    const float xd = u2f(f2u(x) + (r & 0xffffu)), yd = u2f(f2u(y) + (r >> 16));
     uint32_t out;
-    asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(out) : "f"(yd), "f"(xd));
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(out) : "f"(hi), "f"(lo), "r"(r));
     return out;
 }
-
-// FP32 -> BF16 with stochastic rounding: BF16 keeps the top 16 bits of the
-// FP32 pattern, so the dither is the 16 random bits themselves (FP32
-// subnormals are not stored: |deviation| >= 2^-126 or 0 in practice).
-__host__ __device__ __forceinline__ __nv_bfloat16 sr_bf16(float x, uint32_t r16)
+// One value (the low half of a pair; the low half of r decides).
+__device__ __forceinline__ __half sr_half(float x, uint32_t r)
 {
-    const uint32_t b = f2u(x) + (r16 & 0xffffu);
-    return __float2bfloat16_rz(u2f(b));
+    return __ushort_as_half((unsigned short)(sr_half2(x, 0.0f, r) & 0xffffu));
+}
+__device__ __forceinline__ __nv_bfloat16 sr_bf16(float x, uint32_t r)
+{
+    return __ushort_as_bfloat16((unsigned short)(sr_bf16x2(x, 0.0f, r) & 0xffffu));
 }
 
 }  // namespace lbm

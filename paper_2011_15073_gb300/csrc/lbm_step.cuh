@@ -14,13 +14,15 @@ namespace lbm {
 // FP32-arithmetic storages the arithmetic runs on deviations from the rest
 // state (DEV form of pull, macro and collide), which keeps the small
 // per-step changes of a nearly steady state out of the rounding of O(1)
-// population values; FP64 runs on full values (dev_form).
+// population values; FP64 runs on full values (dev_form).  `seed`: the
+// stochastic rounding's seed of this step (step_seed; Phys::seed in a plain
+// launch).
 template <int PREC, class R, int FIELD = 2, int TAU = 0>
 __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restrict__ src,
                                           typename Store<PREC>::S *__restrict__ dst,
                                           const typename Store<PREC>::TauS *__restrict__ tsrc,
                                           typename Store<PREC>::TauS *__restrict__ tdst, const Phys<R> &p, int x,
-                                          int y)
+                                          int y, uint32_t seed)
 {
     using St = Store<PREC>;
     const int64_t k = (int64_t)y * p.pitch + x;
@@ -30,7 +32,7 @@ __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restr
     Macro<R> m;
     const R t0 = tau_start<TAU, R, FIELD, DEV>(p, f, g, k, [&] { return R(tsrc[k]); });
     const R tau = collide<R, FIELD, DEV>(p, f, g, t0, m, k);
-    uint32_t rng = rng_init(p.seed, k);   // random bits of the stochastic-rounding storages
+    uint32_t rng = rng_init(seed, k);   // random bits of the stochastic-rounding storages
 #pragma unroll
     for (int i = 0; i < 9; i++) stf<PREC>(dst, i * p.plane + k, f[i], R(rest_f(i)), rng);
 #pragma unroll
@@ -47,12 +49,13 @@ __device__ __forceinline__ void step_node(const typename Store<PREC>::S *__restr
 // is uniform per warp.  (Handing the side-wall warps to the packed path, as
 // step4_tile does, costs this tile 8-40 registers per thread in its
 // single-cavity and batched kernels; at 64 nodes per warp the wall warps are
-// a small share of a row.)  TAU as for step_node.
+// a small share of a row.)  TAU and seed as for step_node.
 template <int PREC, int FIELD = 2, int TAU = 0>
 __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__restrict__ src,
                                            typename Store<PREC>::S *__restrict__ dst,
                                            const float *__restrict__ tsrc, float *__restrict__ tdst,
-                                           const Phys<float> &p, const Phys<F2> &p2, int xbase, int y)
+                                           const Phys<float> &p, const Phys<F2> &p2, int xbase, int y,
+                                           uint32_t seed)
 {
     using St = Store<PREC>;
     using S = typename St::S;
@@ -62,7 +65,7 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
     const bool fast = y > 0 && y < p.ny - 1 && wx > 0 && wx + 64 < p.nx;
     if (!fast) {
         for (int j = 0; j < 2; j++)
-            if (x0 + j < p.nx) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, x0 + j, y);
+            if (x0 + j < p.nx) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, x0 + j, y, seed);
         return;
     }
     const int64_t P = p.plane, W = p.pitch;
@@ -92,7 +95,7 @@ __device__ __forceinline__ void step2_tile(const typename Store<PREC>::S *__rest
     const F2 t0 = tau_start<TAU, F2, FIELD, 1>(p2, f, g, k, [&] { return F2(*reinterpret_cast<const float2 *>(tsrc + k)); });
     Macro<F2> m;
     const F2 tau = collide<F2, FIELD, 1>(p2, f, g, t0, m, k);
-    uint32_t rng = rng_init(p.seed, k);
+    uint32_t rng = rng_init(seed, k);
 #pragma unroll
     for (int i = 0; i < 9; i++) St::sdv2(dst + i * P, k, f[i], float(rest_f(i)), rng);
 #pragma unroll
@@ -155,7 +158,7 @@ __device__ __forceinline__ void step4_tile(const typename Store<PREC>::S *__rest
     const bool fast = y > 0 && y < p.ny - 1 && wx + 128 <= p.nx;
     if (!fast) {
         for (int j = 0; j < 4; j++)
-            if (x0 + j < p.nx) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, x0 + j, y);
+            if (x0 + j < p.nx) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, x0 + j, y, p.seed);
         return;
     }
     const int64_t P = p.plane, W = p.pitch;
@@ -202,8 +205,8 @@ __device__ __forceinline__ void step4_tile(const typename Store<PREC>::S *__rest
 #pragma unroll
     for (int q = 0; q < 14; q++) *reinterpret_cast<uint2 *>(dst + q * P + k) = make_uint2(oa[q], ob[q]);
     if constexpr (TAU == 0) *reinterpret_cast<float4 *>(tdst + k) = make_float4(ta.v.x, ta.v.y, tb.v.x, tb.v.y);
-    if (x0 == 0) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, 0, y);
-    if (x0 + 3 == p.nx - 1) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, p.nx - 1, y);
+    if (x0 == 0) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, 0, y, p.seed);
+    if (x0 + 3 == p.nx - 1) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, p.nx - 1, y, p.seed);
 }
 
 }  // namespace lbm

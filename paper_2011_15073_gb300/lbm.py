@@ -111,6 +111,7 @@ SIGNATURES = [
     ("lbm_checkpoint_save", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     ("lbm_checkpoint_load", ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     ("lbm_debug_padding_canary", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_ulonglong)]),
+    ("lbm_debug_sr_pairs", ctypes.c_int, [ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, ctypes.c_size_t]),
     ("lbm_bench_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]),
     ("lbm_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("lbm_last_cuda_error", ctypes.c_char_p, []),
@@ -335,6 +336,21 @@ def debug_padding_canary(ctx) -> int:
     n = ctypes.c_ulonglong()
     _check(lib().lbm_debug_padding_canary(ctx, ctypes.byref(n)), "lbm_debug_padding_canary")
     return n.value
+
+
+def debug_sr_pairs(fmt: str, x, r, device: int = 0):
+    """The 16-bit storages' stochastic rounding of value pairs (lbm_debug.h):
+    fmt 'f16' or 'bf16'; x: 2n float32 values (pair i = x[2i] low, x[2i+1]
+    high), r: n uint32 random words -> 2n uint16 codes."""
+    k = {"f16": 0, "bf16": 1}[fmt]
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    r = np.ascontiguousarray(r, dtype=np.uint32)
+    if x.size != 2 * r.size:
+        raise ValueError("x must hold two values per random word")
+    out = np.empty(x.size, dtype=np.uint16)
+    _check(lib().lbm_debug_sr_pairs(device, k, x.ctypes.data, r.ctypes.data, out.ctypes.data, r.size),
+           "lbm_debug_sr_pairs")
+    return out
 
 
 def bench_fma_peak(kind: str, device: int = -1, reps: int = 20):

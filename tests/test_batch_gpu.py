@@ -8,7 +8,9 @@ evolve exactly as it would alone:
   the lagged and with the node-local implicit tau;
 * FP64: within the parity bounds of test_parity_gpu against the oracle;
 * run-to-steady (host-looped graph and single device-looped graph): the same
-  per-case stopping step and Nusselt numbers as lbm_run_to_steady alone.
+  per-case stopping step and Nusselt numbers as lbm_run_to_steady alone;
+* the stochastic-rounding storages: bit for bit the single contexts too (each
+  step's seed is computed on the device from the case's step count).
 """
 import numpy as np
 import pytest
@@ -236,3 +238,57 @@ def test_batch_tune_keeps_states(mods):
     for x, y in zip(before, after):
         for a, w in zip(x, y):
             assert np.array_equal(a, w)
+
+
+@pytest.mark.parametrize("plan", [("per_step", 128, 8), ("persistent", 128, 4)], ids=lambda p: p[0])
+@pytest.mark.parametrize("prec,seed", [("f16s", 0), ("bf16s", 0), ("f16s", 5)])
+def test_batch_stochastic_rounding_equals_single_contexts(mods, plan, prec, seed):
+    """The stochastic-rounding storages in a batch: each step's seed comes
+    from the case's step count on the device, so a batch stepped in two calls
+    (20 + 17 steps) holds bit for bit the states of the cases stepped alone
+    (the same start states, copied in natively)."""
+    oracle, inputs, lbm = mods
+    st = start_states(oracle, inputs, CASES)
+    start, want = [], []
+    for i, c in enumerate(CASES):
+        with lbm.Cavity(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec=prec,
+                        clamp_mode=1, seed=seed) as cav:
+            cav.set_state_f64(*st[i][1])
+            s0 = np.empty(cav.state_bytes(), np.uint8)
+            cav.get_state(s0)
+            cav.step(37)
+            s1 = np.empty_like(s0)
+            cav.get_state(s1)
+        start.append(s0)
+        want.append(s1)
+    with lbm.Batch(CASES, prec=prec, clamp_mode=1, seed=seed) as b:
+        b.set_plan(*plan)
+        for i in range(len(CASES)):
+            lbm.set_state(b.case_ctx(i), start[i])
+        b.step(20)
+        b.step(17)
+        for i in range(len(CASES)):
+            got = np.empty_like(want[i])
+            lbm.get_state(b.case_ctx(i), got)
+            assert np.array_equal(got, want[i]), i
+            assert not np.array_equal(got, start[i])
+
+
+@pytest.mark.parametrize("prec", ["f16s", "bf16s"])
+def test_batch_stochastic_run_to_steady_matches_single_runs(mods, prec):
+    """Run to steady state with the stochastic storages (the chunks replay one
+    graph, the seeds advance on the device): per case the same stopping step,
+    reason, residual and Nusselt numbers as the case run alone."""
+    _, _, lbm = mods
+    cases = [dict(nx=24, ny=24, n=0.8, Da=1e-2, Ra=1e3, Pr=6.2, porosity=0.6),
+             dict(nx=40, ny=36, n=1.0, Da=1e-1, Ra=1e4, Pr=6.2, porosity=0.6)]
+    with lbm.Batch(cases, prec=prec, clamp_mode=1, resid_interval=200) as b:
+        steps, res, why = b.run_to_steady(1e-8, 40_000, graph_mode=1)
+        hot, cold = b.nusselt()
+    for i, c in enumerate(cases):
+        with lbm.Cavity(c["nx"], c["ny"], c["n"], c["Da"], c["Ra"], c["Pr"], c["porosity"], prec=prec,
+                        clamp_mode=1, resid_interval=200) as cav:
+            s1, r1, w1 = cav.run_to_steady(1e-8, 40_000)
+            h1, c1, _ = cav.nusselt()
+        assert (steps[i], why[i]) == (s1, w1), (i, steps, why, s1, w1)
+        assert res[i] == r1 and hot[i] == h1 and cold[i] == c1

@@ -138,11 +138,10 @@ def test_header_struct_matches_binding():
     assert flat == [f[0] for f in lbm.Opts._fields_]
 
 
-@pytest.mark.parametrize("opts", [dict(prec=5), dict(prec=6), dict(prec=6, tau_iters=2), dict(layout=1)])
+@pytest.mark.parametrize("opts", [dict(layout=1), dict(prec=5, layout=1)])
 def test_batch_refuses_what_is_not_built(L, opts):
-    """The batched sweep is not built for the stochastic-rounding storages
-    (a replayed graph would repeat their seeds) or the in-place layout
-    (checked before any device work)."""
+    """The batched sweep is not built for the in-place layout (checked
+    before any device work)."""
     from paper_2011_15073_gb300 import lbm
     o = lbm.default_opts(resid_interval=1000, **opts)
     case = lbm.Case(16, 16, 0.6, 1e-2, 1e5, 6.2, 0.6)
@@ -168,6 +167,21 @@ def test_fma_probe_rejects_bad_arguments():
     assert lbm.lib().lbm_bench_fma_peak(3, -1, 5, ctypes.byref(out), None) == -1
     assert lbm.lib().lbm_bench_fma_peak(0, -1, 0, ctypes.byref(out), None) == -1
     assert lbm.lib().lbm_bench_fma_peak(0, -1, 5, None, None) == -1
+
+
+def test_sr_pairs_check_rejects_bad_arguments():
+    """lbm_debug_sr_pairs validates its arguments (and does nothing for zero
+    pairs) before touching a device."""
+    import numpy as np
+    from paper_2011_15073_gb300 import lbm
+    L = lbm.lib()
+    x, r, o = np.zeros(2, np.float32), np.zeros(1, np.uint32), np.zeros(2, np.uint16)
+    assert L.lbm_debug_sr_pairs(0, 2, x.ctypes.data, r.ctypes.data, o.ctypes.data, 1) == -1
+    assert L.lbm_debug_sr_pairs(0, 0, None, r.ctypes.data, o.ctypes.data, 1) == -1
+    assert L.lbm_debug_sr_pairs(0, 1, x.ctypes.data, r.ctypes.data, None, 1) == -1
+    assert L.lbm_debug_sr_pairs(0, 0, x.ctypes.data, r.ctypes.data, o.ctypes.data, 0) == 0
+    with __import__("pytest").raises(ValueError):
+        lbm.debug_sr_pairs("f16", np.zeros(3, np.float32), np.zeros(1, np.uint32))
 
 
 def test_slab_and_batch_calls_validate_arguments_before_the_device():

@@ -1,6 +1,7 @@
-"""Host check of the 16-bit stochastic rounding (csrc/lbm_round.cuh): built
-with nvcc for the CPU and run here; see tests/host/sr_check.cu for what it
-checks (neighbours only, unbiased over all 2^16 draws, hash invertible)."""
+"""Host check of the hash behind the 16-bit stochastic rounding's random bits
+(csrc/lbm_round.cuh): built with nvcc for the CPU and run here; see
+tests/host/sr_check.cu (hash invertible, hashed starts uniform).  The
+conversions are device instructions: tests/test_rounding_gpu.py."""
 import os
 import shutil
 import subprocess
@@ -10,7 +11,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_stochastic_rounding_is_unbiased_and_brackets(tmp_path):
+def test_rounding_hash_is_a_uniform_bijection(tmp_path):
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
         pytest.skip("nvcc not available")
