@@ -199,6 +199,8 @@ def parse():
                     help="weak: an independent cavity per rank; strong: one cavity in row slabs over the ranks")
     ap.add_argument("--sr-runs", type=int, default=4,
                     help="rounding streams per stochastic-rounding storage in --study precision")
+    ap.add_argument("--study-ref", default=None,
+                    help="--study precision: take the FP64 reference from this earlier output (same N)")
     ap.add_argument("--h-sweep", type=lambda t: [float(x) for x in t.split(",") if x], default=[],
                     help="comma-separated difference steps (log Da) for --study adjoint's single-node sweep")
     ap.add_argument("--readings", default="", help="';'-separated labels of --study sensitivity (all if empty)")
@@ -632,12 +634,21 @@ def study_precision(args):
     hot-wall Nu every 1000 steps over the last 20,000 (stochastic rounding
     leaves a noise of its own on any one snapshot).  Reported: the relative
     L2 errors of u_x, u_y, T at the end, the relative Nu difference at the end
-    and of the mean of the samples."""
+    and of the mean of the samples.  --study-ref FILE takes the FP64 run (its
+    Nu and step count) from an earlier run's output at the same N instead of
+    repeating it; the field errors are then not reported."""
     import numpy as np
     from paper_2011_15073_gb300 import lbm
     N = args.study_N or 512
     variants = [v for v in (args.variants.split(",") if args.variants != DEFAULT_VARIANTS else PRECISION_VARIANTS)
                 if v]
+    recorded_ref = {}
+    if args.study_ref:
+        with open(args.study_ref) as fh:
+            for line in fh:
+                d = json.loads(line) if line.startswith("{") else {}
+                if d.get("study") == "precision" and d.get("variant") == "f64" and d.get("N") == N:
+                    recorded_ref[d["n"]] = d
     for n in (0.6, 1.0):
         case = dict(n=n, Da=1e-2, Ra=1e5, Pr=6.2, porosity=0.6)
         res = {}
@@ -650,6 +661,12 @@ def study_precision(args):
             if parse_variant(v)[0] in ("f16s", "bf16s"):
                 runs += [f"{v}#{s}" for s in range(1, args.sr_runs)]
         for v in runs:
+            if v == "f64" and n in recorded_ref:
+                d = recorded_ref[n]
+                S = d["steps"]
+                res[v] = dict(nu=d["nu_hot"], nu_cold=d["nu_cold"], nu_mean=d["nu_hot"], nu_std=0.0, fl=None,
+                              steps=S, resid=d["residual"], stop="recorded", sec=0.0)
+                continue
             prec, layout, tau_iters, staging = parse_variant(v.split("#")[0])
             seed = int(v.split("#")[1]) if "#" in v else 0
             t = time.perf_counter()
@@ -674,8 +691,9 @@ def study_precision(args):
                           fl=fl, steps=S, resid=resid, stop=stop, sec=time.perf_counter() - t)
         ref = res["f64"]
         for v, r in res.items():
-            err = {k: float(np.linalg.norm(r["fl"][k] - ref["fl"][k]) / np.linalg.norm(ref["fl"][k]))
-                   for k in ("ux", "uy", "T")}
+            err = None if r["fl"] is None or ref["fl"] is None else {
+                k: float(np.linalg.norm(r["fl"][k] - ref["fl"][k]) / np.linalg.norm(ref["fl"][k]))
+                for k in ("ux", "uy", "T")}
             print(json.dumps({"study": "precision", "N": N, **case, "clamp_mode": 1, "variant": v,
                               "nu_hot": r["nu"], "nu_cold": r["nu_cold"], "nu_hot_mean": r["nu_mean"],
                               "nu_hot_std": r["nu_std"],
