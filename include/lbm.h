@@ -119,11 +119,13 @@ typedef struct {
                           steps (rounded up to even) instead of one
                           launch per step, which pays on small,
                           launch-bound grids: 0 auto (64 steps for
-                          grids of at most 512 x 512 nodes whose
-                          storage is not F16S / BF16S, else none);
-                          -1 never; G > 0 always (F16S / BF16S get
-                          LBM_ERR_UNSUPPORTED: a replayed graph would
-                          repeat the stochastic rounding's seeds).
+                          grids of at most 512 x 512 nodes, none for
+                          F16S / BF16S in layout 1), -1 never, G > 0
+                          always (F16S / BF16S with layout 1 get
+                          LBM_ERR_UNSUPPORTED).  With F16S / BF16S the
+                          captured kernels compute each step's seed on
+                          the device from the step count the replay
+                          starts at, so the seeds are a plain launch's.
                           Results are identical either way.  The graph
                           is captured on the context's stream at the
                           first use (and again after

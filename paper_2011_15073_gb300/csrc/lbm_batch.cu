@@ -80,8 +80,6 @@ __global__ void build_active_kernel(const CaseDev *cases, const int *active, int
     if (threadIdx.x == 0 && blockIdx.x == 0) build_active(cases, active, n, a);
 }
 
-constexpr bool rounds_stochastically(int prec) { return prec == LBM_F16S || prec == LBM_BF16S; }
-
 // Where a step of the sweep stands in each case's own step count: step s of
 // the current launch or chunk, `off` steps into the batch call, plus (in a
 // run to steady state, whose chunks replay one graph) the steps the case's

@@ -39,8 +39,10 @@ int graph_len_for(const lbm_ctx *c)
     const int g = c->opts.graph_steps;
     if (g < 0) return 0;
     if (g > 0) return (g + 1) & ~1;
-    const bool sr = c->opts.prec == LBM_F16S || c->opts.prec == LBM_BF16S;
-    return (!sr && (int64_t)c->nx * c->ny <= 512 * 512) ? 64 : 0;
+    // the stochastic-rounding storages take their seeds from the device in a
+    // graph: built for the two-buffer kernels, not the in-place ones
+    const bool sr_aa = lbm::rounds_stochastically(c->opts.prec) && c->opts.layout == 1;
+    return (!sr_aa && (int64_t)c->nx * c->ny <= 512 * 512) ? 64 : 0;
 }
 
 int graph_parity(const lbm_ctx *c) { return c->opts.layout == 1 ? (c->aa_form_o ? 1 : 0) : c->cur; }
@@ -51,12 +53,22 @@ int graph_parity(const lbm_ctx *c) { return c->opts.layout == 1 ? (c->aa_form_o 
 int capture_steps(lbm_ctx *c, int G, int par)
 {
     cudaGraph_t g = nullptr;
+    if (lbm::rounds_stochastically(c->opts.prec) && !c->d_step_base &&
+        cudaMalloc(&c->d_step_base, sizeof(long long)) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_OOM;
+    }
     if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return LBM_ERR_UNSUPPORTED;
     }
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < G && e == cudaSuccess; i++) e = lbm::launch_step(c);
+    const bool sr = lbm::rounds_stochastically(c->opts.prec);
+    for (int i = 0; i < G && e == cudaSuccess; i++) {
+        c->capture_s = sr ? i : -1;   // seeds from d_step_base + i (lbm_kernels.cu)
+        e = lbm::launch_step(c);
+    }
+    c->capture_s = -1;
     const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
     if (e == cudaSuccess) e = e2;
     if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph[par], g, 0);
@@ -95,7 +107,8 @@ int map_lattice(int nx, int ny, double n, double Da, double Ra, double Pr, doubl
         o.device < -1 || o.tau_iters < 0 || o.tau_iters > LBM_TAU_ITERS_MAX || o.staging < 0 ||
         o.staging > 3 || o.graph_steps < -1)
         return LBM_ERR_ARG;
-    if (o.graph_steps > 0 && (o.prec == LBM_F16S || o.prec == LBM_BF16S)) return LBM_ERR_UNSUPPORTED;
+    if (o.graph_steps > 0 && (o.prec == LBM_F16S || o.prec == LBM_BF16S) && o.layout == 1)
+        return LBM_ERR_UNSUPPORTED;
     if (o.staging == 2) return LBM_ERR_UNSUPPORTED;  // the staged kernel is not built
     if (o.staging == 3 && !(o.prec == LBM_BF16D || o.prec == LBM_F16D || o.prec == LBM_F16S || o.prec == LBM_BF16S))
         return LBM_ERR_UNSUPPORTED;
@@ -145,6 +158,7 @@ void free_ctx(lbm_ctx *c)
     cudaFree(c->d_part);
     cudaFree(c->d_nuloc);
     cudaFree(c->d_da);
+    cudaFree(c->d_step_base);
     drop_graphs(c);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -458,6 +472,7 @@ int lbm_step(lbm_ctx *c, int64_t k)
                 if (rc == LBM_ERR_UNSUPPORTED) break;   // this stream cannot be captured: plain launches
                 if (rc) return rc;
             }
+            if (c->d_step_base) CK(lbm::launch_set_step_base(c));   // the replay's seeds start here
             CK(cudaGraphLaunch(c->step_graph[par], c->stream));
             c->steps += G;   // an even number of steps leaves the parity as it was
             t += G;

@@ -17,6 +17,10 @@ struct Buffers {
     void *tau[2] = {nullptr, nullptr};   // 1 plane (double for F64, else float)
 };
 
+// The storages rounded stochastically (their step kernels draw random bits
+// from a per-step seed).
+constexpr bool rounds_stochastically(int prec) { return prec == LBM_F16S || prec == LBM_BF16S; }
+
 struct Launch {
     const void *src;
     void *dst;
@@ -49,6 +53,11 @@ struct lbm_ctx {
     // (two-buffer: which buffer is current; in place: odd-step form).
     cudaGraphExec_t step_graph[2] = {nullptr, nullptr};
     int graph_len = 0;
+    // Stochastic-rounding storages in step graphs: the step count a replay
+    // starts at (device), and while capturing, the place of the launch being
+    // captured (-1 otherwise).
+    long long *d_step_base = nullptr;
+    int capture_s = -1;
     bool have_snap = false;
     bool aa_form_o = false;      // in-place layout: state in the odd-step form
     int64_t steps = 0;
@@ -66,6 +75,8 @@ namespace lbm {
 // cudaError_t from cudaGetLastError().
 cudaError_t launch_init(lbm_ctx *c);
 cudaError_t launch_step(lbm_ctx *c);
+// Write the context's step count to d_step_base (before a step-graph replay).
+cudaError_t launch_set_step_base(lbm_ctx *c);
 // One step of the two-buffer layout between explicit state buffers (same
 // plane geometry as the context's own).
 cudaError_t launch_step_buffers(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst);

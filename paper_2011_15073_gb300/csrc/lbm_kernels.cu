@@ -59,7 +59,45 @@ __global__ void __launch_bounds__(64, 10)
 step4_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
              const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2)
 {
-    step4_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y);
+    step4_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y, [&] { return p.seed; });
+}
+
+// The step kernels of a replayed step graph with the stochastic-rounding
+// storages.  A graph replays its launches' arguments, so the seed cannot be
+// one: it is computed here from the step count the replay starts at (*base,
+// written on the device before each replay) plus the launch's place s in the
+// graph -- the seed a plain launch gets from the host at that step.  Plain
+// launches keep the constant seed (reading it from memory costs the hot
+// kernels a register and 3-5 %).
+struct GraphSeed {
+    const long long *base;
+    int s;
+    uint32_t run;
+};
+__device__ __forceinline__ uint32_t graph_seed(GraphSeed g) { return step_seed((uint64_t)(*g.base + g.s), g.run); }
+
+template <int PREC, int FIELD, int TAU>
+__global__ void __launch_bounds__(128)
+step2_graph_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
+                   const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2,
+                   GraphSeed g)
+{
+    step2_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y, graph_seed(g));
+}
+
+template <int PREC, int FIELD, int TAU>
+__global__ void __launch_bounds__(64, 10)
+step4_graph_kernel(const typename Store<PREC>::S *__restrict__ src, typename Store<PREC>::S *__restrict__ dst,
+                   const float *__restrict__ tsrc, float *__restrict__ tdst, Phys<float> p, Phys<F2> p2,
+                   GraphSeed g)
+{
+    step4_tile<PREC, FIELD, TAU>(src, dst, tsrc, tdst, p, p2, blockIdx.x * 256, blockIdx.y,
+                                 [&] { return graph_seed(g); });
+}
+
+__global__ void set_step_base_kernel(long long *base, long long steps)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *base = steps;
 }
 
 // tau the next collision of every node starts from, in implicit mode (the
@@ -274,6 +312,13 @@ __global__ void export_kernel(double *__restrict__ out, const typename Store<PRE
 // ------------------------------------------------------------- launchers
 static dim3 node_grid(const lbm_ctx *c, int bx) { return dim3((c->nx + bx - 1) / bx, c->ny); }
 
+// Seed source of a launch being captured into a step graph (capture_s: its
+// place in the graph).
+static GraphSeed graph_seed_of(const lbm_ctx *c)
+{
+    return GraphSeed{c->d_step_base, c->capture_s, run_word(c->opts.seed)};
+}
+
 int residual_blocks(const lbm_ctx *c)
 {
     const int64_t n = (int64_t)c->nx * c->ny;
@@ -304,6 +349,15 @@ static cudaError_t step_buffers_tau(lbm_ctx *c, const void *src, void *dst, cons
             (const typename St::S *)src, (typename St::S *)dst, (const typename St::TauS *)tsrc,
             (typename St::TauS *)tdst, make_params<typename St::R>(c));
     } else {
+        if constexpr (rounds_stochastically(PREC)) {
+            if (c->capture_s >= 0) {   // a launch captured into a step graph
+                auto *kern = c->d_da ? step2_graph_kernel<PREC, 1, TAU> : step2_graph_kernel<PREC, 0, TAU>;
+                kern<<<node_grid(c, 256), 128, 0, c->stream>>>(
+                    (const typename St::S *)src, (typename St::S *)dst, (const float *)tsrc, (float *)tdst,
+                    make_params<float>(c), make_params<F2>(c), graph_seed_of(c));
+                return cudaGetLastError();
+            }
+        }
         auto *kern = c->d_da ? step2_kernel<PREC, 1, TAU> : step2_kernel<PREC, 0, TAU>;
         kern<<<node_grid(c, 256), 128, 0, c->stream>>>(
             (const typename St::S *)src, (typename St::S *)dst, (const float *)tsrc, (float *)tdst,
@@ -337,6 +391,15 @@ template <int PREC, int TAU>
 static cudaError_t step4_buffers_tau(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
 {
     using St = Store<PREC>;
+    if constexpr (rounds_stochastically(PREC)) {
+        if (c->capture_s >= 0) {   // a launch captured into a step graph
+            auto *kern = c->d_da ? step4_graph_kernel<PREC, 1, TAU> : step4_graph_kernel<PREC, 0, TAU>;
+            kern<<<node_grid(c, 256), 64, 0, c->stream>>>((const typename St::S *)src, (typename St::S *)dst,
+                                                          (const float *)tsrc, (float *)tdst, make_params<float>(c),
+                                                          make_params<F2>(c), graph_seed_of(c));
+            return cudaGetLastError();
+        }
+    }
     auto *kern = c->d_da ? step4_kernel<PREC, 1, TAU> : step4_kernel<PREC, 0, TAU>;
     kern<<<node_grid(c, 256), 64, 0, c->stream>>>((const typename St::S *)src, (typename St::S *)dst,
                                                   (const float *)tsrc, (float *)tdst, make_params<float>(c),
@@ -510,6 +573,12 @@ cudaError_t launch_halo_unpack(lbm_ctx *c, const void *d_lo, const void *d_hi)
     }
 
 cudaError_t launch_init(lbm_ctx *c) { LBM_DISPATCH(init_t, c) }
+cudaError_t launch_set_step_base(lbm_ctx *c)
+{
+    set_step_base_kernel<<<1, 32, 0, c->stream>>>(c->d_step_base, (long long)c->steps);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step(lbm_ctx *c) { LBM_DISPATCH(step_t, c) }
 cudaError_t launch_step_buffers(lbm_ctx *c, const void *src, void *dst, const void *tsrc, void *tdst)
 {

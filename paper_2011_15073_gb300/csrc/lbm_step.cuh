@@ -143,12 +143,15 @@ __device__ __forceinline__ F2 pair_words(const Phys<F2> &p2, const uint32_t (&in
 // itself (x = 0 or nx - 1) used a value from beyond the wall -- the previous
 // row's tail or the next row's head, inside the allocation -- so that one
 // node is then updated again with the wall rules.  Results equal
-// step2_tile's wherever both take the packed path.
-template <int PREC, int FIELD, int TAU>
+// step2_tile's wherever both take the packed path.  seed_of() returns the
+// step's seed (as for step_node) where it is used: a plain launch reads its
+// parameter there rather than holding it in a register across the tile.
+template <int PREC, int FIELD, int TAU, class SeedOf>
 __device__ __forceinline__ void step4_tile(const typename Store<PREC>::S *__restrict__ src,
                                            typename Store<PREC>::S *__restrict__ dst,
                                            const float *__restrict__ tsrc, float *__restrict__ tdst,
-                                           const Phys<float> &p, const Phys<F2> &p2, int xbase, int y)
+                                           const Phys<float> &p, const Phys<F2> &p2, int xbase, int y,
+                                           SeedOf seed_of)
 {
     static_assert(is16<PREC>(), "four-node tiles are built for the 16-bit storages");
     using S = typename Store<PREC>::S;
@@ -158,7 +161,7 @@ __device__ __forceinline__ void step4_tile(const typename Store<PREC>::S *__rest
     const bool fast = y > 0 && y < p.ny - 1 && wx + 128 <= p.nx;
     if (!fast) {
         for (int j = 0; j < 4; j++)
-            if (x0 + j < p.nx) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, x0 + j, y, p.seed);
+            if (x0 + j < p.nx) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, x0 + j, y, seed_of());
         return;
     }
     const int64_t P = p.plane, W = p.pitch;
@@ -200,13 +203,13 @@ __device__ __forceinline__ void step4_tile(const typename Store<PREC>::S *__rest
         }
     }
     uint32_t oa[14], ob[14];
-    const F2 ta = pair_words<PREC, FIELD, TAU>(p2, ra, F2(lag.x, lag.y), k, p.seed, oa);
-    const F2 tb = pair_words<PREC, FIELD, TAU>(p2, rb, F2(lag.z, lag.w), k + 2, p.seed, ob);
+    const F2 ta = pair_words<PREC, FIELD, TAU>(p2, ra, F2(lag.x, lag.y), k, seed_of(), oa);
+    const F2 tb = pair_words<PREC, FIELD, TAU>(p2, rb, F2(lag.z, lag.w), k + 2, seed_of(), ob);
 #pragma unroll
     for (int q = 0; q < 14; q++) *reinterpret_cast<uint2 *>(dst + q * P + k) = make_uint2(oa[q], ob[q]);
     if constexpr (TAU == 0) *reinterpret_cast<float4 *>(tdst + k) = make_float4(ta.v.x, ta.v.y, tb.v.x, tb.v.y);
-    if (x0 == 0) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, 0, y, p.seed);
-    if (x0 + 3 == p.nx - 1) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, p.nx - 1, y, p.seed);
+    if (x0 == 0) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, 0, y, seed_of());
+    if (x0 + 3 == p.nx - 1) step_node<PREC, float, FIELD, TAU>(src, dst, tsrc, tdst, p, p.nx - 1, y, seed_of());
 }
 
 }  // namespace lbm

@@ -150,11 +150,12 @@ def test_batch_refuses_what_is_not_built(L, opts):
     assert h.value is None
 
 
-def test_graphs_refused_for_stochastic_storages(L):
-    """A replayed graph would repeat the stochastic rounding's seeds."""
+def test_graphs_refused_for_stochastic_storages_in_place(L):
+    """Step graphs of the stochastic-rounding storages are built for the
+    two-buffer layout only (their seeds come from the device there)."""
     from paper_2011_15073_gb300 import lbm
     for prec in ("f16s", "bf16s"):
-        o = lbm.default_opts(prec=prec, graph_steps=16)
+        o = lbm.default_opts(prec=prec, graph_steps=16, layout=1)
         h = ctypes.c_void_p()
         assert L.lbm_init(ctypes.byref(h), 8, 8, 0.6, 1e-2, 1e5, 6.2, 0.6, ctypes.byref(o)) == -7
 

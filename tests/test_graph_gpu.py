@@ -55,3 +55,35 @@ def test_graph_recaptured_after_darcy_field_change(mods):
     b = run(lbm, inputs, nx, ny, "f32d", 0, 32, chunks, Da, Da2)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("prec,staging", [("f16s", 0), ("bf16s", 0), ("f16s", 3), ("bf16s", 3)])
+@pytest.mark.parametrize("graph_steps", [0, 16])
+def test_graph_replay_with_stochastic_rounding(mods, prec, staging, graph_steps):
+    """The stochastic-rounding storages in replayed step graphs: each
+    captured launch computes its seed on the device from the step count the
+    replay starts at, so the states equal one launch per step bit for bit
+    (two- and four-node kernels; the start state is copied in natively,
+    since an import rounds with address-dependent bits)."""
+    inputs, lbm = mods
+    nx, ny = 130, 67
+    chunks = [1, 200, 63, 3, 128]
+    kw = dict(prec=prec, clamp_mode=CASE["clamp_mode"], staging=staging)
+    with lbm.Cavity(nx, ny, CASE["n"], CASE["Da"], CASE["Ra"], CASE["Pr"], CASE["porosity"], graph_steps=-1,
+                    **kw) as a:
+        a.set_state_f64(*inputs.perturbed_state(a.get_state_f64(), seed=nx + ny, amp=1e-2))
+        start = np.empty(a.state_bytes(), np.uint8)
+        a.get_state(start)
+        for k in chunks:
+            a.step(k)
+        want = np.empty_like(start)
+        a.get_state(want)
+    with lbm.Cavity(nx, ny, CASE["n"], CASE["Da"], CASE["Ra"], CASE["Pr"], CASE["porosity"],
+                    graph_steps=graph_steps, **kw) as b:
+        b.set_state(start)
+        for k in chunks:
+            b.step(k)
+        got = np.empty_like(start)
+        b.get_state(got)
+    assert np.array_equal(got, want)
+    assert not np.array_equal(got, start)
