@@ -190,16 +190,25 @@ double stag_floor(const lbm_ctx *c)
 // Copy the 14 distribution planes between host (canonical order, unpadded)
 // and device.  In the in-place layout's canonical form population i of a
 // node lives in plane opp(i).
+// Copy `rows` rows of `row_bytes` between host (packed rows) and device
+// (rows `pitch_bytes` apart).  Unpadded rows are one linear copy: the
+// strided form moved a 1 GB state at a small fraction of the link's rate.
+cudaError_t copy_rows(lbm_ctx *c, void *host, void *dev, size_t row_bytes, size_t pitch_bytes, size_t rows,
+                      bool to_host)
+{
+    const cudaMemcpyKind kind = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
+    if (row_bytes == pitch_bytes)
+        return to_host ? cudaMemcpyAsync(host, dev, row_bytes * rows, kind, c->stream)
+                       : cudaMemcpyAsync(dev, host, row_bytes * rows, kind, c->stream);
+    return to_host ? cudaMemcpy2DAsync(host, row_bytes, dev, pitch_bytes, row_bytes, rows, kind, c->stream)
+                   : cudaMemcpy2DAsync(dev, pitch_bytes, host, row_bytes, row_bytes, rows, kind, c->stream);
+}
+
 int copy_planes(lbm_ctx *c, void *host, bool to_host)
 {
     const size_t es = c->dist_elem, n = (size_t)c->nx * c->ny;
     if (c->opts.layout == 0) {
-        if (to_host)
-            CK(cudaMemcpy2DAsync(host, c->nx * es, c->buf.dist[c->cur], c->pitch * es, c->nx * es,
-                                 14 * (size_t)c->ny, cudaMemcpyDeviceToHost, c->stream));
-        else
-            CK(cudaMemcpy2DAsync(c->buf.dist[c->cur], c->pitch * es, host, c->nx * es, c->nx * es,
-                                 14 * (size_t)c->ny, cudaMemcpyHostToDevice, c->stream));
+        CK(copy_rows(c, host, c->buf.dist[c->cur], c->nx * es, c->pitch * es, 14 * (size_t)c->ny, to_host));
         return LBM_OK;
     }
     static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
@@ -207,12 +216,7 @@ int copy_planes(lbm_ctx *c, void *host, bool to_host)
         const int j = i < 9 ? OPP[i] : 9 + OPP[i - 9];
         char *h = (char *)host + (size_t)i * n * es;
         char *d = (char *)c->buf.dist[0] + (size_t)j * c->plane * es;
-        if (to_host)
-            CK(cudaMemcpy2DAsync(h, c->nx * es, d, c->pitch * es, c->nx * es, c->ny, cudaMemcpyDeviceToHost,
-                                 c->stream));
-        else
-            CK(cudaMemcpy2DAsync(d, c->pitch * es, h, c->nx * es, c->nx * es, c->ny, cudaMemcpyHostToDevice,
-                                 c->stream));
+        CK(copy_rows(c, h, d, c->nx * es, c->pitch * es, (size_t)c->ny, to_host));
     }
     return LBM_OK;
 }
@@ -601,8 +605,8 @@ int lbm_get_state(lbm_ctx *c, void *host, size_t bytes)
     if (int rc0 = canonical(c)) return rc0;
     const size_t es = c->dist_elem, ts = c->tau_elem, n = (size_t)c->nx * c->ny;
     if (int rc0 = copy_planes(c, host, true)) return rc0;
-    CK(cudaMemcpy2DAsync((char *)host + 14 * n * es, c->nx * ts, c->buf.tau[c->cur], c->pitch * ts,
-                         c->nx * ts, c->ny, cudaMemcpyDeviceToHost, c->stream));
+    CK(copy_rows(c, (char *)host + 14 * n * es, c->buf.tau[c->cur], c->nx * ts, c->pitch * ts, (size_t)c->ny,
+                 true));
     CK(cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
@@ -614,8 +618,8 @@ int lbm_set_state(lbm_ctx *c, const void *host, size_t bytes)
     const size_t es = c->dist_elem, ts = c->tau_elem, n = (size_t)c->nx * c->ny;
     c->aa_form_o = false;   // the whole state is replaced by a canonical one
     if (int rc0 = copy_planes(c, const_cast<void *>(host), false)) return rc0;
-    CK(cudaMemcpy2DAsync(c->buf.tau[c->cur], c->pitch * ts, (const char *)host + 14 * n * es, c->nx * ts,
-                         c->nx * ts, c->ny, cudaMemcpyHostToDevice, c->stream));
+    CK(copy_rows(c, (char *)const_cast<void *>(host) + 14 * n * es, c->buf.tau[c->cur], c->nx * ts, c->pitch * ts,
+                 (size_t)c->ny, false));
     CK(cudaStreamSynchronize(c->stream));
     c->have_snap = false;
     return LBM_OK;

@@ -355,11 +355,14 @@ def test_zero_steps_and_repeat_calls(mods):
 
 
 @LAYOUTS
-def test_native_state_roundtrip(mods, layout):
+@pytest.mark.parametrize("nx", [33, 128], ids=["padded", "unpadded"])
+def test_native_state_roundtrip(mods, layout, nx):
+    """Native state out and back in: padded rows (strided copies) and rows
+    of a multiple of 64 nodes (one linear copy), both layouts."""
     _, inputs, lbm = mods
     c = CASES["thinning"]
     for prec in ("f64", "f32", "f32d", "bf16d", "f16d"):
-        with gpu_for(lbm, 33, 21, c, prec, layout) as cav:
+        with gpu_for(lbm, nx, 21, c, prec, layout) as cav:
             cav.step(5)
             buf = np.empty(cav.state_bytes(), dtype=np.uint8)
             cav.get_state(buf)
@@ -371,6 +374,11 @@ def test_native_state_roundtrip(mods, layout):
             again = np.empty_like(buf)
             cav.get_state(again)
             assert np.array_equal(after, again), prec
+            if prec == "f64":   # native layout: f0..f8, g0..g4, tau planes of ny x nx values
+                f, g, tau = cav.get_state_f64()
+                planes = again.view(np.float64).reshape(15, 21, nx)
+                assert np.array_equal(planes[:9], f) and np.array_equal(planes[9:14], g)
+                assert np.array_equal(planes[14], tau)
 
 
 def test_residual_matches_definition(mods):
