@@ -626,6 +626,18 @@ DEFAULT_VARIANTS = "f64,f32,f32d@aa,f32d@tau2,bf16d,f16d,f16s,f16s@reg,bf16s,f16
 PRECISION_VARIANTS = ("f64", "f64@tau4", "f32", "f32@tau2", "f32d", "f16d", "bf16d", "f16s", "bf16s")
 
 
+def recorded_fp64_reference(path, N):
+    """The FP64 rows of an earlier --study precision output at grid N, by
+    power-law index n (JSON lines; other lines of the file are skipped)."""
+    out = {}
+    with open(path) as fh:
+        for line in fh:
+            d = json.loads(line) if line.startswith("{") else {}
+            if d.get("study") == "precision" and d.get("variant") == "f64" and d.get("N") == N:
+                out[d["n"]] = d
+    return out
+
+
 def study_precision(args):
     """Storage formats and tau schemes against FP64 storage (lagged tau) at
     the FP64 steady state: the FP64 run goes to a residual of 1e-10 in S steps
@@ -642,13 +654,7 @@ def study_precision(args):
     N = args.study_N or 512
     variants = [v for v in (args.variants.split(",") if args.variants != DEFAULT_VARIANTS else PRECISION_VARIANTS)
                 if v]
-    recorded_ref = {}
-    if args.study_ref:
-        with open(args.study_ref) as fh:
-            for line in fh:
-                d = json.loads(line) if line.startswith("{") else {}
-                if d.get("study") == "precision" and d.get("variant") == "f64" and d.get("N") == N:
-                    recorded_ref[d["n"]] = d
+    recorded_ref = recorded_fp64_reference(args.study_ref, N) if args.study_ref else {}
     for n in (0.6, 1.0):
         case = dict(n=n, Da=1e-2, Ra=1e5, Pr=6.2, porosity=0.6)
         res = {}

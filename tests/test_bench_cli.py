@@ -66,3 +66,14 @@ def test_reduced_storage_summary_picks_fastest_within_the_bar():
     s = bench.reduced_storage_summary(v, "f32d", 57000.0)
     assert s["variant"] == "f16s" and s["speedup_vs_f64_storage"] == 69000.0 / 2000.0
     assert bench.reduced_storage_summary({"f16s": v["f16s"]}, "f32d", 1.0) is None   # no FP64 run to compare
+
+
+def test_recorded_fp64_reference_reads_the_committed_1024_rows():
+    """--study-ref takes the FP64 rows (Nu and step count per n) of the grid
+    asked for from an earlier output, skipping comment and other lines."""
+    import bench
+    ref = bench.recorded_fp64_reference(os.path.join(ROOT, "profiles", "precision_study_1024.txt"), 1024)
+    assert sorted(ref) == [0.6, 1.0]
+    assert ref[0.6]["steps"] == 1836000 and ref[1.0]["steps"] == 2512000
+    assert abs(ref[0.6]["nu_hot"] - 8.124632) < 1e-6 and abs(ref[1.0]["nu_hot"] - 3.673356) < 1e-6
+    assert bench.recorded_fp64_reference(os.path.join(ROOT, "profiles", "precision_study_1024.txt"), 512) == {}
