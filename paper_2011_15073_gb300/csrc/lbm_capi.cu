@@ -187,9 +187,6 @@ double stag_floor(const lbm_ctx *c)
     }
 }
 
-// Copy the 14 distribution planes between host (canonical order, unpadded)
-// and device.  In the in-place layout's canonical form population i of a
-// node lives in plane opp(i).
 // Copy `rows` rows of `row_bytes` between host (packed rows) and device
 // (rows `pitch_bytes` apart).  Unpadded rows are one linear copy: the
 // strided form moved a 1 GB state at a small fraction of the link's rate.
@@ -204,6 +201,9 @@ cudaError_t copy_rows(lbm_ctx *c, void *host, void *dev, size_t row_bytes, size_
                    : cudaMemcpy2DAsync(dev, pitch_bytes, host, row_bytes, row_bytes, rows, kind, c->stream);
 }
 
+// Copy the 14 distribution planes between host (canonical order, unpadded)
+// and device.  In the in-place layout's canonical form population i of a
+// node lives in plane opp(i).
 int copy_planes(lbm_ctx *c, void *host, bool to_host)
 {
     const size_t es = c->dist_elem, n = (size_t)c->nx * c->ny;
