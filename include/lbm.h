@@ -56,10 +56,10 @@ enum {
  * bits for BF16D and F16D, in 32 bits for F32D; the per-node relaxation time
  * is then stored as FP32.  F16S and BF16S store the same 16-bit deviations
  * rounded stochastically (up or down with probability given by the distance
- * to the two neighbours, random bits hashed from a per-step seed and the
- * element's address), so that updates below the 16-bit spacing are not
+ * to the two neighbours; the random bits are hashed from a per-step seed
+ * and the node's offset), so that updates below the 16-bit spacing are not
  * lost on average near a steady state; the paper has no counterpart (its
- * storage is not stated).  Not built with the batch API or the adjoint. */
+ * storage is not stated).  Not built with the adjoint. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_BF16D = 2, LBM_F16D = 3, LBM_F32D = 4,
                LBM_F16S = 5, LBM_BF16S = 6 } lbm_prec;
 
