@@ -273,14 +273,16 @@ int lbm_set_state_f64(lbm_ctx *ctx, const double *f, const double *g,
  * a field), the power-law index n and the Rayleigh number Ra.  The forward
  * run keeps a checkpoint every ckpt_every steps; the reverse sweep
  * recomputes one segment of states at a time from its checkpoint and runs
- * the hand-written reverse of the fused step over it.  from_rest = 1 first
+ * the hand-written reverse of the fused step over it, recomputing the next
+ * segment on a second stream meanwhile (the result does not depend on
+ * ckpt_every or on that overlap).  from_rest = 1 first
  * resets the state to the rest state of lbm_init and includes the
  * dependence of its relaxation time tau_0 on n and Ra; from_rest = 0 starts
  * from the current state, held fixed.  Afterwards the context holds s_T.
  * Outputs (any may be NULL): *J, dDa (host, nx*ny doubles, [ny][nx]), *dn,
  * *dRa, and *peak_bytes, the device memory the run used (state buffers,
- * checkpoints, one segment of states, two adjoint buffers, FP64 gradient
- * planes).  Parameter gradients accumulate in FP64.  Two-buffer layout with
+ * checkpoints, two segments of states, or one if there is a single segment
+ * or no memory for a second, two adjoint buffers, FP64 gradient planes).  Parameter gradients accumulate in FP64.  Two-buffer layout with
  * FP64 or FP32 storage; other storages get LBM_ERR_UNSUPPORTED.
  * Synchronous.  Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
 int lbm_adjoint_nu(lbm_ctx *ctx, int64_t steps, int ckpt_every, int from_rest,

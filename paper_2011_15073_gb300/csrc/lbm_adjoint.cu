@@ -198,31 +198,60 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
     std::vector<void *> allocs;
     auto alloc = [&](size_t bytes) -> void * {
         void *p = nullptr;
-        if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();   // an allocation failure is reported by the return code
+            return nullptr;
+        }
         allocs.push_back(p);
         return p;
     };
+    // second stream of the reverse sweep and its fork / join events
+    cudaStream_t s2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     auto cleanup = [&]() {
         cudaStreamSynchronize(c->stream);
+        if (s2) cudaStreamSynchronize(s2);
         for (void *p : allocs) cudaFree(p);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (s2) cudaStreamDestroy(s2);
     };
     int rc = LBM_OK;
     // checkpoints s_{j ckpt}, the states of one segment, two adjoint buffers, gradients
     char *ck = (char *)alloc((dist_bytes + tau_bytes) * (size_t)(nseg > 0 ? nseg : 1));
     const int seg_len = (int)(steps < ckpt ? steps : ckpt);
-    char *seg = (char *)alloc((dist_bytes + tau_bytes) * (size_t)(seg_len > 0 ? seg_len : 1));
+    const size_t seg_bytes = (dist_bytes + tau_bytes) * (size_t)(seg_len > 0 ? seg_len : 1);
+    char *segs[2] = {(char *)alloc(seg_bytes), nullptr};
     V *lam[2] = {(V *)alloc(lam_bytes), (V *)alloc(lam_bytes)};
     const dim3 grid((c->nx + 127) / 128, c->ny);
     const size_t nblk = (size_t)grid.x * grid.y;
     double *g3 = (double *)alloc(sizeof(double) * (nn + 2 * nblk));   // dDa per node, dn / dRa per block
     double *red = (double *)alloc(sizeof(double) * 4);
-    if (!ck || !seg || !lam[0] || !lam[1] || !g3 || !red) {
+    if (!ck || !segs[0] || !lam[0] || !lam[1] || !g3 || !red) {
         cleanup();
         return LBM_ERR_OOM;
     }
+    // A second segment buffer and stream let the states of segment j - 1 be
+    // recomputed while the reverse steps of segment j run (both are small,
+    // latency-bound launches at the sizes the adjoint runs at, and share the
+    // SMs).  Without them (one segment, or no memory or stream for them) the
+    // two run one after the other on the context's stream.  The kernels and
+    // their arguments are the same either way, so are the results.
+    if (nseg > 1) {
+        segs[1] = (char *)alloc(seg_bytes);
+        if (segs[1] && (cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+            cudaGetLastError();
+            segs[1] = nullptr;
+        }
+    }
+    const bool overlap = segs[1] != nullptr;
     // device memory of this run: the context's two state buffers plus the
-    // checkpoints, one segment of states, two adjoint buffers and the gradients
-    const double total = (double)(dist_bytes + tau_bytes) * (double)(nseg + seg_len + 2) + 2.0 * lam_bytes +
+    // checkpoints, one or two segments of states, two adjoint buffers and the
+    // gradients
+    const double total = (double)(dist_bytes + tau_bytes) * (double)(nseg + 2) +
+                         (double)seg_bytes * (overlap ? 2.0 : 1.0) + 2.0 * lam_bytes +
                          sizeof(double) * (double)(nn + 2 * nblk);
     if (peak_bytes) *peak_bytes = total;
     if (from_rest) {
@@ -232,8 +261,9 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
     const Phys<V> pv = make_params<V>(c);
     auto ckd = [&](int64_t j) { return (S *)(ck + (size_t)j * (dist_bytes + tau_bytes)); };
     auto ckt = [&](int64_t j) { return (TauS *)(ck + (size_t)j * (dist_bytes + tau_bytes) + dist_bytes); };
-    auto sgd = [&](int j) { return (S *)(seg + (size_t)j * (dist_bytes + tau_bytes)); };
-    auto sgt = [&](int j) { return (TauS *)(seg + (size_t)j * (dist_bytes + tau_bytes) + dist_bytes); };
+    // state i of the segment held in buffer b
+    auto sgd = [&](int b, int i) { return (S *)(segs[b] + (size_t)i * (dist_bytes + tau_bytes)); };
+    auto sgt = [&](int b, int i) { return (TauS *)(segs[b] + (size_t)i * (dist_bytes + tau_bytes) + dist_bytes); };
     // forward with checkpoints (the context's own buffers advance to s_T)
     for (int64_t j = 0; j < nseg && rc == LBM_OK; j++) {
         if (cudaMemcpyAsync(ckd(j), c->buf.dist[c->cur], dist_bytes, cudaMemcpyDeviceToDevice, c->stream) ||
@@ -262,7 +292,7 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
                                                                        L / (3.0 * c->ny * dT));
         if (cudaGetLastError() != cudaSuccess) rc = LBM_ERR_CUDA;
     }
-    // reverse sweep, one segment at a time
+    // reverse sweep, one segment at a time, the last one first
     Chain chain{c->lat.n, 0.0, c->lat.tauT, 0.0, 0.0, 0.0, 0.0};
     {
         // Ra from the mapping: tauT - 1/2 = 3 U_c L / sqrt(Ra)
@@ -275,58 +305,111 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
         chain.b_wT = wT * wT * (chain.tauT - 0.5) / (2.0 * chain.Ra);
         chain.inv_Da = c->lat.L * c->lat.L / c->lat.K;
     }
-    // One segment's kernels: the states s_{j ckpt + i}, i = 1..len-1,
-    // recomputed from the copy of the checkpoint in slot 0, then the reverse
-    // steps i = len-1..0 from adjoint buffer `c0`.
-    auto segment = [&](int len, int c0) -> int {
-        for (int i = 1; i < len; i++)
-            if (lbm::launch_step_buffers(c, sgd(i - 1), sgd(i), sgt(i - 1), sgt(i)) != cudaSuccess)
-                return LBM_ERR_CUDA;
+    auto seg_len_of = [&](int64_t j) { return (j + 1) * ckpt <= steps ? ckpt : steps - j * ckpt; };
+    auto buf_of = [&](int64_t j) { return overlap ? (int)(j & 1) : 0; };
+    // Checkpoint j into slot 0 of its segment buffer (a plain copy on the
+    // context's stream, never part of a graph: its source differs per
+    // segment).
+    auto copy_ckpt = [&](int64_t j) -> int {
+        const int b = buf_of(j);
+        if (cudaMemcpyAsync(sgd(b, 0), ckd(j), dist_bytes, cudaMemcpyDeviceToDevice, c->stream) ||
+            cudaMemcpyAsync(sgt(b, 0), ckt(j), tau_bytes, cudaMemcpyDeviceToDevice, c->stream))
+            return LBM_ERR_CUDA;
+        return LBM_OK;
+    };
+    // The states s_{j ckpt + i}, i = 1..len-1, of segment j recomputed from
+    // slot 0 on stream `s` (the context's step launcher, pointed at `s` for
+    // these launches).
+    auto recompute = [&](int64_t j, cudaStream_t s) -> int {
+        const int b = buf_of(j), len = (int)seg_len_of(j);
+        const cudaStream_t own = c->stream;
+        c->stream = s;
+        int r = LBM_OK;
+        for (int i = 1; i < len && r == LBM_OK; i++)
+            if (lbm::launch_step_buffers(c, sgd(b, i - 1), sgd(b, i), sgt(b, i - 1), sgt(b, i)) != cudaSuccess)
+                r = LBM_ERR_CUDA;
+        c->stream = own;
+        return r;
+    };
+    // The reverse steps i = len-1..0 of segment j from adjoint buffer c0, on
+    // the context's stream.
+    auto reverse = [&](int64_t j, int c0) -> int {
+        const int b = buf_of(j), len = (int)seg_len_of(j);
         int cc = c0;
         for (int i = len - 1; i >= 0; i--) {
-            adj_step_kernel<PREC, V><<<grid, 128, 0, c->stream>>>(sgd(i), sgt(i), lam[cc], lam[cc ^ 1], g3,
+            adj_step_kernel<PREC, V><<<grid, 128, 0, c->stream>>>(sgd(b, i), sgt(b, i), lam[cc], lam[cc ^ 1], g3,
                                                                  g3 + nn, g3 + nn + nblk, pv, chain);
             if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
             cc ^= 1;
         }
         return LBM_OK;
     };
-    // Full segments replay one captured graph per parity of the adjoint
-    // buffer they start from (same kernels, same arguments: identical
-    // results); a shorter last segment, or a stream that is already being
-    // captured, runs plain launches.
-    cudaGraphExec_t seg_exec[2] = {nullptr, nullptr};
+    // Run `body` (launches on the context's stream, and on the second stream
+    // forked from and joined back into it) through the cached graph `ex`:
+    // captured at first use, replayed afterwards with the same kernels and
+    // arguments, so the results are identical.  Pieces that are not
+    // `cacheable`, or a stream that is already being captured, run plain.
     cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
     const bool can_capture = cudaStreamIsCapturing(c->stream, &cap_status) == cudaSuccess &&
                              cap_status == cudaStreamCaptureStatusNone && ckpt >= 2;
-    for (int64_t j = nseg - 1; j >= 0 && rc == LBM_OK; j--) {
-        const int64_t len = (j + 1) * ckpt <= steps ? ckpt : steps - j * ckpt;
-        cudaMemcpyAsync(sgd(0), ckd(j), dist_bytes, cudaMemcpyDeviceToDevice, c->stream);
-        cudaMemcpyAsync(sgt(0), ckt(j), tau_bytes, cudaMemcpyDeviceToDevice, c->stream);
-        bool replayed = false;
-        if (can_capture && len == ckpt) {
-            if (!seg_exec[cur]) {
+    std::vector<cudaGraphExec_t> execs;
+    auto run = [&](cudaGraphExec_t &ex, bool cacheable, auto &&body) -> int {
+        if (can_capture && cacheable) {
+            if (!ex) {
                 cudaGraph_t g = nullptr;
                 if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-                    const int rs = segment((int)len, cur);
+                    const int rs = body();
                     const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
-                    if (rs == LBM_OK && ee == cudaSuccess && g &&
-                        cudaGraphInstantiate(&seg_exec[cur], g, 0) != cudaSuccess)
-                        seg_exec[cur] = nullptr;
+                    if (rs == LBM_OK && ee == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess)
+                        execs.push_back(ex);
+                    else
+                        ex = nullptr;
                     if (g) cudaGraphDestroy(g);
                     cudaGetLastError();
                 }
             }
-            if (seg_exec[cur]) {
-                if (cudaGraphLaunch(seg_exec[cur], c->stream) != cudaSuccess) rc = LBM_ERR_CUDA;
-                replayed = true;
-            }
+            if (ex) return cudaGraphLaunch(ex, c->stream) == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
         }
-        if (!replayed && rc == LBM_OK) rc = segment((int)len, cur);
+        return body();
+    };
+    // Stage j.  With two segment buffers: the reverse steps of segment j on
+    // the context's stream and, beside them on the second stream, the
+    // recomputation of segment j - 1 into the other buffer, whose last
+    // reader (the reverse of segment j + 1) ended with the previous stage;
+    // its checkpoint is copied in first.  With one buffer: the reverse steps,
+    // then the copy and the recomputation, one after the other.  Only the
+    // last segment can be shorter than ckpt, and it comes first; the stage of
+    // segment 0, which runs once, is not captured.
+    cudaGraphExec_t ex_both[2][2] = {}, ex_rev[2] = {}, ex_rec = nullptr;
+    if (rc == LBM_OK && nseg > 0) {
+        rc = copy_ckpt(nseg - 1);
+        if (rc == LBM_OK) rc = recompute(nseg - 1, c->stream);
+    }
+    for (int64_t j = nseg - 1; j >= 0 && rc == LBM_OK; j--) {
+        const int64_t len = seg_len_of(j);
+        const bool full = len == ckpt;
+        if (overlap) {
+            if (j >= 1) rc = copy_ckpt(j - 1);
+            if (rc == LBM_OK)
+                rc = run(ex_both[buf_of(j)][cur], full && j >= 1, [&]() -> int {
+                    if (cudaEventRecord(ev_fork, c->stream) || cudaStreamWaitEvent(s2, ev_fork, 0))
+                        return LBM_ERR_CUDA;
+                    if (int r = reverse(j, cur)) return r;
+                    if (j >= 1)
+                        if (int r = recompute(j - 1, s2)) return r;
+                    if (cudaEventRecord(ev_join, s2) || cudaStreamWaitEvent(c->stream, ev_join, 0))
+                        return LBM_ERR_CUDA;
+                    return LBM_OK;
+                });
+        } else {
+            rc = run(ex_rev[cur], full, [&]() -> int { return reverse(j, cur); });
+            if (rc == LBM_OK && j >= 1) rc = copy_ckpt(j - 1);
+            if (rc == LBM_OK && j >= 1)
+                rc = run(ex_rec, seg_len_of(j - 1) == ckpt, [&]() -> int { return recompute(j - 1, c->stream); });
+        }
         if (len & 1) cur ^= 1;
     }
-    for (auto &e : seg_exec)
-        if (e) cudaGraphExecDestroy(e);
+    for (cudaGraphExec_t e : execs) cudaGraphExecDestroy(e);
     // reductions: sum of the n and Ra partials, and lambda_0 on tau for tau_0(n, Ra)
     double h[3] = {0, 0, 0};
     if (rc == LBM_OK) {

@@ -9,6 +9,7 @@
   1e-14 / 1e-4 = 1e-10, so 1e-5 relative is a safe bound).
 * FP32 adjoint against the FP64 one (the FP32 run's gradient carries the
   FP32 trajectory's rounding: 1e-2 relative on the aggregate gradients).
+* The same gradients, bit for bit, whatever the checkpoint segmentation.
 """
 import numpy as np
 import pytest
@@ -118,6 +119,32 @@ def test_fp32_adjoint_close_to_fp64(mods):
     assert np.linalg.norm(d32 - d64) <= 1e-2 * np.linalg.norm(d64)
     assert n32 == pytest.approx(n64, rel=1e-2)
     assert R32 == pytest.approx(R64, rel=1e-2)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_adjoint_is_independent_of_the_segmentation(mods, prec):
+    """The reverse sweep recomputes each checkpoint segment on a second
+    stream while the reverse steps of the following segment run.  The
+    kernels and their inputs do not depend on how the run is cut, so every
+    segmentation must give the same J and gradients bit for bit: one segment
+    (nothing recomputed beside the reverse steps), even segments (replayed
+    stage graphs), odd ones (both adjoint-buffer parities) with a shorter
+    last segment, and segments of two steps."""
+    inputs, lbm = mods
+    nx, ny, steps = 48, 40, 230
+    Da = inputs.darcy_field(19, nx, ny)
+    out = []
+    for ckpt in (230, 50, 7, 2):
+        with lbm.Cavity(nx, ny, CASE["n"], 1e-2, CASE["Ra"], CASE["Pr"], CASE["porosity"], prec=prec,
+                        clamp_mode=1) as cav:
+            cav.set_darcy_field(Da)
+            out.append(cav.adjoint_nu(steps, ckpt_every=ckpt, from_rest=True))
+    J0, d0, n0, R0, peak0 = out[0]
+    assert np.abs(d0).max() > 0
+    for J, dDa, dn, dRa, peak in out[1:]:
+        assert J == J0 and dn == n0 and dRa == R0
+        assert np.array_equal(dDa, d0)
+        assert peak > 0
 
 
 def test_autograd_function_carries_the_adjoint(mods):
