@@ -64,10 +64,15 @@ __global__ void adj_seed_kernel(V *__restrict__ lam, Phys<V> p, double coef0, do
 }
 
 // Sum of v over a block of 128 threads (fixed order); thread 0 gets it.
-__device__ __forceinline__ double block128_sum(double v, double *sh)
+// Within a warp the sum runs in the compute type (for the FP32 adjoint:
+// FP32 shuffles and adds, where the FP64 pipe of this part runs at 1/64 of
+// the FP32 rate and a per-thread FP64 reduction was a serial tail of every
+// reverse step), across the four warps in FP64.
+template <class V>
+__device__ __forceinline__ double block128_sum(V v, double *sh)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = double(v);
     __syncthreads();
     const double t = threadIdx.x == 0 ? (sh[0] + sh[1]) + (sh[2] + sh[3]) : 0.0;
     __syncthreads();
@@ -131,7 +136,7 @@ adj_step_kernel(const typename Store<PREC>::S *__restrict__ st, const typename S
     dRa = vfma(pa.nu_ref, V(ch.b_nu), pa.omegaT * V(ch.b_wT));
     gDa[(int64_t)y * p.nx + x] += double(dDa);
     }
-    const double sn = block128_sum(double(dn), sh), sR = block128_sum(double(dRa), sh);
+    const double sn = block128_sum(dn, sh), sR = block128_sum(dRa, sh);
     if (threadIdx.x == 0) {
         const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
         gnb[b] += sn;
