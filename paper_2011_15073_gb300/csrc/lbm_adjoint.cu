@@ -38,6 +38,22 @@ struct Chain {
     double inv_Da;       // 1 / Da of a uniform permeability
 };
 
+// The constants the reverse step reads, in its compute type: rounded once on
+// the host (to nearest, as a conversion in the kernel would), so the FP32
+// kernel spends no FP64-pipe conversions on them.
+template <class V>
+struct ChainV {
+    V a_nu, b_nu, b_wT, inv_Da;
+};
+
+// Programmatic dependent launch: a reverse step lets the next one be
+// launched as soon as all its blocks have started, and that one loads the
+// recomputed state (written before the stage began) and then waits for the
+// whole previous step to complete before it reads or writes an adjoint or
+// gradient buffer.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
+__device__ __forceinline__ void wait_for_previous_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Seed: lambda_T = dJ/ds_T.  Nu_hot = mean_j -L (9 theta_0 - theta_1 - 8)/3
 // with theta = (T - T_c)/(T_h - T_c) and T the sum of the pulled g at
 // columns 0 and 1; every pulled value there reads exactly one slot.
@@ -88,23 +104,31 @@ template <int PREC, class V>
 __global__ void __launch_bounds__(128)
 adj_step_kernel(const typename Store<PREC>::S *__restrict__ st, const typename Store<PREC>::TauS *__restrict__ tst,
                 const V *__restrict__ lam_out, V *__restrict__ lam_in, double *__restrict__ gDa,
-                double *__restrict__ gnb, double *__restrict__ gRab, Phys<V> p, Chain ch)
+                double *__restrict__ gnb, double *__restrict__ gRab, Phys<V> p, ChainV<V> ch)
 {
     __shared__ double sh[4];
+    allow_dependent_launch();
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    V dn = V(0), dRa = V(0);
-    if (x < p.nx) {
+    const bool in = x < p.nx;
     const int64_t P = p.plane, W = p.pitch;
-    const int64_t k = (int64_t)y * W + x;
+    const int64_t k = (int64_t)y * W + (in ? x : 0);
     V f[9], g[5];
-    pull<PREC, V>(st, p, x, y, f, g);
-    const V tau_prev = V(tst[k]);
+    V tau_prev = V(1);
+    if (in) {
+        pull<PREC, V>(st, p, x, y, f, g);
+        tau_prev = V(tst[k]);
+    }
+    wait_for_previous_grid();
+    V dn = V(0), dRa = V(0);
+    if (in) {
+    // the adjoint of s_{t+1}, written by the previous step: read at L2
+    // (never from a line an earlier kernel left in this SM's L1)
     V fo[9], go[5];
 #pragma unroll
-    for (int i = 0; i < 9; i++) fo[i] = lam_out[i * P + k];
+    for (int i = 0; i < 9; i++) fo[i] = __ldcg(lam_out + i * P + k);
 #pragma unroll
-    for (int i = 0; i < 5; i++) go[i] = lam_out[(9 + i) * P + k];
-    const V tb_new = lam_out[14 * P + k];
+    for (int i = 0; i < 5; i++) go[i] = __ldcg(lam_out + (9 + i) * P + k);
+    const V tb_new = __ldcg(lam_out + 14 * P + k);
     V fb[9], gb[5], tb_prev;
     ParamAdj<V> pa;
     collide_adj<V>(p, f, g, tau_prev, k, fo, go, tb_new, fb, gb, tb_prev, pa);
@@ -129,18 +153,19 @@ adj_step_kernel(const typename Store<PREC>::S *__restrict__ st, const typename S
     // parameters: porous coefficients of this node -> Da(x) (K = Da L^2, so
     // every coefficient scales as 1/Da or 1/sqrt(Da)), in the compute type
     const Porous<V> q = porous_at(p, k);
-    const V iDa = p.da ? vrcp(load_da(p, k)) : V(ch.inv_Da);
+    const V iDa = p.da ? vrcp(load_da(p, k)) : ch.inv_Da;
     const V dDa = -iDa * (vfma(q.heK, pa.heK, q.eK * pa.eK) + V(0.5) * vfma(q.c1, pa.c1, q.eFsK * pa.eFsK));
     // nu_ref = Pr Ra^(-(2-n)/2) U_c L, n - 1, and 1/tauT with tauT - 1/2 ~ Ra^(-1/2)
-    dn = vfma(pa.nu_ref, V(ch.a_nu), pa.nm1);
-    dRa = vfma(pa.nu_ref, V(ch.b_nu), pa.omegaT * V(ch.b_wT));
-    gDa[(int64_t)y * p.nx + x] += double(dDa);
+    dn = vfma(pa.nu_ref, ch.a_nu, pa.nm1);
+    dRa = vfma(pa.nu_ref, ch.b_nu, pa.omegaT * ch.b_wT);
+    double *gd = gDa + (int64_t)y * p.nx + x;
+    *gd = __ldcg(gd) + double(dDa);
     }
     const double sn = block128_sum(dn, sh), sR = block128_sum(dRa, sh);
     if (threadIdx.x == 0) {
         const int64_t b = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-        gnb[b] += sn;
-        gRab[b] += sR;
+        gnb[b] = __ldcg(gnb + b) + sn;
+        gRab[b] = __ldcg(gRab + b) + sR;
     }
 }
 
@@ -310,6 +335,7 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
         chain.b_wT = wT * wT * (chain.tauT - 0.5) / (2.0 * chain.Ra);
         chain.inv_Da = c->lat.L * c->lat.L / c->lat.K;
     }
+    const ChainV<V> chain_v{V(chain.a_nu), V(chain.b_nu), V(chain.b_wT), V(chain.inv_Da)};
     auto seg_len_of = [&](int64_t j) { return (j + 1) * ckpt <= steps ? ckpt : steps - j * ckpt; };
     auto buf_of = [&](int64_t j) { return overlap ? (int)(j & 1) : 0; };
     // Checkpoint j into slot 0 of its segment buffer (a plain copy on the
@@ -342,9 +368,19 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
         const int b = buf_of(j), len = (int)seg_len_of(j);
         int cc = c0;
         for (int i = len - 1; i >= 0; i--) {
-            adj_step_kernel<PREC, V><<<grid, 128, 0, c->stream>>>(sgd(b, i), sgt(b, i), lam[cc], lam[cc ^ 1], g3,
-                                                                 g3 + nn, g3 + nn + nblk, pv, chain);
-            if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = grid;
+            cfg.blockDim = dim3(128);
+            cfg.stream = c->stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            attr[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            if (cudaLaunchKernelEx(&cfg, adj_step_kernel<PREC, V>, (const S *)sgd(b, i), (const TauS *)sgt(b, i),
+                                   (const V *)lam[cc], lam[cc ^ 1], g3, g3 + nn, g3 + nn + nblk, pv, chain_v) !=
+                cudaSuccess)
+                return LBM_ERR_CUDA;
             cc ^= 1;
         }
         return LBM_OK;
