@@ -377,10 +377,18 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
             attr[0].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            if (cudaLaunchKernelEx(&cfg, adj_step_kernel<PREC, V>, (const S *)sgd(b, i), (const TauS *)sgt(b, i),
-                                   (const V *)lam[cc], lam[cc ^ 1], g3, g3 + nn, g3 + nn + nblk, pv, chain_v) !=
-                cudaSuccess)
-                return LBM_ERR_CUDA;
+            auto launch = [&] {
+                return cudaLaunchKernelEx(&cfg, adj_step_kernel<PREC, V>, (const S *)sgd(b, i),
+                                          (const TauS *)sgt(b, i), (const V *)lam[cc], lam[cc ^ 1], g3, g3 + nn,
+                                          g3 + nn + nblk, pv, chain_v);
+            };
+            cudaError_t e = launch();
+            if (e != cudaSuccess) {   // a stream that refuses the attribute: an ordinary launch
+                cudaGetLastError();
+                cfg.numAttrs = 0;
+                e = launch();
+            }
+            if (e != cudaSuccess) return LBM_ERR_CUDA;
             cc ^= 1;
         }
         return LBM_OK;
