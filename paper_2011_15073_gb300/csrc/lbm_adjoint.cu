@@ -294,7 +294,10 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
     // state i of the segment held in buffer b
     auto sgd = [&](int b, int i) { return (S *)(segs[b] + (size_t)i * (dist_bytes + tau_bytes)); };
     auto sgt = [&](int b, int i) { return (TauS *)(segs[b] + (size_t)i * (dist_bytes + tau_bytes) + dist_bytes); };
-    // forward with checkpoints (the context's own buffers advance to s_T)
+    // forward with checkpoints (the context's own buffers advance to s_T),
+    // through lbm_step, so small grids replay the context's step graphs
+    // (same kernels and arguments as plain launches: identical states); it
+    // also advances the context's step count
     for (int64_t j = 0; j < nseg && rc == LBM_OK; j++) {
         if (cudaMemcpyAsync(ckd(j), c->buf.dist[c->cur], dist_bytes, cudaMemcpyDeviceToDevice, c->stream) ||
             cudaMemcpyAsync(ckt(j), c->buf.tau[c->cur], tau_bytes, cudaMemcpyDeviceToDevice, c->stream)) {
@@ -302,8 +305,7 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
             break;
         }
         const int64_t len = (j + 1) * ckpt <= steps ? ckpt : steps - j * ckpt;
-        for (int64_t s = 0; s < len && rc == LBM_OK; s++)
-            if (lbm::launch_step(c) != cudaSuccess) rc = LBM_ERR_CUDA;
+        rc = lbm_step(c, len);
     }
     // J and the seed
     if (rc == LBM_OK && lbm::launch_nusselt(c) != cudaSuccess) rc = LBM_ERR_CUDA;
@@ -485,7 +487,6 @@ int run_adjoint(lbm_ctx *c, int64_t steps, int ckpt, int from_rest, double *J, d
         }
         if (dn) *dn = gn;
         if (dRa) *dRa = gR;
-        c->steps += steps;
         c->have_snap = false;
     }
     cleanup();
