@@ -10,7 +10,13 @@ respect to the parameters (per-node Darcy field, power-law index n, Rayleigh
 number Ra) through a whole run.  It is pinned to ``oracle.c`` by a CPU test
 (same states to round-off) and its gradients to central differences of the C
 oracle.  Branches of the literal power law are taken by the forward values
-(the derivative is the one of the branch taken).
+(the derivative is the one of the branch taken).  The node-local implicit
+tau (tau_iters > 0: Newton steps on ln tau toward tau = Phi(tau), the
+alternative to the lagged tau for the implicit tau-strain coupling of the
+collision-matrix and strain-rate equations) is restated too, and autograd
+differentiates through its Newton steps as computed; it is pinned to the C
+oracle's implicit solve node by node and over whole runs, and its gradients
+to central differences of the C oracle run with the same Newton steps.
 """
 from __future__ import annotations
 
@@ -46,8 +52,9 @@ class Params:
     following the same mapping as the C oracle's orc_map_params."""
 
     def __init__(self, nx, ny, n, Ra, Da, Pr, porosity=0.6, Ma=0.1, porous_model=1, clamp_mode=0,
-                 s_e=1.5, s_p=1.5):
+                 s_e=1.5, s_p=1.5, tau_iters=0):
         self.nx, self.ny = nx, ny
+        self.tau_iters = int(tau_iters)
         self.n = n if torch.is_tensor(n) else torch.tensor(float(n), dtype=DT)
         self.Ra = Ra if torch.is_tensor(Ra) else torch.tensor(float(Ra), dtype=DT)
         Da = Da if torch.is_tensor(Da) else torch.tensor(Da, dtype=DT)
@@ -133,8 +140,13 @@ def _apparent(p: Params, gs):
     return torch.pow(torch.clamp(gs, p.gamma1, p.gamma2), nm1)
 
 
-def collide(fs, gs, tau_prev, p: Params):
-    """Node update of every node, steps 1-9 of oracle.c's node_update."""
+def _strain(fs, gs, tau_in, p: Params, want_R=False):
+    """Steps 1-6 of oracle.c's node update (its strain_state) for every node,
+    started from the relaxation time tau_in: the porous velocity, the force,
+    and |gamma| from the literal strain-rate sum; with want_R also
+    R = d ln|gamma| / d ln(1/tau_in) at fixed velocity (omega gamma:gamma_p /
+    gamma:gamma, gamma_p the same sum with S replaced by diag(0, ..., 0, 1, 1)),
+    0 where gamma = 0."""
     ex, ey = E9[:, 0][:, None, None], E9[:, 1][:, None, None]
     rho = fs.sum(0)
     jx = (fs * ex).sum(0)
@@ -144,32 +156,73 @@ def collide(fs, gs, tau_prev, p: Params):
     Gy = p.gbeta * (T - p.Tm)
     vx = jx / rho + 0.5 * p.eps * Gx
     vy = jy / rho + 0.5 * p.eps * Gy
-    nu_prev = (tau_prev - 0.5) / 3.0
+    nu_in = (tau_in - 0.5) / 3.0
     K = p.K
-    c0 = 0.5 * (1.0 + p.eps * nu_prev / (2.0 * K))
+    c0 = 0.5 * (1.0 + p.eps * nu_in / (2.0 * K))
     c1 = p.eps * p.Feps / (2.0 * torch.sqrt(torch.as_tensor(K, dtype=DT)))
     vmag = torch.sqrt(vx * vx + vy * vy)
     den = c0 + torch.sqrt(c0 * c0 + c1 * vmag)
     ux, uy = vx / den, vy / den
     umag = torch.sqrt(ux * ux + uy * uy)
     sK = torch.sqrt(torch.as_tensor(K, dtype=DT))
-    Fx = -p.eps * nu_prev * ux / K - p.eps * p.Feps * umag * ux / sK + p.eps * Gx
-    Fy = -p.eps * nu_prev * uy / K - p.eps * p.Feps * umag * uy / sK + p.eps * Gy
+    Fx = -p.eps * nu_in * ux / K - p.eps * p.Feps * umag * ux / sK + p.eps * Gx
+    Fy = -p.eps * nu_in * uy / K - p.eps * p.Feps * umag * uy / sK + p.eps * Gy
     # velocity-space equilibrium and the literal strain-rate sum
     eu = ex * ux + ey * uy
     u2 = ux * ux + uy * uy
     W = W9[:, None, None]
     feq = W * rho * (1.0 + 3.0 * eu + 4.5 * eu * eu / p.eps - 1.5 * u2 / p.eps)
     fneq = fs - feq
-    Sp = p.s[:, None, None].expand(9, *tau_prev.shape).clone()
-    Sp[7] = 1.0 / tau_prev
-    Sp[8] = 1.0 / tau_prev
-    mneq = torch.einsum("ij,jyx->iyx", M, fneq) * Sp
-    h = torch.einsum("ij,jyx->iyx", MINV, mneq)
+    Sp = p.s[:, None, None].expand(9, *rho.shape).clone()
+    Sp[7] = 1.0 / tau_in
+    Sp[8] = 1.0 / tau_in
+    mfneq = torch.einsum("ij,jyx->iyx", M, fneq)
+    h = torch.einsum("ij,jyx->iyx", MINV, mfneq * Sp)
     gxx = -3.0 / (2.0 * rho) * (h * ex * ex).sum(0)
     gyy = -3.0 / (2.0 * rho) * (h * ey * ey).sum(0)
     gxy = -3.0 / (2.0 * rho) * (h * ex * ey).sum(0)
-    gamma = torch.sqrt(2.0 * (gxx * gxx + gyy * gyy + 2.0 * gxy * gxy))
+    gg = gxx * gxx + gyy * gyy + 2.0 * gxy * gxy
+    gamma = torch.sqrt(2.0 * gg)
+    R = None
+    if want_R:
+        Pm = torch.zeros(9, dtype=DT)
+        Pm[7] = Pm[8] = 1.0
+        hp = torch.einsum("ij,jyx->iyx", MINV, mfneq * Pm[:, None, None])
+        pxx = -3.0 / (2.0 * rho) * (hp * ex * ex).sum(0)
+        pyy = -3.0 / (2.0 * rho) * (hp * ey * ey).sum(0)
+        pxy = -3.0 / (2.0 * rho) * (hp * ex * ey).sum(0)
+        ggp = gxx * pxx + gyy * pyy + 2.0 * gxy * pxy
+        safe = torch.where(gg > 0, gg, torch.ones_like(gg))
+        R = torch.where(gg > 0, (1.0 / tau_in) * ggp / safe, torch.zeros_like(gg))
+    return rho, T, ux, uy, Fx, Fy, gamma, R
+
+
+def implicit_tau(fs, gs, p: Params, iters):
+    """oracle.c's node-local implicit tau for every node: `iters` Newton steps
+    on ln tau toward tau = Phi(tau) = 3 nu_ref D(gamma*(tau)) + 1/2 from the
+    rest-state tau0, tau <- tau (Phi / tau)^(1/J) with
+    J = 1 - (1 - n) R (Phi - 1/2) / Phi where the power law has slope
+    (gamma1 < gamma* < gamma2), else J = 1 and tau <- Phi."""
+    tau = p.tau0 * torch.ones(fs.shape[1:], dtype=DT)
+    for _ in range(iters):
+        *_, gamma, R = _strain(fs, gs, tau, p, want_R=True)
+        gsn = gamma * p.gamma_scale
+        phi = 3.0 * p.nu_ref * _apparent(p, gsn) + 0.5
+        slope = (gsn > p.gamma1) & (gsn < p.gamma2)
+        J = torch.where(slope, 1.0 - (1.0 - p.n) * R * (phi - 0.5) / phi, torch.ones_like(phi))
+        newton = tau * torch.pow(phi / tau, 1.0 / J)
+        tau = torch.where(J == 1.0, phi, newton)
+    return tau
+
+
+def collide(fs, gs, tau_prev, p: Params):
+    """Node update of every node, steps 1-9 of oracle.c's node_update, started
+    from tau_prev (the lagged tau, or the implicit one)."""
+    ex, ey = E9[:, 0][:, None, None], E9[:, 1][:, None, None]
+    rho, T, ux, uy, Fx, Fy, gamma, _ = _strain(fs, gs, tau_prev, p)
+    eu = ex * ux + ey * uy
+    u2 = ux * ux + uy * uy
+    W = W9[:, None, None]
     nu = p.nu_ref * _apparent(p, gamma * p.gamma_scale)
     tau = 3.0 * nu + 0.5
     # forced MRT collision
@@ -196,9 +249,13 @@ def collide(fs, gs, tau_prev, p: Params):
 
 
 def step(f, g, tau, p: Params, k=1):
+    """k steps.  With p.tau_iters > 0 each collision starts from the implicit
+    tau and the tau passed in is not used (the returned tau is then the one
+    the last collision produced, which the C oracle does not keep)."""
     for _ in range(k):
         fs, gs = stream(f, g, p)
-        f, g, tau = collide(fs, gs, tau, p)
+        t_in = implicit_tau(fs, gs, p, p.tau_iters) if p.tau_iters > 0 else tau
+        f, g, tau = collide(fs, gs, t_in, p)
     return f, g, tau
 
 
