@@ -7,8 +7,9 @@
 // post-collision slot to exactly one pulled value (a neighbour, or the node
 // itself across a wall, negated by the anti-bounce-back), so P^T is a scatter
 // in which every slot is written once: no atomics.  Parameter gradients
-// (per-node Darcy number, n, Ra) are summed per node in FP64 planes that
-// each node owns, and reduced once at the end.
+// accumulate in FP64 over the steps: the per-node Darcy number in a plane
+// that each node owns, n and Ra in one slot per block (fixed order), reduced
+// once at the end.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
